@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the Naive Bayes hot path on one GB300 (or N independent replicas).
+
+One step = one pass of the whole hot path over the workload's synthetic data:
+    nb_refit   on the training split (exact class counts -> FP64 tables)
+  + nb_score_group over all N files (log-odds / scores, label, margin,
+    log posteriors, FP64 recheck of marked rows).
+Default workload: 2 classes, N = 1,000,000 files x F = 1,024 opcode-count
+features (u16 counts, Dirichlet(0.1) class profiles, lognormal(8.5, 1) file
+totals, 2:1 per-class train split), stored as u8 + overflow list.  The plain
+FP32 path (FP32 feature storage) is timed on the same data and reported beside.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("files/sec & HBM-roofline % at F=1024, plain FP32 vs low-prec; "
+          "serving p99 latency")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev, self.proc, self.lines = dev, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[4 + k].lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def make_workload(args, device):
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    import synth
+    seed = synth.seed_for(2)
+    N, F = args.n, args.F
+    p = synth.dirichlet_profiles(seed, 2, F, 0.1)
+    y = synth.labels_bernoulli(seed + 1, N)
+    T = synth.file_totals(seed + 2, N, 8.5, 1.0)
+    X16 = synth.count_rows(seed + 3, p, y, T, 65535, out_dtype="uint16", device=device,
+                           chunk_rows=1 << 16)
+    tr, _ = synth.split_per_class(seed + 4, y)
+    tr_dev = torch.as_tensor(tr, device=device)
+    X16_tr = X16.view(torch.int16).index_select(0, tr_dev).view(torch.uint16)
+    y_dev = torch.as_tensor(y, device=device)
+    y_tr = y_dev.index_select(0, tr_dev).contiguous()
+    low_all = nb.pack_u8(X16)
+    low_tr = nb.pack_u8(X16_tr)
+    torch.cuda.synchronize()
+    return {"X16": X16, "X16_tr": X16_tr, "y": y, "y_dev": y_dev, "tr": tr, "y_tr": y_tr,
+            "low_all": low_all, "low_tr": low_tr, "p": p}
+
+
+def _out(n, C, device):
+    import torch
+    return {"label": torch.empty(n, dtype=torch.uint8, device=device),
+            "margin": torch.empty(n, dtype=torch.float32, device=device),
+            "logpost": torch.empty((n, C), dtype=torch.float32, device=device),
+            "n_rechecked": torch.zeros(1, dtype=torch.int64, device=device)}
+
+
+def _features_bytes(f):
+    # bytes the scorer reads: the F used columns of each row + side arrays
+    b = f.n * f.F * f.data.element_size()
+    for t in (f.ovf_ptr, f.ovf_col, f.ovf_add, f.row_exp):
+        if t is not None:
+            b += t.numel() * t.element_size()
+    return b
+
+
+def time_steps(model, ftr, y_tr, fall, out, steps, warmup, stream):
+    """Time `steps` refit+score steps; per-step fit / score durations too."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            nb.refit(model, ftr, y_tr, no_sync=True, stream=stream)
+            nb.score(model, fall, out=out, stream=stream)
+        stream.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        l0 = nb.nb_kernel_launches()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            nb.refit(model, ftr, y_tr, no_sync=True, stream=stream)
+            ev[k][1].record(stream)
+            nb.score(model, fall, out=out, stream=stream)
+            ev[k][2].record(stream)
+        t1.record(stream)
+        stream.synchronize()
+        launches = nb.nb_kernel_launches() - l0
+    total = t0.elapsed_time(t1)
+    fit = [e[0].elapsed_time(e[1]) for e in ev]
+    sc = [e[1].elapsed_time(e[2]) for e in ev]
+    return total, fit, sc, launches
+
+
+def time_e2e(model, host, dev, out, host_out, steps, warmup, stream):
+    """Same step through the C ABI with host buffers: H2D of the step's inputs
+    from pinned memory, refit + score, D2H of the results."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    with torch.cuda.stream(stream):
+        def one():
+            for k in host:
+                dev[k].copy_(host[k], non_blocking=True)
+            nb.refit(model, dev["ftr"], dev["y_tr"], no_sync=True, stream=stream)
+            nb.score(model, dev["fall"], out=out, stream=stream)
+            for k in ("label", "margin", "logpost"):
+                host_out[k].copy_(out[k], non_blocking=True)
+        for _ in range(warmup):
+            one()
+        stream.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            one()
+        t1.record(stream)
+        stream.synchronize()
+    return t0.elapsed_time(t1) / steps
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ----------------------------------------------------------------------------
+def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_total):
+    """Time the FP64 oracle (single thread) on a sample; extrapolate one step."""
+    import oracle
+    Xf = X16_host_fit.astype(np.float64)
+    t = time.perf_counter()
+    m = oracle.mn_fit(Xf, y_fit, 2)
+    t_fit = time.perf_counter() - t
+    del Xf
+    t_score = 0.0
+    chunk = 50_000
+    for r0 in range(0, X16_host_score.shape[0], chunk):
+        Xs = X16_host_score[r0:r0 + chunk].astype(np.float64)
+        t = time.perf_counter()
+        oracle.score(Xs, m, nthreads=1)
+        t_score += time.perf_counter() - t
+    nf, ns = X16_host_fit.shape[0], X16_host_score.shape[0]
+    step_s = t_fit * (n_train_total / nf) + t_score * (n_total / ns)
+    return {"value": n_total / step_s, "unit": "files/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, 1 thread: fit on {nf} training files "
+                      f"({t_fit:.2f} s) + score {ns} files ({t_score:.2f} s), "
+                      f"extrapolated linearly to fit {n_train_total} + score {n_total}",
+            "step_s_extrapolated": step_s}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    import torch
+    seed = synth.seed_for(2)
+    n_fit, n_score = args.ref_fit_rows, args.ref_score_rows
+    N, F = args.n, args.F
+    p = synth.dirichlet_profiles(seed, 2, F, 0.1)
+    y = synth.labels_bernoulli(seed + 1, N)
+    T = synth.file_totals(seed + 2, N, 8.5, 1.0)
+    tr, _ = synth.split_per_class(seed + 4, y)
+    n_fit = min(n_fit, len(tr))
+    n_score = min(n_score, N)
+    rows = np.unique(np.concatenate([tr[:n_fit], np.arange(n_score)]))
+    sub = synth.count_rows(seed + 3, p, y[rows], T[rows], 65535, out_dtype="uint16",
+                           device="cpu")
+    Xs = sub.view(torch.int16).numpy().view(np.uint16)
+    pos = {r: k for k, r in enumerate(rows)}
+    Xfit = Xs[[pos[r] for r in tr[:n_fit]]]
+    Xsc = Xs[[pos[r] for r in range(n_score)]]
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(Xfit[: max(1000, n_fit // 10)], y[tr[: max(1000, n_fit // 10)]],
+                          Xsc[: max(1000, n_score // 10)], len(tr), N)
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(Xfit, y[tr[:n_fit]], Xsc, len(tr), N))
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "files/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median([x["step_s_extrapolated"] for x in vals]) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"multinomial NB, C=2, N={N} files x F={F} u16 counts",
+                       "N": N, "F": F, "C": 2},
+            "cpu_baseline": {"value": v, "unit": "files/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "files/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--F", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-fit-rows", type=int, default=100_000)
+    ap.add_argument("--cpu-score-rows", type=int, default=200_000)
+    ap.add_argument("--ref-fit-rows", type=int, default=20_000)
+    ap.add_argument("--ref-score-rows", type=int, default=40_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1905_13746_gb300 as nb
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    nb.build()
+    nb.lib()
+
+    W = make_workload(args, device)
+    N, F, C = args.n, args.F, 2
+    stream = torch.cuda.Stream(device)
+    out = _out(N, C, device)
+    with torch.cuda.stream(stream):
+        model = nb.fit(W["low_tr"], W["y_tr"], C, stream=stream)   # validated fit
+    stream.synchronize()
+
+    hbm_peak, peak_kind = _peaks()
+    # ---- low-precision (u8 + overflow) step, the headline -----------------
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        total_ms, fit_ms, sc_ms, launches = time_steps(
+            model, W["low_tr"], W["y_tr"], W["low_all"], out, args.steps, args.warmup, stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_step = total_ms / args.steps
+    n_rechecked = int(out["n_rechecked"].item())
+
+    # ---- plain FP32 step on the same data ---------------------------------
+    f32_all = nb.Features(W["X16"].to(torch.int32).to(torch.float32), nb.NB_F32)
+    f32_tr = nb.Features(W["X16_tr"].to(torch.int32).to(torch.float32), nb.NB_F32)
+    with torch.cuda.stream(stream):
+        m32 = nb.fit(f32_tr, W["y_tr"], C, stream=stream)
+    p_total, p_fit, p_sc, _ = time_steps(m32, f32_tr, W["y_tr"], f32_all, out, args.steps,
+                                         args.warmup, stream)
+    p_rechecked = int(out["n_rechecked"].item())
+    del f32_all, f32_tr, m32
+    torch.cuda.empty_cache()
+
+    # ---- roofline of the dominant kernel (the score call) ------------------
+    score_bytes = _features_bytes(W["low_all"]) + N * (1 + 4 + 4 * C)
+    fit_bytes = _features_bytes(W["low_tr"]) + W["y_tr"].numel() * 4
+    sc_avg = statistics.mean(sc_ms)
+    fit_avg = statistics.mean(fit_ms)
+    achieved = score_bytes / (sc_avg * 1e-3) / 1e9
+    plain_score_bytes = N * F * 4 + N * (1 + 4 + 4 * C)
+    plain_ach = plain_score_bytes / (statistics.mean(p_sc) * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    e2e = None
+    if not args.no_e2e:
+        lt, la = W["low_tr"], W["low_all"]
+        names = {"tr_plane": lt.data, "tr_ptr": lt.ovf_ptr, "tr_col": lt.ovf_col,
+                 "tr_add": lt.ovf_add, "y_tr": W["y_tr"], "all_plane": la.data,
+                 "all_ptr": la.ovf_ptr, "all_col": la.ovf_col, "all_add": la.ovf_add}
+        host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in names.items()}
+        for k, v in names.items():
+            host[k].copy_(v)
+        devb = {k: torch.empty_like(v) for k, v in names.items()}
+        dev = {"ftr": nb.Features(devb["tr_plane"], nb.NB_U8, devb["tr_ptr"], devb["tr_col"],
+                                  devb["tr_add"]),
+               "fall": nb.Features(devb["all_plane"], nb.NB_U8, devb["all_ptr"],
+                                   devb["all_col"], devb["all_add"]),
+               "y_tr": devb["y_tr"]}
+        host_pairs = {k: host[k] for k in names}
+        dev_pairs = dict(devb)
+        hb = sum(t.numel() * t.element_size() for t in host.values())
+        host_out = {k: torch.empty_like(out[k], device="cpu").pin_memory()
+                    for k in ("label", "margin", "logpost")}
+        db = sum(t.numel() * t.element_size() for t in host_out.values())
+        # the copy targets are the device buffers behind dev["ftr"] / dev["fall"]
+        e2e_ms = time_e2e(model, host_pairs, dev_pairs | dev, out, host_out,
+                          max(3, args.steps // 2), args.warmup, stream)
+        e2e = {"value": N / (e2e_ms * 1e-3), "unit": "files/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
+        del host, devb, dev
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only) -----------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        tr = W["tr"]
+        nfit = min(args.cpu_fit_rows, len(tr))
+        fit_rows = torch.as_tensor(tr[:nfit], device=device)
+        Xfit = W["X16"].view(torch.int16).index_select(0, fit_rows).cpu().numpy().view(np.uint16)
+        Xsc = W["X16"][: args.cpu_score_rows].view(torch.int16).cpu().numpy().view(np.uint16)
+        cpu = cpu_oracle_sample(Xfit, W["y"][tr[:nfit]], Xsc, len(tr), N)
+        cpu.pop("step_s_extrapolated", None)
+
+    files_per_s = ws * N / (ms_step * 1e-3)
+    line = {
+        "metric": METRIC, "value": files_per_s, "unit": "files/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"multinomial NB, C=2, N={N} files x F={F} opcode counts "
+                               f"(u16 generated, stored u8 + overflow list), fit on the "
+                               f"2:1 per-class train split ({len(W['tr'])} files) + score "
+                               f"all N with log posteriors and FP64 recheck",
+                   "N": N, "F": F, "C": 2, "train_files": len(W["tr"]),
+                   "storage": "u8+overflow", "weights": "22-bit fixed-point Delta, int8 limbs",
+                   "l2": "inputs larger than L2 (score reads %.2f GB per step)" % (score_bytes / 1e9),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "kernel": "nb_score_group (k_score2_u8 + recheck scan)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes": score_bytes,
+                     "ms": sc_avg},
+        "fit": {"ms": fit_avg, "algorithmic_bytes": fit_bytes,
+                "gbs": fit_bytes / (fit_avg * 1e-3) / 1e9},
+        "score_files_per_s": N / (sc_avg * 1e-3),
+        "n_rechecked": n_rechecked,
+        "plain_fp32": {"ms_per_step": p_total / args.steps, "files_per_s": N / (p_total / args.steps * 1e-3),
+                       "score_ms": statistics.mean(p_sc), "fit_ms": statistics.mean(p_fit),
+                       "score_gbs": plain_ach, "score_frac": plain_ach / hbm_peak,
+                       "n_rechecked": p_rechecked},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * nbgpu -- Naive Bayes fit and group scoring on one sm_103a GPU (C ABI).
+ *
+ * Method: Sahay & Chaudhari, "An Efficient Detection of Malware by Naive
+ * Bayes Classifier Using GPGPU".
+ *   Sec. 3  files are opcode-occurrence-count vectors, partitioned into
+ *           size groups;
+ *   Sec. 4  a Naive Bayes model is trained on labelled vectors; a file's
+ *           posterior is P(C | a_1..a_n) = P(a_1..a_n | C) / P(a_1..a_n)
+ *           with class-conditionally independent features (the single
+ *           display equation), and the file is malware when the malware
+ *           posterior is higher, otherwise benign (the decision rule below
+ *           it); the files of a group are classified in parallel on the GPU.
+ *
+ * Readings used throughout (the paper leaves them open):
+ *   - count features: multinomial event model, Laplace smoothing alpha
+ *     (default 1): log theta_cj = log(N_cj + alpha) - log(N_c + alpha F);
+ *   - real features: Gaussian class densities, maximum-likelihood variance
+ *     plus eps = var_smoothing * max_j Var(x_.j);
+ *   - prior: empirical n_c / n unless log priors are supplied;
+ *   - ties go to the lowest class index (benign = 0 for two classes);
+ *   - margin = (top score) - (second score), natural-log units, >= 0;
+ *   - logpost_c = s_c - logsumexp_c(s), so the dropped evidence and the
+ *     multinomial coefficient (class-independent) do not matter.
+ *
+ * Conventions
+ *   - Every pointer named X, y, label, margin, logpost, ovf_*, row_exp,
+ *     n_rechecked is a caller-owned DEVICE pointer unless stated otherwise.
+ *     Models and servers are library-owned opaque handles.
+ *   - Matrices are row-major, one row per file, leading dimension `ld`
+ *     elements (ld >= F).  The buffer must be readable for n * ld elements.
+ *     The fast paths need base and ld * element_size 16-byte aligned; other
+ *     layouts take a slower, still exact, path.
+ *   - Calls are asynchronous on the given CUDA stream (`cuda_stream` is a
+ *     cudaStream_t; NULL = legacy default stream) unless documented.
+ *   - No exception crosses the ABI.  Every call returns an nb_status; the
+ *     message of the last failure on the calling thread is nb_last_error().
+ *   - C <= 255 (labels are uint8; 255 is reserved as an internal marker).
+ */
+#ifndef NBGPU_H
+#define NBGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NB_API __attribute__((visibility("default")))
+#else
+#define NB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NB_OK = 0,
+  NB_EINVAL = 1,        /* bad argument or invalid data (e.g. a label >= C) */
+  NB_ENOMEM = 2,        /* a device or host allocation failed */
+  NB_ECUDA = 3,         /* a CUDA runtime call failed */
+  NB_ETIMEOUT = 4,      /* a bounded wait ran out */
+  NB_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+  NB_EBUSY = 6          /* no free slot or memory for the request */
+} nb_status;
+
+typedef enum { NB_MULTINOMIAL = 0, NB_GAUSSIAN = 1 } nb_kind;
+
+/* Feature storage types.  Counts are exact in U16 (0..65535), in U8 (0..255,
+ * or up to 255 + 65535 with the overflow list of nb_aux), in BF16 up to 256
+ * and in FP8 E4M3 up to 16 (above, the per-row power-of-two scale of nb_aux
+ * applies and values are rounded to the format). */
+typedef enum {
+  NB_F32 = 0,
+  NB_U16 = 1,
+  NB_U8 = 2,
+  NB_BF16 = 3,
+  NB_FP8E4M3 = 4
+} nb_dtype;
+
+/* Side arrays of the compact storage formats (all device pointers).
+ *   NB_U8 overflow list: row i's entries are ovf_ptr[i] .. ovf_ptr[i+1]-1; an
+ *     entry (ovf_col[k], ovf_add[k]) adds ovf_add[k] to the stored byte (255)
+ *     of column ovf_col[k].  ovf_ptr has n+1 entries, ovf_ptr[0] = 0.
+ *   NB_FP8E4M3 row scale: row i's values are multiplied by 2^row_exp[i]. */
+typedef struct {
+  const int64_t* ovf_ptr;
+  const uint16_t* ovf_col;
+  const uint16_t* ovf_add;
+  const int8_t* row_exp;
+} nb_aux;
+
+typedef struct {
+  double alpha;             /* multinomial smoothing (>= 0); 1 = Laplace */
+  const double* log_prior;  /* HOST pointer to C log priors, or NULL = empirical */
+  double var_smoothing;     /* Gaussian epsilon factor (>= 0), default 1e-9 */
+  const nb_aux* aux;        /* side arrays of X's format, or NULL */
+  int no_sync;              /* 0: nb_fit waits for the stream and reports
+                               invalid data (labels outside [0,C), negative or
+                               fractional counts) as NB_EINVAL; 1: fully
+                               asynchronous, check later with nb_model_check */
+} nb_fit_opts;
+
+/* Recheck policy for rows whose FP32/fixed-point result might differ from
+ * the FP64 definition:
+ *   NB_RECHECK_OFF   -- no recheck (labels may differ on near-ties);
+ *   NB_RECHECK_LABEL -- rows whose margin is within the rigorous error bound
+ *                       of the fast path are recomputed in FP64, so every
+ *                       label equals the FP64 decision;
+ *   NB_RECHECK_LP    -- additionally rows whose log posteriors could be off
+ *                       by more than 1e-5 * max(1, |logpost|).  */
+typedef enum { NB_RECHECK_OFF = 0, NB_RECHECK_LABEL = 1, NB_RECHECK_LP = 2 } nb_recheck;
+
+typedef struct {
+  int want_logpost;     /* write logpost (n x C, float) when non-zero */
+  nb_recheck recheck;   /* default NB_RECHECK_LP */
+  const nb_aux* aux;    /* side arrays of X's format, or NULL */
+} nb_score_opts;
+
+typedef struct nb_model nb_model;
+typedef struct nb_server nb_server;
+
+/* ---- fit -----------------------------------------------------------------
+ * Train one model on n labelled files (Sec. 4, "trained the model").
+ *   kind  NB_MULTINOMIAL: X holds counts (U8[+overflow], U16, F32, BF16,
+ *         FP8E4M3 with integer values); N_cj is accumulated exactly in
+ *         uint64, then log theta and log prior in FP64 on the device.
+ *         NB_GAUSSIAN: X holds real values (F32); class means and MLE
+ *         variances are computed in FP64 by two deterministic passes.
+ *   y     int32 labels in [0, C) (device), n entries.
+ *   C     2 <= C <= 255;  F >= 1.
+ * On success *out owns device tables; free it with nb_model_free.  Errors:
+ * NB_EINVAL (arguments, or invalid data when opts->no_sync == 0), NB_ENOMEM,
+ * NB_ECUDA.  The call may allocate device memory. */
+NB_API nb_status nb_fit(nb_kind kind, const void* X, nb_dtype dtype, int64_t n,
+                 int32_t F, int64_t ld, const int32_t* y, int32_t C,
+                 const nb_fit_opts* opts, void* cuda_stream, nb_model** out);
+
+/* Re-trains an existing model in place on new data with the same F and C
+ * (kind, C and F are the model's).  Allocates no model memory, so a training
+ * loop or a timed benchmark step does not pay for cudaMalloc / cudaFree; the
+ * count reduction still takes stream-ordered scratch (cudaMallocAsync).  The
+ * model must not be in use by a score call on another stream meanwhile.
+ * Same errors as nb_fit. */
+NB_API nb_status nb_refit(nb_model* model, const void* X, nb_dtype dtype, int64_t n,
+                   int64_t ld, const int32_t* y, const nb_fit_opts* opts,
+                   void* cuda_stream);
+
+/* Waits for the model's fit and returns NB_EINVAL if its data were invalid. */
+NB_API nb_status nb_model_check(const nb_model* model);
+
+/* Copies the exact multinomial counts N_cj (C x F) and n_c (C) to HOST
+ * buffers (either may be NULL).  Synchronises the fit's stream. */
+NB_API nb_status nb_model_counts(const nb_model* model, uint64_t* host_counts,
+                          uint64_t* host_nc);
+
+/* Copies the FP64 parameters to HOST buffers (any may be NULL):
+ *   multinomial: p0 = log theta (C x F);  Gaussian: p0 = mu, p1 = var;
+ *   log_pi (C). */
+NB_API nb_status nb_model_params(const nb_model* model, double* host_p0,
+                          double* host_p1, double* host_log_pi);
+
+/* Shape of a model (any out pointer may be NULL). */
+NB_API nb_status nb_model_info(const nb_model* model, int32_t* kind, int32_t* C,
+                        int32_t* F);
+
+NB_API void nb_model_free(nb_model* model);
+
+/* ---- score ---------------------------------------------------------------
+ * Classify n files (one group) with a fitted model (Sec. 4 posterior and
+ * decision rule).  X has F = the model's F columns in `dtype`.
+ *   label    uint8[n]   argmax class (ties -> lowest index)
+ *   margin   float[n]   top-1 minus top-2 joint log score
+ *   logpost  float[n*C] log posteriors, or NULL
+ *   n_rechecked  device int64 (or NULL): receives the number of rows this
+ *            call recomputed in FP64.
+ * Two-class multinomial models use the difference form d = s_1 - s_0 =
+ * b + sum_j x_j (log theta_1j - log theta_0j).  n may be 0.  Asynchronous. */
+NB_API nb_status nb_score_group(const nb_model* model, const void* X, nb_dtype dtype,
+                         int64_t n, int64_t ld, uint8_t* label, float* margin,
+                         float* logpost, const nb_score_opts* opts,
+                         void* cuda_stream, int64_t* n_rechecked);
+
+/* ---- storage packing (supporting; not part of a timed score) ------------
+ * U16 counts -> U8 plane + overflow list, in two calls:
+ *   nb_pack_u8_count writes ovf_ptr (n+1 entries, device) and returns the
+ *   total number of entries in *host_total (synchronises the stream);
+ *   nb_pack_u8_fill writes plane (n x ld_out bytes), ovf_col and ovf_add.
+ * Entries are ordered by row, then column. */
+NB_API nb_status nb_pack_u8_count(const uint16_t* X, int64_t n, int32_t F, int64_t ld,
+                           int64_t* ovf_ptr, int64_t* host_total,
+                           void* cuda_stream);
+NB_API nb_status nb_pack_u8_fill(const uint16_t* X, int64_t n, int32_t F, int64_t ld,
+                          uint8_t* plane, int64_t ld_out,
+                          const int64_t* ovf_ptr, uint16_t* ovf_col,
+                          uint16_t* ovf_add, void* cuda_stream);
+/* U16 or F32 non-negative values -> BF16 (round to nearest even). */
+NB_API nb_status nb_pack_bf16(const void* X, nb_dtype src, int64_t n, int32_t F,
+                       int64_t ld, uint16_t* out, int64_t ld_out,
+                       void* cuda_stream);
+/* U16 or F32 non-negative values -> FP8 E4M3 with a per-row exponent
+ * e = max(0, ceil(log2(max_row / 448))), stored byte = E4M3(x / 2^e) (round
+ * to nearest even). */
+NB_API nb_status nb_pack_fp8(const void* X, nb_dtype src, int64_t n, int32_t F,
+                      int64_t ld, uint8_t* out, int64_t ld_out,
+                      int8_t* row_exp, void* cuda_stream);
+
+/* ---- errors / misc -------------------------------------------------------*/
+NB_API const char* nb_last_error(void);
+/* Number of CUDA kernels this library has launched in this process. */
+NB_API uint64_t nb_kernel_launches(void);
+NB_API const char* nb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBGPU_H */

@@ -58,6 +58,8 @@ def _load():
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
             lib.oracle_mn_fit.argtypes = [P, i64, i32, P, i32, f64, P, P, P, P, P]
             lib.oracle_mn_fit.restype = ctypes.c_int
+            lib.oracle_mn_finalize.argtypes = [P, P, i64, i32, i32, f64, P, P, P]
+            lib.oracle_mn_finalize.restype = ctypes.c_int
             lib.oracle_gauss_fit.argtypes = [P, i64, i32, P, i32, f64, P, P, P, P, P]
             lib.oracle_gauss_fit.restype = ctypes.c_int
             lib.oracle_mn_joint.argtypes = [P, i64, i32, i32, P, P, P, ctypes.c_int]
@@ -97,6 +99,23 @@ def mn_fit(X, y, C, alpha=1.0, log_prior=None):
                            _ptr(counts), _ptr(nc), _ptr(log_theta), _ptr(log_pi))
     if rc != 0:
         raise OracleError("oracle_mn_fit rejected its arguments")
+    return {"kind": "multinomial", "counts": counts, "nc": nc,
+            "log_theta": log_theta, "log_pi": log_pi, "alpha": float(alpha)}
+
+
+def mn_finalize(counts, nc, n, alpha=1.0, log_prior=None):
+    """log theta and log prior from exact per-class counts (second half of mn_fit)."""
+    lib = _load()
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    nc = np.ascontiguousarray(nc, dtype=np.uint64)
+    C, F = counts.shape
+    lp = None if log_prior is None else _f64(log_prior)
+    log_theta = np.zeros((C, F), np.float64)
+    log_pi = np.zeros(C, np.float64)
+    rc = lib.oracle_mn_finalize(_ptr(counts), _ptr(nc), int(n), F, C, float(alpha), _ptr(lp),
+                                _ptr(log_theta), _ptr(log_pi))
+    if rc != 0:
+        raise OracleError("oracle_mn_finalize rejected its arguments")
     return {"kind": "multinomial", "counts": counts, "nc": nc,
             "log_theta": log_theta, "log_pi": log_pi, "alpha": float(alpha)}
 

@@ -42,6 +42,35 @@
 
 static const double kPi = 3.14159265358979323846;
 
+/* The second half of the multinomial fit, from exact counts:
+ *   log theta_cj = log(N_cj + alpha) - log(N_c + alpha * F),  N_c = sum_j N_cj
+ *   log pi_c     = log n_c - log n, or the supplied log prior.             */
+int oracle_mn_finalize(const uint64_t* counts, const uint64_t* nc, int64_t n,
+                       int32_t F, int32_t C, double alpha,
+                       const double* log_prior, double* log_theta,
+                       double* log_pi) {
+  if (F < 1 || C < 2 || !(alpha >= 0.0)) return OR_EINVAL;
+  for (int32_t c = 0; c < C; ++c) {
+    uint64_t Nc = 0;
+    for (int32_t j = 0; j < F; ++j) Nc += counts[(int64_t)c * F + j];
+    double log_den = log((double)Nc + alpha * (double)F);
+    for (int32_t j = 0; j < F; ++j) {
+      double num = (double)counts[(int64_t)c * F + j] + alpha;
+      log_theta[(int64_t)c * F + j] = log(num) - log_den;
+    }
+  }
+  for (int32_t c = 0; c < C; ++c) {
+    if (log_prior) {
+      if (!isfinite(log_prior[c])) return OR_EINVAL;
+      log_pi[c] = log_prior[c];
+    } else {
+      if (nc[c] == 0) return OR_EINVAL;
+      log_pi[c] = log((double)nc[c]) - log((double)n);
+    }
+  }
+  return OR_OK;
+}
+
 /* ---------------------------------------------------------------------------
  * Multinomial fit (Sec. 4: "trained the model" on per-class opcode counts).
  *   n_c    = #{i : y_i = c}
@@ -70,25 +99,8 @@ int oracle_mn_fit(const double* X, int64_t n, int32_t F, const int32_t* y,
       counts[(int64_t)c * F + j] += (uint64_t)v;
     }
   }
-  for (int32_t c = 0; c < C; ++c) {
-    uint64_t Nc = 0;
-    for (int32_t j = 0; j < F; ++j) Nc += counts[(int64_t)c * F + j];
-    double log_den = log((double)Nc + alpha * (double)F);
-    for (int32_t j = 0; j < F; ++j) {
-      double num = (double)counts[(int64_t)c * F + j] + alpha;
-      log_theta[(int64_t)c * F + j] = log(num) - log_den;
-    }
-  }
-  for (int32_t c = 0; c < C; ++c) {
-    if (log_prior) {
-      if (!isfinite(log_prior[c])) return OR_EINVAL;
-      log_pi[c] = log_prior[c];
-    } else {
-      if (nc[c] == 0) return OR_EINVAL;
-      log_pi[c] = log((double)nc[c]) - log((double)n);
-    }
-  }
-  return OR_OK;
+  return oracle_mn_finalize(counts, nc, n, F, C, alpha, log_prior, log_theta,
+                            log_pi);
 }
 
 /* ---------------------------------------------------------------------------

@@ -1,0 +1,323 @@
+"""nbgpu: Naive Bayes fit and group scoring on one sm_103a GPU.
+
+Thin Python binding over the C ABI of ``libnbgpu.so`` (declared in
+``include/nbgpu.h``).  This module only marshals arguments: every step of
+the fit and of the scoring runs in the library's CUDA kernels.  PyTorch is
+used for device memory and streams.  If the library is missing the import of
+the entry points fails loudly -- there is no CPU fallback.
+
+Low-level names mirror the C functions (``nb_fit``, ``nb_score_group`` ...)
+and take raw device pointers; ``fit`` / ``score`` / ``Model`` accept torch
+tensors.  Method: Sahay & Chaudhari, Sec. 4 (posterior and decision rule).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB, build  # noqa: F401
+
+# ---- enums (nbgpu.h) -------------------------------------------------------
+NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ETIMEOUT, NB_EUNSUPPORTED, NB_EBUSY = range(7)
+NB_MULTINOMIAL, NB_GAUSSIAN = 0, 1
+NB_F32, NB_U16, NB_U8, NB_BF16, NB_FP8E4M3 = range(5)
+NB_RECHECK_OFF, NB_RECHECK_LABEL, NB_RECHECK_LP = 0, 1, 2
+
+STATUS_NAMES = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA",
+                4: "NB_ETIMEOUT", 5: "NB_EUNSUPPORTED", 6: "NB_EBUSY"}
+
+_P = ctypes.c_void_p
+_i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class NbAux(ctypes.Structure):
+    _fields_ = [("ovf_ptr", _P), ("ovf_col", _P), ("ovf_add", _P), ("row_exp", _P)]
+
+
+class NbFitOpts(ctypes.Structure):
+    _fields_ = [("alpha", _f64), ("log_prior", _P), ("var_smoothing", _f64),
+                ("aux", ctypes.POINTER(NbAux)), ("no_sync", ctypes.c_int)]
+
+
+class NbScoreOpts(ctypes.Structure):
+    _fields_ = [("want_logpost", ctypes.c_int), ("recheck", ctypes.c_int),
+                ("aux", ctypes.POINTER(NbAux))]
+
+
+class NbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("nb_fit", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, _i64, _i32, _i64, _P, _i32,
+                              ctypes.POINTER(NbFitOpts), _P, ctypes.POINTER(_P)]),
+    ("nb_refit", ctypes.c_int, [_P, _P, ctypes.c_int, _i64, _i64, _P,
+                                ctypes.POINTER(NbFitOpts), _P]),
+    ("nb_model_check", ctypes.c_int, [_P]),
+    ("nb_model_counts", ctypes.c_int, [_P, _P, _P]),
+    ("nb_model_params", ctypes.c_int, [_P, _P, _P, _P]),
+    ("nb_model_info", ctypes.c_int, [_P, _P, _P, _P]),
+    ("nb_model_free", None, [_P]),
+    ("nb_score_group", ctypes.c_int, [_P, _P, ctypes.c_int, _i64, _i64, _P, _P, _P,
+                                      ctypes.POINTER(NbScoreOpts), _P, _P]),
+    ("nb_pack_u8_count", ctypes.c_int, [_P, _i64, _i32, _i64, _P, ctypes.POINTER(_i64), _P]),
+    ("nb_pack_u8_fill", ctypes.c_int, [_P, _i64, _i32, _i64, _P, _i64, _P, _P, _P, _P]),
+    ("nb_pack_bf16", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _P, _i64, _P]),
+    ("nb_pack_fp8", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _P, _i64, _P, _P]),
+    ("nb_last_error", ctypes.c_char_p, []),
+    ("nb_kernel_launches", ctypes.c_uint64, []),
+    ("nb_version", ctypes.c_char_p, []),
+]
+
+EXPORTED = [s[0] for s in _SIGS]
+
+
+def lib():
+    """Load libnbgpu.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(
+                    f"{LIB} is missing: build it with paper_1905_13746_gb300.build() "
+                    "(nvcc, sm_103a); there is no CPU fallback")
+            handle = ctypes.CDLL(LIB)
+            for name, res, args in _SIGS:
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def _check(status):
+    if status != NB_OK:
+        raise NbError(status, lib().nb_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- raw entry points (device pointers as ints) ---------------------------
+def nb_fit(kind, X, dtype, n, F, ld, y, C, alpha=1.0, log_prior=None, var_smoothing=1e-9,
+           aux=None, no_sync=False, stream=None):
+    prior_buf = None
+    if log_prior is not None:
+        prior_buf = (ctypes.c_double * C)(*[float(v) for v in log_prior])
+    opts = NbFitOpts(float(alpha), ctypes.cast(prior_buf, _P) if prior_buf else None,
+                     float(var_smoothing), ctypes.pointer(aux) if aux else None, int(no_sync))
+    out = _P()
+    _check(lib().nb_fit(kind, X, dtype, n, F, ld, y, C, ctypes.byref(opts),
+                        _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def nb_refit(model, X, dtype, n, ld, y, alpha=1.0, log_prior=None, var_smoothing=1e-9,
+             aux=None, no_sync=False, stream=None):
+    prior_buf = None
+    if log_prior is not None:
+        prior_buf = (ctypes.c_double * len(log_prior))(*[float(v) for v in log_prior])
+    opts = NbFitOpts(float(alpha), ctypes.cast(prior_buf, _P) if prior_buf else None,
+                     float(var_smoothing), ctypes.pointer(aux) if aux else None, int(no_sync))
+    _check(lib().nb_refit(model, X, dtype, n, ld, y, ctypes.byref(opts), _stream_ptr(stream)))
+
+
+def nb_kernel_launches():
+    return int(lib().nb_kernel_launches())
+
+
+def nb_score_group(model, X, dtype, n, ld, label, margin, logpost=None, want_logpost=False,
+                   recheck=NB_RECHECK_LP, aux=None, stream=None, n_rechecked=None):
+    opts = NbScoreOpts(int(want_logpost), int(recheck), ctypes.pointer(aux) if aux else None)
+    _check(lib().nb_score_group(model, X, dtype, n, ld, label, margin, logpost,
+                                ctypes.byref(opts), _stream_ptr(stream), n_rechecked))
+
+
+def nb_model_free(model):
+    if model:
+        lib().nb_model_free(model)
+
+
+def nb_last_error():
+    return lib().nb_last_error().decode(errors="replace")
+
+
+# ---- torch conveniences ----------------------------------------------------
+def _torch_dtype_code(t, fp8=False):
+    import torch
+    m = {torch.float32: NB_F32, torch.uint8: NB_FP8E4M3 if fp8 else NB_U8,
+         torch.bfloat16: NB_BF16, torch.float8_e4m3fn: NB_FP8E4M3}
+    if hasattr(torch, "uint16"):
+        m[torch.uint16] = NB_U16
+    if t.dtype not in m:
+        raise TypeError(f"unsupported feature dtype {t.dtype}")
+    return m[t.dtype]
+
+
+class Features:
+    """A device feature matrix in one of the storage formats, plus side arrays."""
+
+    def __init__(self, data, dtype_code=None, ovf_ptr=None, ovf_col=None, ovf_add=None,
+                 row_exp=None):
+        self.data = data
+        self.dtype_code = _torch_dtype_code(data) if dtype_code is None else dtype_code
+        self.ovf_ptr, self.ovf_col, self.ovf_add, self.row_exp = ovf_ptr, ovf_col, ovf_add, row_exp
+        if data.dim() != 2 or (data.numel() > 0 and data.stride(1) != 1):
+            raise ValueError("features must be a row-major matrix")
+
+    @property
+    def n(self):
+        return self.data.shape[0]
+
+    @property
+    def F(self):
+        return self.data.shape[1]
+
+    @property
+    def ld(self):
+        return self.data.stride(0)
+
+    def aux(self):
+        if self.ovf_ptr is None and self.row_exp is None:
+            return None
+        p = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+        return NbAux(p(self.ovf_ptr), p(self.ovf_col), p(self.ovf_add), p(self.row_exp))
+
+    def nbytes(self):
+        b = self.data.numel() * self.data.element_size()
+        for t in (self.ovf_ptr, self.ovf_col, self.ovf_add, self.row_exp):
+            if t is not None:
+                b += t.numel() * t.element_size()
+        return b
+
+
+def as_features(X):
+    return X if isinstance(X, Features) else Features(X)
+
+
+class Model:
+    """Owns an nb_model handle (freed with the object)."""
+
+    def __init__(self, handle, kind, C, F):
+        self.handle, self.kind, self.C, self.F = handle, kind, C, F
+
+    def __del__(self):
+        try:
+            if self.handle:
+                nb_model_free(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+    def counts(self):
+        import numpy as np
+        c = np.zeros((self.C, self.F), np.uint64)
+        nc = np.zeros(self.C, np.uint64)
+        _check(lib().nb_model_counts(self.handle, c.ctypes.data, nc.ctypes.data))
+        return c, nc
+
+    def params(self):
+        import numpy as np
+        p0 = np.zeros((self.C, self.F), np.float64)
+        p1 = np.zeros((self.C, self.F), np.float64) if self.kind == NB_GAUSSIAN else None
+        lp = np.zeros(self.C, np.float64)
+        _check(lib().nb_model_params(self.handle, p0.ctypes.data,
+                                     p1.ctypes.data if p1 is not None else None, lp.ctypes.data))
+        return p0, p1, lp
+
+    def check(self):
+        _check(lib().nb_model_check(self.handle))
+
+
+def fit(X, y, C, kind=NB_MULTINOMIAL, alpha=1.0, log_prior=None, var_smoothing=1e-9,
+        no_sync=False, stream=None):
+    Xf = as_features(X)
+    h = nb_fit(kind, Xf.data.data_ptr(), Xf.dtype_code, Xf.n, Xf.F, Xf.ld, y.data_ptr(), C,
+               alpha=alpha, log_prior=log_prior, var_smoothing=var_smoothing, aux=Xf.aux(),
+               no_sync=no_sync, stream=stream)
+    return Model(h, kind, C, Xf.F)
+
+
+def refit(model, X, y, alpha=1.0, log_prior=None, var_smoothing=1e-9, no_sync=False,
+          stream=None):
+    Xf = as_features(X)
+    nb_refit(model.handle, Xf.data.data_ptr(), Xf.dtype_code, Xf.n, Xf.ld, y.data_ptr(),
+             alpha=alpha, log_prior=log_prior, var_smoothing=var_smoothing, aux=Xf.aux(),
+             no_sync=no_sync, stream=stream)
+    return model
+
+
+def score(model, X, want_logpost=True, recheck=NB_RECHECK_LP, stream=None, out=None):
+    """Score a group; returns dict(label, margin, logpost, n_rechecked) of device tensors."""
+    import torch
+    Xf = as_features(X)
+    dev = Xf.data.device
+    n = Xf.n
+    if out is None:
+        out = {"label": torch.empty(n, dtype=torch.uint8, device=dev),
+               "margin": torch.empty(n, dtype=torch.float32, device=dev),
+               "logpost": torch.empty((n, model.C), dtype=torch.float32, device=dev)
+               if want_logpost else None,
+               "n_rechecked": torch.zeros(1, dtype=torch.int64, device=dev)}
+    lp = out["logpost"].data_ptr() if want_logpost else None
+    nb_score_group(model.handle, Xf.data.data_ptr(), Xf.dtype_code, n, Xf.ld,
+                   out["label"].data_ptr(), out["margin"].data_ptr(), lp,
+                   want_logpost=want_logpost, recheck=recheck, aux=Xf.aux(), stream=stream,
+                   n_rechecked=out["n_rechecked"].data_ptr())
+    return out
+
+
+# ---- packing ---------------------------------------------------------------
+def pack_u8(X16, stream=None):
+    """u16 counts (n x F) -> Features(u8 plane + overflow list)."""
+    import torch
+    n, F = X16.shape
+    dev = X16.device
+    ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    total = _i64(0)
+    st = _stream_ptr(stream)
+    _check(lib().nb_pack_u8_count(X16.data_ptr(), n, F, X16.stride(0), ptr.data_ptr(),
+                                  ctypes.byref(total), st))
+    ld_out = (F + 15) // 16 * 16
+    plane = torch.empty((n, ld_out), dtype=torch.uint8, device=dev)[:, :F]
+    col = torch.empty(max(total.value, 1), dtype=torch.int16, device=dev)
+    add = torch.empty(max(total.value, 1), dtype=torch.int16, device=dev)
+    _check(lib().nb_pack_u8_fill(X16.data_ptr(), n, F, X16.stride(0), plane.data_ptr(), ld_out,
+                                 ptr.data_ptr(), col.data_ptr(), add.data_ptr(), st))
+    return Features(plane, NB_U8, ptr, col, add)
+
+
+def pack_bf16(X, stream=None):
+    import torch
+    n, F = X.shape
+    src = NB_F32 if X.dtype == torch.float32 else NB_U16
+    ld_out = (F + 7) // 8 * 8
+    out = torch.empty((n, ld_out), dtype=torch.bfloat16, device=X.device)[:, :F]
+    _check(lib().nb_pack_bf16(X.data_ptr(), src, n, F, X.stride(0), out.data_ptr(), ld_out,
+                              _stream_ptr(stream)))
+    return Features(out, NB_BF16)
+
+
+def pack_fp8(X, stream=None):
+    import torch
+    n, F = X.shape
+    src = NB_F32 if X.dtype == torch.float32 else NB_U16
+    ld_out = (F + 15) // 16 * 16
+    out = torch.empty((n, ld_out), dtype=torch.uint8, device=X.device)[:, :F]
+    row_exp = torch.empty(n, dtype=torch.int8, device=X.device)
+    _check(lib().nb_pack_fp8(X.data_ptr(), src, n, F, X.stride(0), out.data_ptr(), ld_out,
+                             row_exp.data_ptr(), _stream_ptr(stream)))
+    return Features(out, NB_FP8E4M3, row_exp=row_exp)

@@ -1,0 +1,137 @@
+// Internal declarations of the nbgpu library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbgpu.h"
+
+namespace nbg {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+nb_status cuda_status(cudaError_t e, const char* what);
+
+#define NB_TRY_CUDA(expr, what)                          \
+  do {                                                   \
+    cudaError_t e__ = (expr);                            \
+    if (e__ != cudaSuccess) return ::nbg::cuda_status(e__, what); \
+  } while (0)
+
+// device status word bits (model / call error words)
+enum : int {
+  ST_BAD_LABEL = 1,       // a label outside [0, C)
+  ST_BAD_VALUE = 2,       // negative, fractional or non-finite count
+  ST_TIMEOUT = 4,         // a bounded wait gave up
+  ST_BAD_TABLE = 8,       // non-finite parameter table
+  ST_OVF_RANGE = 16       // overflow column outside [0, F)
+};
+
+constexpr uint8_t kLabelRecheck = 255;   // internal marker in label[]
+
+inline int elem_size(nb_dtype d) {
+  switch (d) {
+    case NB_F32: return 4;
+    case NB_U16: return 2;
+    case NB_BF16: return 2;
+    case NB_U8: return 1;
+    case NB_FP8E4M3: return 1;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// two-class scalars produced on the device by the fit (one struct in HBM)
+// ---------------------------------------------------------------------------
+struct C2Header {
+  float b;            // log pi_1 - log pi_0 (FP32)
+  float maxabs;       // max_j |Delta_j| of the FP32 table
+  float inv_scale;    // 2^-S: fixed-point step of the integer Delta table
+  float maxabs_q;     // max_j |Delta_j| bound used with the fixed-point table
+  double b64;         // FP64 b
+  int32_t S;          // Delta_q = round(Delta * 2^S), |Delta_q| <= 2^22
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// model (library-owned)
+// ---------------------------------------------------------------------------
+struct ModelDev {
+  // all pointers into one device allocation
+  uint64_t* counts;    // C x F      (multinomial)
+  uint64_t* nc;        // C
+  double* p0;          // C x F      log theta (multinomial) | mu (Gaussian)
+  double* p1;          // C x F      var (Gaussian)
+  double* log_pi;      // C
+  double* gconst;      // C          Gaussian: log pi_c - 1/2 sum_j log(2 pi var_cj)
+  int* status;         // 1 int: ST_* bits raised while fitting
+  // two-class multinomial tables
+  C2Header* c2;        // 1
+  float* delta;        // F_pad      FP32 Delta, plain order
+  int32_t* delta_q;    // F_pad      fixed-point Delta
+  uint4* limbs;        // 3 * nvec8  int8 limbs of delta_q, interleaved (u8 path)
+  float4* il[3];       // interleaved FP32 quads for 4/8/16 elements per vector
+  // general-C tables (CUDA-core scorer)
+  float* w;            // C x F_pad  centred weights log theta_cj - mean_c log theta_cj
+  float* bias;         // C          log pi_c
+  float* wmax;         // 1          max |w|
+  // Gaussian FP32 tables
+  float* g_mu;         // C x F_pad
+  float* g_ivar;       // C x F_pad  1 / var
+  float* g_const;      // C          gconst in FP32
+};
+
+}  // namespace nbg
+
+struct nb_model {
+  nb_kind kind;
+  int C;
+  int F;
+  int F_pad;        // F rounded up to a multiple of 16
+  int nvec8;        // F_pad / 16 (u8 vectors of 16 bytes)
+  double alpha;
+  double var_smoothing;
+  int device;
+  cudaStream_t stream;   // stream of the fit
+  void* mem;
+  size_t mem_bytes;
+  nbg::ModelDev d;
+};
+
+namespace nbg {
+
+// launchers implemented in fit.cu / score2.cu / recheck.cu / pack.cu
+nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt,
+                                 int64_t n, int64_t ld, const int32_t* y,
+                                 const nb_aux* aux, const double* log_prior_dev,
+                                 cudaStream_t st);
+nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n,
+                              int64_t ld, const int32_t* y,
+                              const double* log_prior_dev, cudaStream_t st);
+
+struct ScoreOut {
+  uint8_t* label;
+  float* margin;
+  float* logpost;
+  int64_t* n_rechecked;
+  int want_lp;
+  int recheck;
+};
+
+nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt,
+                        int64_t n, int64_t ld, const nb_aux* aux,
+                        const ScoreOut& o, cudaStream_t st);
+nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt,
+                               int64_t n, int64_t ld, const nb_aux* aux,
+                               const ScoreOut& o, cudaStream_t st);
+nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt,
+                         int64_t n, int64_t ld, const nb_aux* aux,
+                         const ScoreOut& o, cudaStream_t st);
+
+int num_sms();
+// process-wide count of kernels this library has launched
+void count_launch();
+
+}  // namespace nbg

@@ -1,0 +1,436 @@
+// CUDA-core scorers for any class count (Sec. 4 posterior and decision rule).
+//
+// Multinomial, C >= 2: s_c = log pi_c + sum_j x_j w_cj with the centred table
+// w_cj = log theta_cj - mean_c log theta_cj (the per-feature shift is the same
+// for every class, so it cancels in the label, the margin and the log
+// posterior, and it keeps |w| small for the error bound).  A block scores 64
+// files x 64 classes per pass as a register-tiled FP32 product over 32-feature
+// chunks staged in shared memory; the epilogue takes the arg-max (lowest
+// index among the maxima), the top-2 margin and the log-sum-exp.
+//
+// Gaussian: s_c = k_c - 1/2 sum_j (x_j - mu_cj)^2 / var_cj with
+// k_c = log pi_c - 1/2 sum_j log(2 pi var_cj) from the FP64 fit.
+//
+// Both mark rows for the FP64 recheck when a rigorous bound on the FP32
+// rounding error cannot guarantee the decision (or the log posteriors).
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace nbg {
+
+constexpr int GBM = 64;   // rows per tile
+constexpr int GBK = 32;   // features per chunk
+constexpr int GCB = 64;   // classes per pass
+
+struct GArgs {
+  const char* X;
+  int64_t ld;        // elements
+  int64_t n;
+  int F, F_pad, C, dtype, aligned;
+  const int64_t* ovf_ptr;
+  const uint16_t* ovf_col;
+  const uint16_t* ovf_add;
+  const int8_t* row_exp;
+  const float* w;      // C x F_pad
+  const float* bias;   // C
+  const float* wmax;
+  const double* log_pi;
+  uint8_t* label;
+  float* margin;
+  float* logpost;
+  int want_lp, recheck;
+  int* status;
+};
+
+// element j of a row as float (scalar path, any alignment)
+__device__ __forceinline__ float gload1(int dt, const char* rp, int j) {
+  switch (dt) {
+    case NB_F32: return reinterpret_cast<const float*>(rp)[j];
+    case NB_U16: return (float)reinterpret_cast<const uint16_t*>(rp)[j];
+    case NB_U8: return (float)reinterpret_cast<const uint8_t*>(rp)[j];
+    case NB_BF16: return __uint_as_float((uint32_t)reinterpret_cast<const uint16_t*>(rp)[j] << 16);
+    default: return e4m3x2_to_f32((uint16_t)reinterpret_cast<const uint8_t*>(rp)[j]).x;
+  }
+}
+
+__device__ __forceinline__ void decode16(int dt, const uint4& x, float* v, int& cnt) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+  switch (dt) {
+    case NB_F32:
+      cnt = 4;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(w[k]);
+      break;
+    case NB_U16:
+      cnt = 8;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[2 * k] = u_field_to_f32(w[k], kSelU16Lo);
+        v[2 * k + 1] = u_field_to_f32(w[k], kSelU16Hi);
+      }
+      break;
+    case NB_BF16:
+      cnt = 8;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+      }
+      break;
+    case NB_U8:
+      cnt = 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v[4 * k + b] = u_field_to_f32(w[k], sel_u8(b));
+      break;
+    default:
+      cnt = 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 lo = e4m3x2_to_f32((uint16_t)(w[k] & 0xFFFFu));
+        const float2 hi = e4m3x2_to_f32((uint16_t)(w[k] >> 16));
+        v[4 * k] = lo.x;
+        v[4 * k + 1] = lo.y;
+        v[4 * k + 2] = hi.x;
+        v[4 * k + 3] = hi.y;
+      }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_score_gen(const GArgs a) {
+  extern __shared__ __align__(16) float gsm[];
+  float* Xs = gsm;                         // [GBK][GBM + 4]
+  float* Ws = Xs + GBK * (GBM + 4);        // [GBK][GCB + 4]
+  float* Ss = Ws + GBK * (GCB + 4);        // [GBM][C_pad]
+  const int C_pad = ((a.C + 3) / 4) * 4;
+  float* Ts = Ss + GBM * C_pad;            // [GBM]
+  float* Tslot = Ts + GBM;                 // [GBM * 8] per-slot |x| sums
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int es = a.dtype == NB_F32 ? 4 : ((a.dtype == NB_U16 || a.dtype == NB_BF16) ? 2 : 1);
+  const int epv = 16 / es;
+  const int vpr = GBK / epv;               // vectors per row per chunk (2, 4 or 8)
+  const int64_t ntile = (a.n + GBM - 1) / GBM;
+  const float wmax = *a.wmax;
+  float bmax = 0.f;
+  for (int c = 0; c < a.C; ++c) bmax = fmaxf(bmax, fabsf(a.bias[c]));
+  const int nchunk = (a.F + GBK - 1) / GBK;
+
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t r0 = tile * GBM;
+    float tpart[2] = {0.f, 0.f};   // |x| sums of the (row, vector) slots this thread loads
+    for (int cb = 0; cb < a.C; cb += GCB) {
+      float run[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) run[i][j] = 0.f;
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int k0 = ch * GBK;
+        // X tile -> Xs[k][row] (FP32)
+        for (int s = 0, slot = tid; slot < GBM * vpr; ++s, slot += 256) {
+          const int row = slot / vpr, vv = slot % vpr;
+          const int64_t gr = r0 + row;
+          float v[16];
+          int cnt = epv;
+          const int kb = k0 + vv * epv;
+          if (gr < a.n) {
+            const char* rp = a.X + gr * a.ld * es;
+            if (a.aligned && kb + epv <= a.F) {
+              decode16(a.dtype, ld_stream16(rp + (int64_t)kb * es), v, cnt);
+            } else {
+              for (int e = 0; e < epv; ++e) v[e] = kb + e < a.F ? gload1(a.dtype, rp, kb + e) : 0.f;
+            }
+            if (a.dtype == NB_FP8E4M3 && a.row_exp) {
+              const float sc = exp2f((float)a.row_exp[gr]);
+              for (int e = 0; e < epv; ++e) v[e] *= sc;
+            }
+          } else {
+            for (int e = 0; e < epv; ++e) v[e] = 0.f;
+          }
+          float tsum = 0.f;
+          for (int e = 0; e < epv; ++e) {
+            Xs[(vv * epv + e) * (GBM + 4) + row] = v[e];
+            tsum += fabsf(v[e]);
+          }
+          if (cb == 0) tpart[s] += tsum;
+        }
+        // W tile -> Ws[k][c]
+        for (int slot = tid; slot < GCB * (GBK / 4); slot += 256) {
+          const int c = slot / (GBK / 4), kq = slot % (GBK / 4);
+          float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (cb + c < a.C)
+            wv = *reinterpret_cast<const float4*>(a.w + (int64_t)(cb + c) * a.F_pad + k0 + kq * 4);
+          Ws[(kq * 4 + 0) * (GCB + 4) + c] = wv.x;
+          Ws[(kq * 4 + 1) * (GCB + 4) + c] = wv.y;
+          Ws[(kq * 4 + 2) * (GCB + 4) + c] = wv.z;
+          Ws[(kq * 4 + 3) * (GCB + 4) + c] = wv.w;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < GBK; ++k) {
+          const float4 ra = *reinterpret_cast<const float4*>(&Xs[k * (GBM + 4) + ty * 4]);
+          const float4 rb = *reinterpret_cast<const float4*>(&Ws[k * (GCB + 4) + tx * 4]);
+          const float A[4] = {ra.x, ra.y, ra.z, ra.w};
+          const float B[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(A[i], B[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) run[i][j] += acc[i][j];
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = cb + tx * 4 + j;
+          if (c < a.C) Ss[(ty * 4 + i) * C_pad + c] = run[i][j];
+        }
+    }
+    // row |x| totals, summed over the row's slots in a fixed order
+    for (int s = 0, slot = tid; slot < GBM * vpr; ++s, slot += 256) Tslot[slot] = tpart[s];
+    __syncthreads();
+    if (tid < GBM) {
+      float t = 0.f;
+      for (int vv = 0; vv < vpr; ++vv) t += Tslot[tid * vpr + vv];
+      Ts[tid] = t;
+    }
+    __syncthreads();
+    // overflow entries (u8 storage): one thread per (row, class), entries in order
+    if (a.dtype == NB_U8 && a.ovf_ptr) {
+      for (int q = tid; q < GBM * a.C; q += 256) {
+        const int row = q / a.C, c = q % a.C;
+        const int64_t gr = r0 + row;
+        if (gr >= a.n) continue;
+        float s = Ss[row * C_pad + c];
+        float t = 0.f;
+        for (int64_t k = a.ovf_ptr[gr]; k < a.ovf_ptr[gr + 1]; ++k) {
+          const int j = a.ovf_col[k];
+          if (j >= a.F) continue;
+          const float add = (float)a.ovf_add[k];
+          s = fmaf(add, a.w[(int64_t)c * a.F_pad + j], s);
+          t += add;
+        }
+        Ss[row * C_pad + c] = s;
+        if (c == 0) Tslot[row] = t;
+      }
+      __syncthreads();
+      if (tid < GBM) Ts[tid] += Tslot[tid];
+      __syncthreads();
+    }
+    // epilogue: a warp per row
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int row = warp; row < GBM; row += 8) {
+      const int64_t gr = r0 + row;
+      if (gr >= a.n) continue;
+      float best = -INFINITY;
+      int bi = 0x7FFFFFFF;
+      for (int c = lane; c < a.C; c += 32) {
+        const float s = Ss[row * C_pad + c] + a.bias[c];
+        if (s > best) { best = s; bi = c; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      float second = -INFINITY, se = 0.f;
+      for (int c = lane; c < a.C; c += 32) {
+        const float s = Ss[row * C_pad + c] + a.bias[c];
+        if (c != bi) second = fmaxf(second, s);
+        se += expf(s - best);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        second = fmaxf(second, __shfl_xor_sync(0xFFFFFFFFu, second, off));
+        se += __shfl_xor_sync(0xFFFFFFFFu, se, off);
+      }
+      const float lse = best + logf(se);
+      const float margin = best - second;
+      const int64_t novf = (a.dtype == NB_U8 && a.ovf_ptr) ? a.ovf_ptr[gr + 1] - a.ovf_ptr[gr] : 0;
+      const float k = (float)(GBK + nchunk + 3 + novf);
+      const float gam = k * 5.9604645e-8f / (1.f - k * 5.9604645e-8f);
+      const float tau = 2.f * (gam * (Ts[row] * wmax + bmax) * 1.01f + 1e-12f * (Ts[row] * wmax + bmax)) + 1e-30f;
+      bool flag = false;
+      if (a.recheck != NB_RECHECK_OFF) {
+        flag = !(margin > tau);
+        if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
+      }
+      if (lane == 0) {
+        a.label[gr] = flag ? kLabelRecheck : (uint8_t)bi;
+        a.margin[gr] = margin;
+      }
+      if (a.want_lp)
+        for (int c = lane; c < a.C; c += 32)
+          a.logpost[gr * a.C + c] = Ss[row * C_pad + c] + a.bias[c] - lse;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian scorer: a warp per row, classes one after another
+// ---------------------------------------------------------------------------
+struct GGArgs {
+  const float* X;
+  int64_t ld, n;
+  int F, F_pad, C;
+  const float* mu;
+  const float* ivar;
+  const float* kc;
+  uint8_t* label;
+  float* margin;
+  float* logpost;
+  int want_lp, recheck;
+};
+
+__global__ void __launch_bounds__(256) k_score_gauss(const GGArgs a) {
+  __shared__ float ssh[8][32], tsh[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const int kdepth = (a.F + 31) / 32 + 5 + 8;
+  const float gam = kdepth * 5.9604645e-8f / (1.f - kdepth * 5.9604645e-8f);
+  for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < a.n; r += nwarps) {
+    const float* xr = a.X + r * a.ld;
+    for (int c = 0; c < a.C; ++c) {
+      const float* mu = a.mu + (int64_t)c * a.F_pad;
+      const float* iv = a.ivar + (int64_t)c * a.F_pad;
+      float q = 0.f, B = 0.f;
+      for (int j = lane; j < a.F; j += 32) {
+        const float x = __ldg(xr + j), m = mu[j], v = iv[j];
+        const float dx = x - m;
+        q = fmaf(dx * dx, v, q);
+        const float ab = fabsf(x) + fabsf(m);
+        B = fmaf(ab * ab, v, B);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
+        B += __shfl_xor_sync(0xFFFFFFFFu, B, off);
+      }
+      if (lane == 0) {
+        ssh[warp][c] = a.kc[c] - 0.5f * q;
+        tsh[warp][c] = 0.5f * gam * B * 1.01f + 3e-7f * fabsf(a.kc[c]) + 1e-12f * (B + fabsf(a.kc[c]));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const float* s = ssh[warp];
+      int bi = 0;
+      for (int c = 1; c < a.C; ++c)
+        if (s[c] > s[bi]) bi = c;
+      float second = -INFINITY;
+      for (int c = 0; c < a.C; ++c)
+        if (c != bi && s[c] > second) second = s[c];
+      float tmax = 0.f;
+      for (int c = 0; c < a.C; ++c) tmax = fmaxf(tmax, tsh[warp][c]);
+      const float margin = s[bi] - second;
+      const float tau = 2.f * tmax + 1e-30f;
+      bool flag = false;
+      if (a.recheck != NB_RECHECK_OFF) {
+        flag = !(margin > tau);
+        if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
+      }
+      a.label[r] = flag ? kLabelRecheck : (uint8_t)bi;
+      a.margin[r] = margin;
+      if (a.want_lp) {
+        float se = 0.f;
+        for (int c = 0; c < a.C; ++c) se += expf(s[c] - s[bi]);
+        const float lse = s[bi] + logf(se);
+        for (int c = 0; c < a.C; ++c) a.logpost[r * a.C + c] = s[c] - lse;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt, int64_t n,
+                               int64_t ld, const nb_aux* aux, const ScoreOut& o, cudaStream_t st) {
+  if (n == 0) return NB_OK;
+  if (m->kind == NB_GAUSSIAN) {
+    if (dt != NB_F32) {
+      set_error("Gaussian models score F32 features");
+      return NB_EINVAL;
+    }
+    GGArgs a{};
+    a.X = static_cast<const float*>(X);
+    a.ld = ld;
+    a.n = n;
+    a.F = m->F;
+    a.F_pad = m->F_pad;
+    a.C = m->C;
+    a.mu = m->d.g_mu;
+    a.ivar = m->d.g_ivar;
+    a.kc = m->d.g_const;
+    a.label = o.label;
+    a.margin = o.margin;
+    a.logpost = o.logpost;
+    a.want_lp = o.want_lp;
+    a.recheck = o.recheck;
+    const int64_t blocks = (n + 7) / 8;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    count_launch();
+    k_score_gauss<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(a);
+    NB_TRY_CUDA(cudaGetLastError(), "k_score_gauss launch");
+    return NB_OK;
+  }
+  const int es = elem_size(dt);
+  GArgs a{};
+  a.X = static_cast<const char*>(X);
+  a.ld = ld;
+  a.n = n;
+  a.F = m->F;
+  a.F_pad = m->F_pad;
+  a.C = m->C;
+  a.dtype = dt;
+  a.aligned = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ld * es) % 16 == 0);
+  a.ovf_ptr = aux ? aux->ovf_ptr : nullptr;
+  a.ovf_col = aux ? aux->ovf_col : nullptr;
+  a.ovf_add = aux ? aux->ovf_add : nullptr;
+  a.row_exp = aux ? aux->row_exp : nullptr;
+  a.w = m->d.w;
+  a.bias = m->d.bias;
+  a.wmax = m->d.wmax;
+  a.log_pi = m->d.log_pi;
+  a.label = o.label;
+  a.margin = o.margin;
+  a.logpost = o.logpost;
+  a.want_lp = o.want_lp;
+  a.recheck = o.recheck;
+  a.status = m->d.status;
+  const int C_pad = ((m->C + 3) / 4) * 4;
+  const int smem =
+      (int)sizeof(float) * (GBK * (GBM + 4) + GBK * (GCB + 4) + GBM * C_pad + GBM + GBM * 8);
+  static int configured = 0;
+  if (smem > 48 * 1024 && configured < smem) {
+    NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem > 96 * 1024 ? smem : 96 * 1024),
+                "cudaFuncSetAttribute");
+    configured = smem > 96 * 1024 ? smem : 96 * 1024;
+  }
+  int occ = 0;
+  NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_gen, 256, smem),
+              "occupancy");
+  const int64_t tiles = (n + GBM - 1) / GBM;
+  const int64_t cap = (int64_t)num_sms() * (occ > 0 ? occ : 1);
+  count_launch();
+  k_score_gen<<<(unsigned)(tiles < cap ? tiles : cap), 256, smem, st>>>(a);
+  NB_TRY_CUDA(cudaGetLastError(), "k_score_gen launch");
+  return NB_OK;
+}
+
+}  // namespace nbg

@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64
+oracle on the same seeded inputs, element by element.
+
+Bar (Sec. 4 posterior and decision rule; tolerance from the task's
+specification of the scorer): labels bit-exact, integer fit counts bit-exact,
+log posteriors and margins within 1e-5 * max(1, |reference|), Gaussian
+moments within 1e-12 relative.  Sizes span several tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import formats
+from tests._common import compare, count_matrix, oracle_mn, stored, to_np
+
+pytestmark = pytest.mark.gpu
+
+nb = pytest.importorskip("paper_1905_13746_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    nb.build()
+    nb.lib()
+
+
+def _fit_score(fmt, Xfit, yfit, Xsc, C=2, log_prior=None, recheck=nb.NB_RECHECK_LP):
+    ffit, vfit = stored(Xfit, fmt)
+    fsc, vsc = stored(Xsc, fmt)
+    y = torch.from_numpy(yfit).cuda()
+    model = nb.fit(ffit, y, C, log_prior=log_prior)
+    res = to_np(nb.score(model, fsc, recheck=recheck))
+    torch.cuda.synchronize()
+    return model, res, vfit, vsc
+
+
+# ----------------------------------------------------------------------------
+# fit: exact counts, FP64 tables
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fmt", ["u16", "u8ovf", "u8", "f32", "bf16", "fp8"])
+@pytest.mark.parametrize("F", [1, 37, 1024])
+def test_fit_counts_exact(fmt, F):
+    X, y, _ = count_matrix(100 + F, 3001, F, clip=65535 if fmt != "u8" else 255,
+                           mu=6.0 if fmt == "fp8" else 8.5)
+    f, vals = stored(X, fmt)
+    model = nb.fit(f, torch.from_numpy(y).cuda(), 2)
+    counts, nc = model.counts()
+    ref_counts = np.stack([vals[y == c].sum(axis=0) for c in range(2)]).astype(np.uint64)
+    assert (counts == ref_counts).all()
+    assert nc.tolist() == [int((y == 0).sum()), int((y == 1).sum())]
+    ref = oracle.mn_finalize(ref_counts, nc, len(y))
+    lt, _, lpi = model.params()
+    assert np.allclose(lt, ref["log_theta"], rtol=1e-14, atol=1e-13)
+    assert np.allclose(lpi, ref["log_pi"], rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("C", [3, 17, 64])
+def test_fit_counts_many_classes(C):
+    X, y, _ = count_matrix(7 * C, 4099, 300, C=C, conc=0.1, clip=255)
+    f, vals = stored(X, "u8")
+    model = nb.fit(f, torch.from_numpy(y).cuda(), C)
+    counts, nc = model.counts()
+    ref_counts = np.stack([vals[y == c].sum(axis=0) for c in range(C)]).astype(np.uint64)
+    assert (counts == ref_counts).all()
+    assert (nc == np.bincount(y, minlength=C)).all()
+
+
+def test_fit_given_prior_and_alpha():
+    X, y, _ = count_matrix(5, 2000, 50)
+    f, vals = stored(X, "u16")
+    lp = np.log([0.3, 0.7])
+    model = nb.fit(f, torch.from_numpy(y).cuda(), 2, alpha=0.5, log_prior=lp)
+    ref = oracle.mn_fit(vals, y, 2, alpha=0.5, log_prior=lp)
+    lt, _, lpi = model.params()
+    assert np.allclose(lt, ref["log_theta"], rtol=1e-14, atol=1e-13)
+    assert (lpi == lp).all()
+
+
+# ----------------------------------------------------------------------------
+# two-class scoring, every storage format
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fmt", ["u8ovf", "u8", "u16", "f32", "bf16", "fp8"])
+@pytest.mark.parametrize("F", [3, 64, 1000, 1024])
+def test_score_two_class(fmt, F):
+    n_fit, n_sc = 3001, 5003
+    clip = 255 if fmt == "u8" else 65535
+    X, y, _ = count_matrix(200 + F, n_fit + n_sc, F, clip=clip,
+                           mu=6.0 if fmt == "fp8" else 8.5)
+    model, res, vfit, vsc = _fit_score(fmt, X[:n_fit], y[:n_fit], X[n_fit:])
+    _, ref = oracle_mn(vfit, y[:n_fit], 2, vsc)
+    compare(res, ref)
+
+
+def test_score_two_class_low_totals_near_ties():
+    # small totals and overlapping profiles: many rows near the boundary,
+    # which exercises the marked-row FP64 recheck
+    F = 256
+    p = synth.dirichlet_profiles(3, 2, F, 5.0)
+    X, y, _ = count_matrix(9, 20000, F, mu=2.0, sigma=1.0, p=p)
+    model, res, vfit, vsc = _fit_score("u8ovf", X[:5000], y[:5000], X[5000:])
+    _, ref = oracle_mn(vfit, y[:5000], 2, vsc)
+    compare(res, ref)
+    assert res["n_rechecked"] > 0
+
+
+def test_all_zero_rows_tie_to_benign():
+    X, y, _ = count_matrix(11, 2000, 64)
+    f, _ = stored(X, "u16")
+    model = nb.fit(f, torch.from_numpy(y).cuda(), 2, log_prior=np.log([0.5, 0.5]))
+    for fmt in ["u8", "u16", "f32", "bf16", "fp8"]:
+        z, _ = stored(np.zeros((40, 64), np.int64), fmt)
+        r = to_np(nb.score(model, z))
+        assert (r["label"] == 0).all() and (r["margin"] == 0).all()
+        assert np.allclose(r["lp"], np.log(0.5), atol=1e-7)
+
+
+def test_recheck_off_and_label_modes():
+    X, y, _ = count_matrix(13, 8000, 128)
+    f, vals = stored(X, "u8ovf")
+    model = nb.fit(stored(X[:3000], "u8ovf")[0], torch.from_numpy(y[:3000]).cuda(), 2)
+    _, ref = oracle_mn(vals[:3000], y[:3000], 2, vals[3000:])
+    fsc, _ = stored(X[3000:], "u8ovf")
+    r_label = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LABEL))
+    compare(r_label, ref, check_lp=False)
+    r_off = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_OFF))
+    assert r_off["n_rechecked"] == 0
+    assert (r_off["label"] != 255).all()
+
+
+# ----------------------------------------------------------------------------
+# many classes (CUDA-core general scorer)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("C,F,fmt", [(3, 100, "u16"), (16, 512, "u8"), (64, 256, "u8"),
+                                     (5, 77, "f32"), (17, 1000, "bf16"), (7, 64, "fp8")])
+def test_score_many_class_labels(C, F, fmt):
+    X, y, _ = count_matrix(300 + C, 6000, F, C=C, conc=0.1, clip=255 if fmt == "u8" else 65535,
+                           mu=6.0 if fmt == "fp8" else 8.5)
+    model, res, vfit, vsc = _fit_score(fmt, X[:2500], y[:2500], X[2500:], C=C,
+                                       recheck=nb.NB_RECHECK_LABEL)
+    _, ref = oracle_mn(vfit, y[:2500], C, vsc)
+    stats = compare(res, ref, check_lp=False)
+    assert stats["lp_err"] < 1e-3
+
+
+@pytest.mark.parametrize("C", [3, 16])
+def test_score_many_class_lp_mode(C):
+    X, y, _ = count_matrix(400 + C, 4000, 200, C=C, conc=0.1, clip=255)
+    model, res, vfit, vsc = _fit_score("u8", X[:2000], y[:2000], X[2000:], C=C)
+    _, ref = oracle_mn(vfit, y[:2000], C, vsc)
+    compare(res, ref)
+
+
+# ----------------------------------------------------------------------------
+# Gaussian (real-valued features), the 2,000 / 10,000 x 64 workload in full
+# ----------------------------------------------------------------------------
+def test_gaussian_workload_full():
+    w = synth.gaussian_workload(synth.seed_for(1))
+    Xf = torch.from_numpy(w["X_fit"]).cuda()
+    model = nb.fit(Xf, torch.from_numpy(w["y_fit"]).cuda(), 2, kind=nb.NB_GAUSSIAN,
+                   log_prior=w["log_prior"])
+    ref_m = oracle.gauss_fit(w["X_fit"], w["y_fit"], 2, log_prior=w["log_prior"])
+    mu, var, lpi = model.params()
+    assert np.allclose(mu, ref_m["mu"], rtol=1e-12, atol=1e-12)
+    assert np.allclose(var, ref_m["var"], rtol=1e-12, atol=0)
+    res = to_np(nb.score(model, torch.from_numpy(w["X_score"]).cuda()))
+    ref = oracle.score(w["X_score"], ref_m)
+    compare(res, ref)
+
+
+@pytest.mark.parametrize("C,F", [(3, 5), (8, 200)])
+def test_gaussian_many_class(C, F):
+    rng = np.random.default_rng(C * 100 + F)
+    mu = rng.uniform(0, 10, size=(C, F))
+    sd = rng.uniform(0.5, 3, size=(C, F))
+    y = np.concatenate([np.arange(C), rng.integers(0, C, 3000)]).astype(np.int32)
+    X = rng.normal(mu[y], sd[y]).astype(np.float32)
+    model = nb.fit(torch.from_numpy(X[:1500]).cuda(), torch.from_numpy(y[:1500]).cuda(), C,
+                   kind=nb.NB_GAUSSIAN)
+    ref_m = oracle.gauss_fit(X[:1500], y[:1500], C)
+    res = to_np(nb.score(model, torch.from_numpy(X[1500:]).cuda()))
+    compare(res, oracle.score(X[1500:], ref_m))
+
+
+# ----------------------------------------------------------------------------
+# packing kernels against the format definitions
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("F", [1, 33, 1024])
+def test_pack_u8_overflow_exact(F):
+    X, _, _ = count_matrix(500 + F, 3000, F)
+    t = torch.from_numpy(X.view(np.int16)).cuda().view(torch.uint16)
+    f = nb.pack_u8(t)
+    plane, ptr, col, add = formats.pack_u8_overflow(X)
+    assert (f.data.cpu().numpy() == plane).all()
+    assert (f.ovf_ptr.cpu().numpy() == ptr).all()
+    k = ptr[-1]
+    assert (f.ovf_col.cpu().numpy().view(np.uint16)[:k] == col).all()
+    assert (f.ovf_add.cpu().numpy().view(np.uint16)[:k] == add).all()
+
+
+def test_pack_bf16_and_fp8_exact():
+    X, _, _ = count_matrix(600, 2000, 99, mu=7.0)
+    t = torch.from_numpy(X.view(np.int16)).cuda().view(torch.uint16)
+    fb = nb.pack_bf16(t)
+    got = fb.data.contiguous().view(torch.int16).cpu().numpy().view(np.uint16)
+    assert (got == formats.bf16_bits(X)).all()
+    f8 = nb.pack_fp8(t)
+    codes, e = formats.pack_e4m3(X)
+    assert (f8.row_exp.cpu().numpy() == e).all()
+    assert (f8.data.cpu().numpy() == codes).all()
+    tf = torch.from_numpy(X.astype(np.float32)).cuda()
+    assert (nb.pack_fp8(tf).data.cpu().numpy() == codes).all()
+
+
+# ----------------------------------------------------------------------------
+# edge cases
+# ----------------------------------------------------------------------------
+def test_empty_and_single_row():
+    X, y, _ = count_matrix(700, 1000, 40)
+    f, vals = stored(X, "u8ovf")
+    model = nb.fit(f, torch.from_numpy(y).cuda(), 2)
+    e, _ = stored(X[:0], "u8")
+    r = nb.score(model, e)
+    assert r["label"].numel() == 0
+    one, v1 = stored(X[:1], "u8ovf")
+    r1 = to_np(nb.score(model, one))
+    _, ref = oracle_mn(vals, y, 2, v1)
+    compare(r1, ref)
+
+
+def test_unaligned_leading_dimension_takes_general_path():
+    X, y, _ = count_matrix(710, 3000, 50, clip=255)
+    base = torch.zeros((3000, 53), dtype=torch.uint8)
+    base[:, :50] = torch.from_numpy(X.astype(np.uint8))
+    Xd = base.cuda()[:, :50]              # ld = 53 bytes: not 16-byte aligned rows
+    f = nb.Features(Xd, nb.NB_U8)
+    model = nb.fit(f, torch.from_numpy(y).cuda(), 2)
+    r = to_np(nb.score(model, f))
+    _, ref = oracle_mn(X.astype(np.float64), y, 2, X.astype(np.float64))
+    compare(r, ref)
+
+
+def test_invalid_inputs_rejected():
+    X, y, _ = count_matrix(720, 500, 16)
+    f, _ = stored(X, "u16")
+    bad_y = torch.from_numpy(np.where(np.arange(500) == 7, 2, y).astype(np.int32)).cuda()
+    with pytest.raises(nb.NbError) as ei:
+        nb.fit(f, bad_y, 2)
+    assert ei.value.status == nb.NB_EINVAL
+    with pytest.raises(nb.NbError):
+        nb.fit(f, torch.from_numpy(y).cuda(), 1)
+    with pytest.raises(nb.NbError):
+        nb.fit(f, torch.from_numpy(y).cuda(), 2, alpha=0.0)
+    neg = torch.from_numpy(-np.ones((10, 16), np.float32)).cuda()
+    with pytest.raises(nb.NbError):
+        nb.fit(neg, torch.from_numpy(y[:10]).cuda(), 2, log_prior=[0.0, 0.0])
+    frac = torch.from_numpy(np.full((10, 16), 0.5, np.float32)).cuda()
+    with pytest.raises(nb.NbError):
+        nb.fit(frac, torch.from_numpy(y[:10]).cuda(), 2, log_prior=[0.0, 0.0])
+
+
+def test_group_alone_equals_group_in_batch():
+    X, y, _ = count_matrix(730, 9000, 300)
+    f, _ = stored(X[:3000], "u8ovf")
+    model = nb.fit(f, torch.from_numpy(y[:3000]).cuda(), 2)
+    fall, _ = stored(X[3000:], "u8ovf")
+    r_all = to_np(nb.score(model, fall))
+    for a, b in [(0, 1), (17, 530), (1000, 1001), (2999, 6000)]:
+        fs, _ = stored(X[3000 + a:3000 + b], "u8ovf")
+        rs = to_np(nb.score(model, fs))
+        assert (rs["label"] == r_all["label"][a:b]).all()
+        assert (rs["margin"].view(np.uint32) == r_all["margin"][a:b].view(np.uint32)).all()
+        assert (rs["lp"].view(np.uint32) == r_all["lp"][a:b].view(np.uint32)).all()
