@@ -294,6 +294,7 @@ def main():
     ap.add_argument("--ref-fit-rows", type=int, default=20_000)
     ap.add_argument("--ref-score-rows", type=int, default=40_000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -319,6 +320,8 @@ def main():
     with torch.cuda.stream(stream):
         model = nb.fit(W["low_tr"], W["y_tr"], C, stream=stream)   # validated fit
     stream.synchronize()
+    tuned, tuned_ms = ((0, 0, 0, 0), 0.0) if args.no_autotune else \
+        model.autotune(W["low_all"], stream=stream)
 
     hbm_peak, peak_kind = _peaks()
     # ---- low-precision (u8 + overflow) step, the headline -----------------
@@ -342,6 +345,9 @@ def main():
     f32_tr = nb.Features(W["X16_tr"].to(torch.int32).to(torch.float32), nb.NB_F32)
     with torch.cuda.stream(stream):
         m32 = nb.fit(f32_tr, W["y_tr"], C, stream=stream)
+    stream.synchronize()
+    if not args.no_autotune:
+        m32.autotune(f32_all, stream=stream)
     p_total, p_fit, p_sc, _ = time_steps(m32, f32_tr, W["y_tr"], f32_all, out, args.steps,
                                          args.warmup, stream)
     p_rechecked = int(out["n_rechecked"].item())
@@ -420,6 +426,8 @@ def main():
                 "gbs": fit_bytes / (fit_avg * 1e-3) / 1e9},
         "score_files_per_s": N / (sc_avg * 1e-3),
         "n_rechecked": n_rechecked,
+        "tile_config": {"variant": tuned[0], "stages": tuned[1], "rows_per_stage": tuned[2],
+                        "rows_per_warp": tuned[3], "autotune_ms": tuned_ms},
         "plain_fp32": {"ms_per_step": p_total / args.steps, "files_per_s": N / (p_total / args.steps * 1e-3),
                        "score_ms": statistics.mean(p_sc), "fit_ms": statistics.mean(p_fit),
                        "score_gbs": plain_ach, "score_frac": plain_ach / hbm_peak,

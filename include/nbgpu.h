@@ -119,6 +119,31 @@ typedef struct {
 typedef struct nb_model nb_model;
 typedef struct nb_server nb_server;
 
+/* Kernel configuration of a model's two-class scorer.
+ *   variant  NB_VARIANT_AUTO: TMA-pipelined kernel when the row fits a stage,
+ *            else the register-streaming kernel;
+ *            NB_VARIANT_PIPELINED / NB_VARIANT_REGISTER: force one.
+ *   stages, rows_per_stage: pipeline depth and rows per shared-memory stage
+ *            (0 = defaults: stages of 16-48 KB filling ~100-180 KB per block);
+ *   rows_per_warp: 1 (32 lanes per row) or 2 (16 lanes per row, more table
+ *            registers per lane); 0 = 1.
+ * For u8 storage every configuration gives bit-identical results (exact
+ * integer sums).  For the FP32 paths the two variants share the reduction
+ * order when a row spans >= 64 sixteen-byte vectors; nb_autotune_score keeps
+ * the variant fixed otherwise, so tuning never changes a result. */
+typedef enum {
+  NB_VARIANT_AUTO = 0,
+  NB_VARIANT_PIPELINED = 1,
+  NB_VARIANT_REGISTER = 2
+} nb_variant;
+
+typedef struct {
+  int variant;
+  int stages;
+  int rows_per_stage;
+  int rows_per_warp;
+} nb_tile_config;
+
 /* ---- fit -----------------------------------------------------------------
  * Train one model on n labelled files (Sec. 4, "trained the model").
  *   kind  NB_MULTINOMIAL: X holds counts (U8[+overflow], U16, F32, BF16,
@@ -179,6 +204,22 @@ NB_API nb_status nb_score_group(const nb_model* model, const void* X, nb_dtype d
                          int64_t n, int64_t ld, uint8_t* label, float* margin,
                          float* logpost, const nb_score_opts* opts,
                          void* cuda_stream, int64_t* n_rechecked);
+
+/* ---- tile configuration and autotuning -----------------------------------
+ * nb_set_tile_config / nb_get_tile_config: set or read a model's scorer
+ * configuration (see nb_tile_config).
+ * nb_autotune_score: times the candidate configurations of the model's scorer
+ * on the caller's data (X as for nb_score_group; outputs go to scratch it
+ * allocates and frees), sets the fastest on the model and returns it in *best
+ * (and its time in ms in *best_ms, either may be NULL).  Synchronises the
+ * stream; not for use inside stream capture.  Only two-class multinomial
+ * models have choices; other models return their default. */
+NB_API nb_status nb_set_tile_config(nb_model* model, const nb_tile_config* cfg);
+NB_API nb_status nb_get_tile_config(const nb_model* model, nb_tile_config* cfg);
+NB_API nb_status nb_autotune_score(nb_model* model, const void* X, nb_dtype dtype,
+                                   int64_t n, int64_t ld, const nb_aux* aux,
+                                   void* cuda_stream, nb_tile_config* best,
+                                   float* best_ms);
 
 /* ---- storage packing (supporting; not part of a timed score) ------------
  * U16 counts -> U8 plane + overflow list, in two calls:

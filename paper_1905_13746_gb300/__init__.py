@@ -45,6 +45,14 @@ class NbScoreOpts(ctypes.Structure):
                 ("aux", ctypes.POINTER(NbAux))]
 
 
+class NbTileConfig(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("stages", ctypes.c_int),
+                ("rows_per_stage", ctypes.c_int), ("rows_per_warp", ctypes.c_int)]
+
+
+NB_VARIANT_AUTO, NB_VARIANT_PIPELINED, NB_VARIANT_REGISTER = 0, 1, 2
+
+
 class NbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -67,6 +75,12 @@ _SIGS = [
     ("nb_model_free", None, [_P]),
     ("nb_score_group", ctypes.c_int, [_P, _P, ctypes.c_int, _i64, _i64, _P, _P, _P,
                                       ctypes.POINTER(NbScoreOpts), _P, _P]),
+    ("nb_set_tile_config", ctypes.c_int, [_P, ctypes.POINTER(NbTileConfig)]),
+    ("nb_get_tile_config", ctypes.c_int, [_P, ctypes.POINTER(NbTileConfig)]),
+    ("nb_autotune_score", ctypes.c_int, [_P, _P, ctypes.c_int, _i64, _i64,
+                                         ctypes.POINTER(NbAux), _P,
+                                         ctypes.POINTER(NbTileConfig),
+                                         ctypes.POINTER(ctypes.c_float)]),
     ("nb_pack_u8_count", ctypes.c_int, [_P, _i64, _i32, _i64, _P, ctypes.POINTER(_i64), _P]),
     ("nb_pack_u8_fill", ctypes.c_int, [_P, _i64, _i32, _i64, _P, _i64, _P, _P, _P, _P]),
     ("nb_pack_bf16", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _P, _i64, _P]),
@@ -240,6 +254,28 @@ class Model:
 
     def check(self):
         _check(lib().nb_model_check(self.handle))
+
+    def tile_config(self):
+        c = NbTileConfig()
+        _check(lib().nb_get_tile_config(self.handle, ctypes.byref(c)))
+        return (c.variant, c.stages, c.rows_per_stage, c.rows_per_warp)
+
+    def set_tile_config(self, variant=NB_VARIANT_AUTO, stages=0, rows_per_stage=0,
+                        rows_per_warp=0):
+        c = NbTileConfig(variant, stages, rows_per_stage, rows_per_warp)
+        _check(lib().nb_set_tile_config(self.handle, ctypes.byref(c)))
+
+    def autotune(self, X, stream=None):
+        """Time the scorer's candidate configurations on X; keep the fastest."""
+        Xf = as_features(X)
+        best = NbTileConfig()
+        ms = ctypes.c_float(0)
+        aux = Xf.aux()
+        _check(lib().nb_autotune_score(self.handle, Xf.data.data_ptr(), Xf.dtype_code, Xf.n,
+                                       Xf.ld, ctypes.byref(aux) if aux else None,
+                                       _stream_ptr(stream), ctypes.byref(best),
+                                       ctypes.byref(ms)))
+        return (best.variant, best.stages, best.rows_per_stage, best.rows_per_warp), ms.value
 
 
 def fit(X, y, C, kind=NB_MULTINOMIAL, alpha=1.0, log_prior=None, var_smoothing=1e-9,

@@ -374,10 +374,17 @@ extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype d
     set_error("nb_score_group: unknown dtype %d", (int)dtype);
     return NB_EINVAL;
   }
-  if (n < 0 || ld < m->F) {
+  if (n < 0 || (n > 0 && ld < m->F)) {
     set_error("nb_score_group: need n >= 0 and ld >= F (n=%lld ld=%lld F=%d)", (long long)n,
               (long long)ld, m->F);
     return NB_EINVAL;
+  }
+  if (n == 0) {
+    if (n_rechecked)
+      NB_TRY_CUDA(cudaMemsetAsync(n_rechecked, 0, sizeof(int64_t),
+                                  static_cast<cudaStream_t>(cuda_stream)),
+                  "memset");
+    return NB_OK;
   }
   const int want_lp = opts ? opts->want_logpost : 0;
   const int recheck = opts ? (int)opts->recheck : (int)NB_RECHECK_LP;

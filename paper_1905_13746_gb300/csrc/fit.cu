@@ -234,30 +234,57 @@ __global__ void __launch_bounds__(256) k_counts(const CountArgs a, long long nwo
     int vv[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) vv[k] = slab * 32 * NV + k * 32 + lane;
-    for (long long p = p0; p < p1; ++p) {
-      const int64_t row = a.idx[p];
-      const char* rp = a.X + row * a.ld_bytes;
-      const int8_t e = (DT == NB_FP8E4M3 && a.row_exp) ? a.row_exp[row] : (int8_t)0;
-      uint4 x[NV];
+    // the run's row indices, lane l holding positions p0 + l + 32 i
+    const int cnt = (int)(p1 - p0);   // <= kRunRows
+    int ridx[kRunRows / 32];
 #pragma unroll
-      for (int k = 0; k < NV; ++k)
-        x[k] = vv[k] < a.nvec_row ? ld_stream16(rp + (int64_t)vv[k] * 16) : make_uint4(0, 0, 0, 0);
+    for (int i = 0; i < kRunRows / 32; ++i) {
+      const int q = lane + 32 * i;
+      ridx[i] = q < cnt ? a.idx[p0 + q] : 0;
+    }
+    // zero the padding beyond F in a partial last vector (never counted)
+    uint32_t wmask[NV][4];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        if (vv[k] < a.nvec_row) {
-          // zero the padding beyond F in the last vector (garbage is never counted)
-          const int base = vv[k] * Dec::EPV;
-          if (base + Dec::EPV > a.F) {
-            uint32_t* w = &x[k].x;
-            const int esz = 16 / Dec::EPV;
+    for (int k = 0; k < NV; ++k) {
+      const int base = vv[k] * Dec::EPV;
+      const int esz = 16 / Dec::EPV;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              int valid = (a.F - base) * esz - 4 * q;   // valid bytes in word q
-              valid = valid < 0 ? 0 : (valid > 4 ? 4 : valid);
-              w[q] &= valid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * valid)) - 1u);
-            }
+      for (int q = 0; q < 4; ++q) {
+        int valid = (a.F - base) * esz - 4 * q;   // valid bytes in word q
+        valid = valid < 0 ? 0 : (valid > 4 ? 4 : valid);
+        wmask[k][q] = valid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * valid)) - 1u);
+      }
+    }
+    constexpr int U = 8;   // rows in flight per lane
+    for (int r0 = 0; r0 < cnt; r0 += U) {
+      uint4 x[U][NV];
+      int8_t ex[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u;
+        const int src = r & 31, slot = r >> 5;
+        int row = ridx[0];
+#pragma unroll
+        for (int i = 1; i < kRunRows / 32; ++i) row = slot == i ? ridx[i] : row;
+        row = __shfl_sync(0xFFFFFFFFu, row, src);
+        const char* rp = a.X + (int64_t)row * a.ld_bytes;
+        ex[u] = (DT == NB_FP8E4M3 && a.row_exp && r < cnt) ? a.row_exp[row] : (int8_t)0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+          x[u][k] = (r < cnt && vv[k] < a.nvec_row) ? ld_stream16(rp + (int64_t)vv[k] * 16)
+                                                   : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          if (vv[k] < a.nvec_row && r0 + u < cnt) {
+            x[u][k].x &= wmask[k][0];
+            x[u][k].y &= wmask[k][1];
+            x[u][k].z &= wmask[k][2];
+            x[u][k].w &= wmask[k][3];
+            Dec::add(x[u][k], acc[k], ex[u], a.status);
           }
-          Dec::add(x[k], acc[k], e, a.status);
         }
       }
     }
@@ -524,7 +551,11 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
                                 cudaMemcpyDeviceToDevice, st),
                 "memcpy prior");
   const int sms = num_sms();
-  if (n > 0) {
+  nb_status piped = NB_EUNSUPPORTED;
+  if (C == 2 && m->tile.variant != NB_VARIANT_REGISTER)
+    piped = launch_fit2_pipe(m, X, dt, n, ld, y, aux, st);
+  if (piped != NB_OK && piped != NB_EUNSUPPORTED) return piped;
+  if (n > 0 && piped != NB_OK) {
     const long long g = (n + 255) / 256;
     const unsigned hb = (unsigned)(g < sms * 4 ? g : sms * 4);
     count_launch();
@@ -631,8 +662,6 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
 // ---------------------------------------------------------------------------
 // Gaussian fit
 // ---------------------------------------------------------------------------
-constexpr int kGChunkRows = 256;   // rows per deterministic partial
-constexpr int kGTile = 64;         // features per block tile
 
 // pass 0: sums of x; pass 1: sums of (x - mean)^2.  Slot C = all rows.
 __global__ void __launch_bounds__(256) k_gauss_partial(const float* X, int64_t ld, int64_t n,

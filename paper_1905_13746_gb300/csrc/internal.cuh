@@ -94,6 +94,7 @@ struct nb_model {
   double alpha;
   double var_smoothing;
   int device;
+  nb_tile_config tile;   // scorer kernel configuration (autotuned or set)
   cudaStream_t stream;   // stream of the fit
   void* mem;
   size_t mem_bytes;
@@ -123,6 +124,11 @@ struct ScoreOut {
 nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt,
                         int64_t n, int64_t ld, const nb_aux* aux,
                         const ScoreOut& o, cudaStream_t st);
+nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, int64_t ld,
+                           const int32_t* y, const nb_aux* aux, cudaStream_t st);
+struct S2Args;
+nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_per_stage,
+                             int rows_per_warp, int stage_entries, cudaStream_t st);
 nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt,
                                int64_t n, int64_t ld, const nb_aux* aux,
                                const ScoreOut& o, cudaStream_t st);
@@ -133,5 +139,24 @@ nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt,
 int num_sms();
 // process-wide count of kernels this library has launched
 void count_launch();
+
+// Gaussian fit: rows per deterministic partial sum, features per block tile
+constexpr int kGChunkRows = 256;
+constexpr int kGTile = 64;
+
+// Gaussian fit kernels (fit.cu)
+__global__ void k_label_hist(const int32_t* y, int64_t n, int C, unsigned long long* nc,
+                             int* status);
+__global__ void k_gauss_partial(const float* X, int64_t ld, int64_t n, int F, int C,
+                                const int32_t* y, int pass, const double* mu_c,
+                                const double* mu_all, double* partial, int* status);
+__global__ void k_gauss_reduce(const double* partial, int nchunk, int F, int C,
+                               const unsigned long long* nc, int64_t n, int pass, double* mu_c,
+                               double* mu_all, double* m2_c, double* m2_all);
+__global__ void k_gauss_finalize(const double* m2_all, int F, int F_pad, int C,
+                                 double var_smoothing, const unsigned long long* nc, int64_t n,
+                                 int prior_given, const double* mu, double* var, double* log_pi,
+                                 double* gconst, float* g_mu, float* g_ivar, float* g_const,
+                                 int* status);
 
 }  // namespace nbg

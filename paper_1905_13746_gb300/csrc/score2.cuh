@@ -1,0 +1,127 @@
+// Pieces shared by the two-class scorers (register-streaming and
+// TMA-pipelined): launch arguments, the epilogue that turns the log-odds d
+// into label / margin / log posteriors and marks rows for the FP64 recheck,
+// and the exact decoders of each storage type into FP32.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace nbg {
+
+struct S2Args {
+  const char* X;
+  int64_t ld_bytes;
+  int64_t n;
+  int F;
+  int nvec_row;   // 16-byte vectors that hold a row's F features
+  int nvec_tab;   // vectors of the padded table (F_pad elements)
+  const void* table;
+  uint32_t table_bytes;
+  const C2Header* hdr;
+  const int32_t* delta_q;   // plain fixed-point table (overflow entries)
+  const float* delta;       // plain FP32 table (overflow entries)
+  const int64_t* ovf_ptr;
+  const uint16_t* ovf_col;
+  const uint16_t* ovf_add;
+  const int8_t* row_exp;
+  uint8_t* label;
+  float* margin;
+  float* logpost;
+  int want_lp;
+  int recheck;
+  int k_base;     // FP32 path: rounding depth of a row without overflow entries
+  int* status;
+};
+
+__device__ __forceinline__ float softplusf(float z) {
+  return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
+}
+
+__device__ __forceinline__ void c2_epilogue(const S2Args& a, int64_t row, float d, float tau) {
+  bool flag = false;
+  const float ad = fabsf(d);
+  if (a.recheck != NB_RECHECK_OFF) {
+    flag = !(ad > tau);  // also true for NaN
+    if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, ad)) flag = true;
+  }
+  a.label[row] = flag ? kLabelRecheck : (d > 0.f ? 1 : 0);
+  a.margin[row] = ad;
+  if (a.want_lp) {
+    a.logpost[2 * row] = -softplusf(d);
+    a.logpost[2 * row + 1] = -softplusf(-d);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 accumulation from any storage type
+// ---------------------------------------------------------------------------
+template <int DT>
+struct Decode;
+
+template <>
+struct Decode<NB_F32> {
+  static constexpr int EPV = 4;
+  __device__ __forceinline__ static void run(const uint4& x, float* v) {
+    v[0] = __uint_as_float(x.x);
+    v[1] = __uint_as_float(x.y);
+    v[2] = __uint_as_float(x.z);
+    v[3] = __uint_as_float(x.w);
+  }
+};
+template <>
+struct Decode<NB_U16> {
+  static constexpr int EPV = 8;
+  __device__ __forceinline__ static void run(const uint4& x, float* v) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = u_field_to_f32(w[k], kSelU16Lo);
+      v[2 * k + 1] = u_field_to_f32(w[k], kSelU16Hi);
+    }
+  }
+};
+template <>
+struct Decode<NB_BF16> {
+  static constexpr int EPV = 8;
+  __device__ __forceinline__ static void run(const uint4& x, float* v) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = __uint_as_float(w[k] << 16);
+      v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+    }
+  }
+};
+template <>
+struct Decode<NB_U8> {
+  static constexpr int EPV = 16;
+  __device__ __forceinline__ static void run(const uint4& x, float* v) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) v[4 * k + b] = u_field_to_f32(w[k], sel_u8(b));
+    }
+  }
+};
+template <>
+struct Decode<NB_FP8E4M3> {
+  static constexpr int EPV = 16;
+  __device__ __forceinline__ static void run(const uint4& x, float* v) {
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 lo = e4m3x2_to_f32((uint16_t)(w[k] & 0xFFFFu));
+      const float2 hi = e4m3x2_to_f32((uint16_t)(w[k] >> 16));
+      v[4 * k] = lo.x;
+      v[4 * k + 1] = lo.y;
+      v[4 * k + 2] = hi.x;
+      v[4 * k + 3] = hi.y;
+    }
+  }
+};
+
+}  // namespace nbg

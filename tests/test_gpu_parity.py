@@ -273,3 +273,38 @@ def test_group_alone_equals_group_in_batch():
         assert (rs["label"] == r_all["label"][a:b]).all()
         assert (rs["margin"].view(np.uint32) == r_all["margin"][a:b].view(np.uint32)).all()
         assert (rs["lp"].view(np.uint32) == r_all["lp"][a:b].view(np.uint32)).all()
+
+
+# ----------------------------------------------------------------------------
+# scorer variants: pipelined (TMA stages) vs register-streaming, autotuner
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("fmt,F", [("u8ovf", 1024), ("u8ovf", 2048), ("u8", 300),
+                                   ("f32", 1024), ("u16", 1000), ("bf16", 512), ("fp8", 777)])
+def test_scorer_variants_agree_and_match_oracle(fmt, F):
+    X, y, _ = count_matrix(800 + F, 9000, F, clip=255 if fmt == "u8" else 65535,
+                           mu=6.0 if fmt == "fp8" else 8.5)
+    ffit, vfit = stored(X[:3000], fmt)
+    fsc, vsc = stored(X[3000:], fmt)
+    model = nb.fit(ffit, torch.from_numpy(y[:3000]).cuda(), 2)
+    _, ref = oracle_mn(vfit, y[:3000], 2, vsc)
+    outs = {}
+    configs = [(nb.NB_VARIANT_REGISTER, 0, 0, 0), (nb.NB_VARIANT_AUTO, 0, 0, 0)]
+    configs += [(nb.NB_VARIANT_PIPELINED, s, r, w) for s, r in [(2, 4), (3, 8), (4, 16), (5, 32)]
+                for w in ((1, 2) if fmt.startswith("u8") else (1,))]
+    for cfg in configs:
+        model.set_tile_config(*cfg)
+        try:
+            outs[cfg] = to_np(nb.score(model, fsc))
+        except nb.NbError as e:
+            assert e.status == nb.NB_EUNSUPPORTED and cfg[0] == nb.NB_VARIANT_PIPELINED
+            continue
+        compare(outs[cfg], ref)
+    base = outs[(nb.NB_VARIANT_AUTO, 0, 0, 0)]
+    for cfg, o in outs.items():
+        if fmt.startswith("u8") or cfg[0] != nb.NB_VARIANT_REGISTER:
+            assert (o["label"] == base["label"]).all(), cfg
+            assert (o["margin"].view(np.uint32) == base["margin"].view(np.uint32)).all(), cfg
+            assert (o["lp"].view(np.uint32) == base["lp"].view(np.uint32)).all(), cfg
+    best, ms = model.autotune(fsc)
+    assert ms > 0
+    compare(to_np(nb.score(model, fsc)), ref)
