@@ -170,6 +170,25 @@ NB_API nb_status nb_refit(nb_model* model, const void* X, nb_dtype dtype, int64_
                    int64_t ld, const int32_t* y, const nb_fit_opts* opts,
                    void* cuda_stream);
 
+/* Allocation-free re-fit of a Gaussian model (this entry point has no
+ * counterpart in the paper; it is a deployment convenience).
+ * Same work and results as nb_refit on a Gaussian model, for callers that may
+ * not allocate device memory when they re-train -- a thread held to a fixed
+ * memory budget, code between a CUDA graph's instantiation and its replays,
+ * an embedded runtime that forbids allocation after start-up.  Its scratch
+ * (per-chunk partial sums) is a fixed 8 MiB device array inside the library,
+ * present on every GPU that loads the library until the process exits:
+ * requests needing more than ceil(n/256) * (C+1) * F + 2F doubles <= 2^20 are
+ * rejected with NB_EINVAL (use nb_refit for those).  The first call made on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  All calls share the array, so calls that may run at
+ * the same time on the GPU (unordered streams) race; order them.  X (F32,
+ * n x ld) and y are device pointers; opts->log_prior (host), var_smoothing
+ * and no_sync act as for nb_refit (alpha and aux are ignored). */
+NB_API nb_status nb_refit_gaussian_noalloc(nb_model* model, const float* X, int64_t n,
+                                           int64_t ld, const int32_t* y,
+                                           const nb_fit_opts* opts, void* cuda_stream);
+
 /* Waits for the model's fit and returns NB_EINVAL if its data were invalid. */
 NB_API nb_status nb_model_check(const nb_model* model);
 

@@ -68,6 +68,8 @@ _SIGS = [
                               ctypes.POINTER(NbFitOpts), _P, ctypes.POINTER(_P)]),
     ("nb_refit", ctypes.c_int, [_P, _P, ctypes.c_int, _i64, _i64, _P,
                                 ctypes.POINTER(NbFitOpts), _P]),
+    ("nb_refit_gaussian_noalloc", ctypes.c_int, [_P, _P, _i64, _i64, _P,
+                                                 ctypes.POINTER(NbFitOpts), _P]),
     ("nb_model_check", ctypes.c_int, [_P]),
     ("nb_model_counts", ctypes.c_int, [_P, _P, _P]),
     ("nb_model_params", ctypes.c_int, [_P, _P, _P, _P]),
@@ -147,6 +149,18 @@ def nb_refit(model, X, dtype, n, ld, y, alpha=1.0, log_prior=None, var_smoothing
     opts = NbFitOpts(float(alpha), ctypes.cast(prior_buf, _P) if prior_buf else None,
                      float(var_smoothing), ctypes.pointer(aux) if aux else None, int(no_sync))
     _check(lib().nb_refit(model, X, dtype, n, ld, y, ctypes.byref(opts), _stream_ptr(stream)))
+
+
+def nb_refit_gaussian_noalloc(model, X, n, ld, y, log_prior=None, var_smoothing=1e-9,
+                              no_sync=False, stream=None):
+    """Gaussian re-fit whose scratch is a fixed device array (no allocation)."""
+    prior_buf = None
+    if log_prior is not None:
+        prior_buf = (ctypes.c_double * len(log_prior))(*[float(v) for v in log_prior])
+    opts = NbFitOpts(1.0, ctypes.cast(prior_buf, _P) if prior_buf else None,
+                     float(var_smoothing), None, int(no_sync))
+    _check(lib().nb_refit_gaussian_noalloc(model, X, n, ld, y, ctypes.byref(opts),
+                                           _stream_ptr(stream)))
 
 
 def nb_kernel_launches():
