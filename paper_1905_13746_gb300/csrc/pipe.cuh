@@ -26,10 +26,26 @@ struct PipeArgs {
 };
 
 struct StageMeta {
-  long long row0;
+  long long row0;       // first row of the stage within its group
   long long ebase;      // first overflow entry staged (aligned down to 8)
   int nr;
   int in_smem;
+  int group;            // group of a segmented launch (0 otherwise)
+  int pad;
+};
+
+// One tile (up to RS rows of one group) as the producer streams it.
+struct TileInfo {
+  const char* X;             // the group's matrix
+  long long ld_bytes;
+  long long row0;            // first row of the tile within the group
+  int nr;                    // rows in the tile
+  int group;
+  const int64_t* ovf_ptr;    // the group's overflow list, or nullptr
+  const uint16_t* ovf_col;
+  const uint16_t* ovf_add;
+  long long E;               // entries in the group's list (ovf_ptr[n])
+  const int32_t* y;          // the group's labels (fit), or nullptr
 };
 
 // what the producer streams
@@ -70,37 +86,72 @@ inline void pipe_layout(PipeArgs& p, int rs, int stages, long long ld_bytes, boo
   p.tiles = (n + rs - 1) / rs;
 }
 
-// Producer warp: the whole warp calls it; lane 0 issues the copies.
-// Tiles [t0, t0 + ntl) of this block; the table (if any) goes on `tabbar`.
-__device__ __forceinline__ void pipe_produce(const PipeSrc& src, const PipeArgs& p,
-                                             unsigned char* sm, uint64_t* full, uint64_t* empty,
-                                             uint64_t* tabbar, long long t0, long long ntl) {
-  const int lane = threadIdx.x & 31;
-  const bool ovf = src.ovf_ptr != nullptr;
-  if (lane == 0 && src.table) {
-    mbar_expect_tx(tabbar, p.tab_bytes);
-    for (uint32_t off = 0; off < p.tab_bytes; off += 32768) {
-      const uint32_t len = p.tab_bytes - off < 32768 ? p.tab_bytes - off : 32768;
-      bulk_g2s(sm + off, static_cast<const char*>(src.table) + off, len, tabbar);
-    }
+// Tiles of one matrix (the single-group case).
+struct SingleSrc {
+  const PipeSrc* src;
+  const PipeArgs* p;
+  long long t0;
+  long long E;
+  __device__ __forceinline__ void init() {
+    E = src->ovf_ptr ? src->ovf_ptr[src->n] : 0;
   }
-  const long long E = ovf ? src.ovf_ptr[src.n] : 0;   // entries in the list
-  // overflow pointers of the next tile, one tile ahead: lane i holds
-  // ptr[row0 + i] and ptr[row0 + 32 + i]
+  __device__ __forceinline__ TileInfo tile(long long k) const {
+    TileInfo t;
+    t.X = src->X;
+    t.ld_bytes = src->ld_bytes;
+    t.row0 = (t0 + k) * p->RS;
+    t.nr = (int)min((long long)p->RS, src->n - t.row0);
+    t.group = 0;
+    t.ovf_ptr = src->ovf_ptr;
+    t.ovf_col = src->ovf_col;
+    t.ovf_add = src->ovf_add;
+    t.E = E;
+    t.y = src->y;
+    return t;
+  }
+};
+
+// Stage the parameter tables: table i (bytes each) goes to sm + i * stride.
+__device__ __forceinline__ void pipe_stage_tables(unsigned char* sm, const void* const* tables,
+                                                  int n_tables, uint32_t bytes, uint32_t stride,
+                                                  uint64_t* tabbar) {
+  if ((threadIdx.x & 31) != 0 || n_tables == 0) return;
+  mbar_expect_tx(tabbar, bytes * (uint32_t)n_tables);
+  for (int i = 0; i < n_tables; ++i)
+    for (uint32_t off = 0; off < bytes; off += 32768) {
+      const uint32_t len = bytes - off < 32768 ? bytes - off : 32768;
+      bulk_g2s(sm + (size_t)i * stride + off, static_cast<const char*>(tables[i]) + off, len,
+               tabbar);
+    }
+}
+
+// Producer warp: the whole warp calls it; lane 0 issues the copies.  `src`
+// describes tiles k = 0 .. ntl-1 of this block.  The overflow pointers of a
+// tile are loaded one tile ahead: lane i holds ptr[row0 + i] and
+// ptr[row0 + 32 + i].
+template <class Src>
+__device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
+                                                   unsigned char* sm, uint64_t* full,
+                                                   uint64_t* empty, long long ntl, int* status) {
+  const int lane = threadIdx.x & 31;
   long long pa = 0, pb = 0;
-  if (ovf && ntl > 0) {
-    const long long r0 = t0 * p.RS;
-    const long long nr = min((long long)p.RS, src.n - r0);
-    pa = lane <= nr ? src.ovf_ptr[r0 + lane] : 0;
-    pb = lane + 32 <= nr ? src.ovf_ptr[r0 + 32 + lane] : 0;
+  TileInfo cur;
+  if (ntl > 0) {
+    cur = src.tile(0);
+    if (cur.ovf_ptr) {
+      pa = lane <= cur.nr ? cur.ovf_ptr[cur.row0 + lane] : 0;
+      pb = lane + 32 <= cur.nr ? cur.ovf_ptr[cur.row0 + 32 + lane] : 0;
+    }
   }
   for (long long k = 0; k < ntl; ++k) {
     long long na = 0, nb = 0;
-    if (ovf && k + 1 < ntl) {
-      const long long r0 = (t0 + k + 1) * p.RS;
-      const long long nr = min((long long)p.RS, src.n - r0);
-      na = lane <= nr ? src.ovf_ptr[r0 + lane] : 0;
-      nb = lane + 32 <= nr ? src.ovf_ptr[r0 + 32 + lane] : 0;
+    TileInfo nxt = cur;
+    if (k + 1 < ntl) {
+      nxt = src.tile(k + 1);
+      if (nxt.ovf_ptr) {
+        na = lane <= nxt.nr ? nxt.ovf_ptr[nxt.row0 + lane] : 0;
+        nb = lane + 32 <= nxt.nr ? nxt.ovf_ptr[nxt.row0 + 32 + lane] : 0;
+      }
     }
     const int s = (int)(k % p.S);
     const uint32_t ph = (uint32_t)((k / p.S) & 1);
@@ -109,13 +160,13 @@ __device__ __forceinline__ void pipe_produce(const PipeSrc& src, const PipeArgs&
       if (lane == 0) ok = mbar_wait_bounded(&empty[s], ph ^ 1u);
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
-        if (lane == 0) atomicOr(src.status, ST_TIMEOUT);
+        if (lane == 0) atomicOr(status, ST_TIMEOUT);
         return;
       }
     }
     unsigned char* st = sm + p.stages_off + (size_t)s * p.stage_bytes;
-    const long long row0 = (t0 + k) * p.RS;
-    const int nr = (int)min((long long)p.RS, src.n - row0);
+    const int nr = cur.nr;
+    const bool ovf = cur.ovf_ptr != nullptr;
     long long e0 = 0, e1 = 0;
     if (ovf) {
       long long* sp = reinterpret_cast<long long*>(st + p.ptr_off);
@@ -126,41 +177,53 @@ __device__ __forceinline__ void pipe_produce(const PipeSrc& src, const PipeArgs&
       const long long tail_b = __shfl_sync(0xFFFFFFFFu, pb, nr & 31);
       e1 = nr < 32 ? tail_a : tail_b;
     }
-    if (src.y) {
+    if (cur.y) {
       // labels through registers (rows of a stage need not start 16-byte aligned)
       int32_t* sy = reinterpret_cast<int32_t*>(st + p.y_off);
-      if (lane < nr) sy[lane] = src.y[row0 + lane];
-      if (lane + 32 < nr) sy[lane + 32] = src.y[row0 + 32 + lane];
+      if (lane < nr) sy[lane] = cur.y[cur.row0 + lane];
+      if (lane + 32 < nr) sy[lane + 32] = cur.y[cur.row0 + 32 + lane];
     }
     __threadfence_block();
     __syncwarp();
     if (lane == 0) {
       StageMeta* m = reinterpret_cast<StageMeta*>(st + p.meta_off);
-      m->row0 = row0;
+      m->row0 = cur.row0;
       m->nr = nr;
-      const uint32_t xb = (uint32_t)nr * (uint32_t)src.ld_bytes;
+      m->group = cur.group;
+      const uint32_t xb = (uint32_t)nr * (uint32_t)cur.ld_bytes;
       uint32_t total = xb;
       const long long eb = e0 & ~7LL, ee = (e1 + 7) & ~7LL;
       int in_smem = 0;
-      if (ovf && e1 > e0 && ee - eb <= p.ent_cap && ee <= E) in_smem = 1;
+      if (ovf && e1 > e0 && ee - eb <= p.ent_cap && ee <= cur.E) in_smem = 1;
       m->in_smem = in_smem;
       m->ebase = eb;
       const uint32_t eb_bytes = in_smem ? (uint32_t)(ee - eb) * 2u : 0u;
       total += 2u * eb_bytes;
       mbar_expect_tx(&full[s], total);
-      const char* x = src.X + row0 * src.ld_bytes;
+      const char* x = cur.X + cur.row0 * cur.ld_bytes;
       for (uint32_t off = 0; off < xb; off += 32768) {
         const uint32_t len = xb - off < 32768 ? xb - off : 32768;
         bulk_g2s(st + off, x + off, len, &full[s]);
       }
       if (eb_bytes) {
-        bulk_g2s(st + p.col_off, src.ovf_col + eb, eb_bytes, &full[s]);
-        bulk_g2s(st + p.add_off, src.ovf_add + eb, eb_bytes, &full[s]);
+        bulk_g2s(st + p.col_off, cur.ovf_col + eb, eb_bytes, &full[s]);
+        bulk_g2s(st + p.add_off, cur.ovf_add + eb, eb_bytes, &full[s]);
       }
     }
     pa = na;
     pb = nb;
+    cur = nxt;
   }
+}
+
+// Single-matrix producer (the table, if any, is staged at offset 0).
+__device__ __forceinline__ void pipe_produce(const PipeSrc& src, const PipeArgs& p,
+                                             unsigned char* sm, uint64_t* full, uint64_t* empty,
+                                             uint64_t* tabbar, long long t0, long long ntl) {
+  if (src.table) pipe_stage_tables(sm, &src.table, 1, p.tab_bytes, 0, tabbar);
+  SingleSrc ss{&src, &p, t0, 0};
+  ss.init();
+  pipe_produce_tiles(ss, p, sm, full, empty, ntl, src.status);
 }
 
 }  // namespace nbg

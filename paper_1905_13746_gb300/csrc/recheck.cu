@@ -14,31 +14,35 @@
 
 #include "device.cuh"
 #include "internal.cuh"
+#include "seg.cuh"
 
 namespace nbg {
 
-struct RArgs {
-  const char* X;
-  int64_t ld;   // elements
-  int64_t n;
-  int F, C, kind, dtype;
-  const int64_t* ovf_ptr;
-  const uint16_t* ovf_col;
-  const uint16_t* ovf_add;
-  const int8_t* row_exp;
+// FP64 tables of one model
+struct RModel {
+  int kind, C;
   const double* p0;       // log theta | mu
   const double* p1;       // var
   const double* log_pi;
   const double* gconst;
+};
+
+// one stored matrix and its outputs
+struct RView {
+  const char* X;
+  int64_t ld;   // elements
+  int dtype, F;
+  const int64_t* ovf_ptr;
+  const uint16_t* ovf_col;
+  const uint16_t* ovf_add;
+  const int8_t* row_exp;
   uint8_t* label;
   float* margin;
   float* logpost;
-  int want_lp;
-  unsigned long long* n_rechecked;
 };
 
-__device__ __forceinline__ double load_x(const RArgs& a, const char* rp, int j, double scale) {
-  switch (a.dtype) {
+__device__ __forceinline__ double load_x(int dtype, const char* rp, int j, double scale) {
+  switch (dtype) {
     case NB_F32: return (double)reinterpret_cast<const float*>(rp)[j];
     case NB_U16: return (double)reinterpret_cast<const uint16_t*>(rp)[j];
     case NB_U8: return (double)reinterpret_cast<const uint8_t*>(rp)[j];
@@ -53,67 +57,80 @@ __device__ __forceinline__ double load_x(const RArgs& a, const char* rp, int j, 
   }
 }
 
+// The whole warp recomputes row r of v with model md; lane 0 writes outputs.
+__device__ __forceinline__ void recheck_row(const RView& v, const RModel& md, int64_t r,
+                                            int want_lp, double* s_sh) {
+  const int lane = threadIdx.x & 31;
+  const int es = v.dtype == NB_F32 ? 4 : ((v.dtype == NB_U16 || v.dtype == NB_BF16) ? 2 : 1);
+  const char* rp = v.X + r * v.ld * es;
+  const double scale =
+      (v.dtype == NB_FP8E4M3 && v.row_exp) ? ldexp(1.0, (int)v.row_exp[r]) : 1.0;
+  for (int c = 0; c < md.C; ++c) {
+    double acc = 0.0;
+    if (md.kind == NB_MULTINOMIAL) {
+      const double* lt = md.p0 + (int64_t)c * v.F;
+      for (int j = lane; j < v.F; j += 32) acc = fma(load_x(v.dtype, rp, j, scale), lt[j], acc);
+      if (v.dtype == NB_U8 && v.ovf_ptr) {
+        for (int64_t k = v.ovf_ptr[r] + lane; k < v.ovf_ptr[r + 1]; k += 32) {
+          const int j = v.ovf_col[k];
+          if (j < v.F) acc = fma((double)v.ovf_add[k], lt[j], acc);
+        }
+      }
+    } else {
+      const double* mu = md.p0 + (int64_t)c * v.F;
+      const double* var = md.p1 + (int64_t)c * v.F;
+      for (int j = lane; j < v.F; j += 32) {
+        const double dx = load_x(v.dtype, rp, j, scale) - mu[j];
+        acc += dx * dx / var[j];
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+    if (lane == 0)
+      s_sh[c] = md.kind == NB_MULTINOMIAL ? md.log_pi[c] + acc : md.gconst[c] - 0.5 * acc;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    int best = 0;
+    for (int c = 1; c < md.C; ++c)
+      if (s_sh[c] > s_sh[best]) best = c;
+    double second = -INFINITY;
+    for (int c = 0; c < md.C; ++c)
+      if (c != best && s_sh[c] > second) second = s_sh[c];
+    v.label[r] = (uint8_t)best;
+    v.margin[r] = (float)(s_sh[best] - second);
+    if (want_lp) {
+      double sum = 0.0;
+      for (int c = 0; c < md.C; ++c) sum += exp(s_sh[c] - s_sh[best]);
+      const double lse = s_sh[best] + log(sum);
+      for (int c = 0; c < md.C; ++c) v.logpost[r * md.C + c] = (float)(s_sh[c] - lse);
+    }
+  }
+  __syncwarp();
+}
+
+struct RArgs {
+  RView v;
+  RModel md;
+  int64_t n;
+  int want_lp;
+  unsigned long long* n_rechecked;
+};
+
 __global__ void __launch_bounds__(256) k_recheck(const RArgs a) {
   __shared__ double s_sh[8][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const int es = a.dtype == NB_F32 ? 4 : ((a.dtype == NB_U16 || a.dtype == NB_BF16) ? 2 : 1);
   unsigned long long cnt = 0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < a.n; base += nwarps * 32) {
     const int64_t row = base + lane;
-    const bool f = row < a.n && a.label[row] == kLabelRecheck;
+    const bool f = row < a.n && a.v.label[row] == kLabelRecheck;
     unsigned m = __ballot_sync(0xFFFFFFFFu, f);
     while (m) {
       const int src = __ffs(m) - 1;
       m &= m - 1;
-      const int64_t r = base + src;
-      const char* rp = a.X + r * a.ld * es;
-      const double scale =
-          (a.dtype == NB_FP8E4M3 && a.row_exp) ? ldexp(1.0, (int)a.row_exp[r]) : 1.0;
-      for (int c = 0; c < a.C; ++c) {
-        double acc = 0.0;
-        if (a.kind == NB_MULTINOMIAL) {
-          const double* lt = a.p0 + (int64_t)c * a.F;
-          for (int j = lane; j < a.F; j += 32) acc = fma(load_x(a, rp, j, scale), lt[j], acc);
-          if (a.dtype == NB_U8 && a.ovf_ptr) {
-            for (int64_t k = a.ovf_ptr[r] + lane; k < a.ovf_ptr[r + 1]; k += 32) {
-              const int j = a.ovf_col[k];
-              if (j < a.F) acc = fma((double)a.ovf_add[k], lt[j], acc);
-            }
-          }
-        } else {
-          const double* mu = a.p0 + (int64_t)c * a.F;
-          const double* var = a.p1 + (int64_t)c * a.F;
-          for (int j = lane; j < a.F; j += 32) {
-            const double dx = load_x(a, rp, j, scale) - mu[j];
-            acc += dx * dx / var[j];
-          }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
-        if (lane == 0)
-          s_sh[warp][c] = a.kind == NB_MULTINOMIAL ? a.log_pi[c] + acc : a.gconst[c] - 0.5 * acc;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        const double* s = s_sh[warp];
-        int best = 0;
-        for (int c = 1; c < a.C; ++c)
-          if (s[c] > s[best]) best = c;
-        double second = -INFINITY;
-        for (int c = 0; c < a.C; ++c)
-          if (c != best && s[c] > second) second = s[c];
-        a.label[r] = (uint8_t)best;
-        a.margin[r] = (float)(s[best] - second);
-        if (a.want_lp) {
-          double sum = 0.0;
-          for (int c = 0; c < a.C; ++c) sum += exp(s[c] - s[best]);
-          const double lse = s[best] + log(sum);
-          for (int c = 0; c < a.C; ++c) a.logpost[r * a.C + c] = (float)(s[c] - lse);
-        }
-        ++cnt;
-      }
-      __syncwarp();
+      recheck_row(a.v, a.md, base + src, a.want_lp, s_sh[warp]);
+      ++cnt;
     }
   }
   if (lane == 0 && cnt && a.n_rechecked) atomicAdd(a.n_rechecked, cnt);
@@ -123,24 +140,19 @@ nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t 
                          const nb_aux* aux, const ScoreOut& o, cudaStream_t st) {
   if (n == 0 || o.recheck == NB_RECHECK_OFF) return NB_OK;
   RArgs a{};
-  a.X = static_cast<const char*>(X);
-  a.ld = ld;
+  a.v.X = static_cast<const char*>(X);
+  a.v.ld = ld;
+  a.v.dtype = dt;
+  a.v.F = m->F;
+  a.v.ovf_ptr = aux ? aux->ovf_ptr : nullptr;
+  a.v.ovf_col = aux ? aux->ovf_col : nullptr;
+  a.v.ovf_add = aux ? aux->ovf_add : nullptr;
+  a.v.row_exp = aux ? aux->row_exp : nullptr;
+  a.v.label = o.label;
+  a.v.margin = o.margin;
+  a.v.logpost = o.logpost;
+  a.md = RModel{m->kind, m->C, m->d.p0, m->d.p1, m->d.log_pi, m->d.gconst};
   a.n = n;
-  a.F = m->F;
-  a.C = m->C;
-  a.kind = m->kind;
-  a.dtype = dt;
-  a.ovf_ptr = aux ? aux->ovf_ptr : nullptr;
-  a.ovf_col = aux ? aux->ovf_col : nullptr;
-  a.ovf_add = aux ? aux->ovf_add : nullptr;
-  a.row_exp = aux ? aux->row_exp : nullptr;
-  a.p0 = m->d.p0;
-  a.p1 = m->d.p1;
-  a.log_pi = m->d.log_pi;
-  a.gconst = m->d.gconst;
-  a.label = o.label;
-  a.margin = o.margin;
-  a.logpost = o.logpost;
   a.want_lp = o.want_lp;
   a.n_rechecked = reinterpret_cast<unsigned long long*>(o.n_rechecked);
   const int64_t chunks = (n + 255) / 256;
@@ -148,6 +160,80 @@ nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t 
   count_launch();
   k_recheck<<<(unsigned)(chunks < cap ? chunks : cap), 256, 0, st>>>(a);
   NB_TRY_CUDA(cudaGetLastError(), "k_recheck launch");
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// segmented recheck: warps take contiguous ranges of 32-row chunks of a group
+// list and walk its groups
+// ---------------------------------------------------------------------------
+struct RSegArgs {
+  const SegGroup* groups;
+  const SegHeader* hdr;
+  RModel md[kSegMaxModels];
+  int dtype, F, want_lp;
+  unsigned long long* n_rechecked;
+};
+
+__global__ void __launch_bounds__(256) k_recheck_seg(const RSegArgs a) {
+  __shared__ double s_sh[8][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_groups = a.hdr->n_groups;
+  const long long chunks = a.hdr->chunks;
+  const long long W = (long long)gridDim.x * 8, w = (long long)blockIdx.x * 8 + warp;
+  const long long c0 = chunks * w / W, c1 = chunks * (w + 1) / W;
+  if (c0 >= c1 || n_groups == 0) return;
+  const SegGroup* gr = a.groups;
+  int g = seg_find(n_groups, c0, [gr](int i) { return gr[i].chunk0; });
+  unsigned long long cnt = 0;
+  for (long long c = c0; c < c1; ++c) {
+    while (g + 1 < n_groups && gr[g + 1].chunk0 <= c) ++g;
+    const SegGroup& G = gr[g];
+    const long long base = (c - G.chunk0) * 32;
+    const long long row = base + lane;
+    const bool f = row < G.n && G.label[row] == kLabelRecheck;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, f);
+    if (!m) continue;
+    RView v;
+    v.X = G.X;
+    v.dtype = a.dtype;
+    v.F = a.F;
+    const int es = a.dtype == NB_F32 ? 4 : ((a.dtype == NB_U16 || a.dtype == NB_BF16) ? 2 : 1);
+    v.ld = G.ld_bytes / es;
+    v.ovf_ptr = G.ovf_ptr;
+    v.ovf_col = G.ovf_col;
+    v.ovf_add = G.ovf_add;
+    v.row_exp = G.row_exp;
+    v.label = G.label;
+    v.margin = G.margin;
+    v.logpost = G.logpost;
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      recheck_row(v, a.md[G.model], base + src, a.want_lp, s_sh[warp]);
+      ++cnt;
+    }
+  }
+  if (lane == 0 && cnt && a.n_rechecked) atomicAdd(a.n_rechecked, cnt);
+}
+
+nb_status launch_recheck_seg(const SegGroup* groups, const SegHeader* hdr,
+                             const nb_model* const* models, int n_models, nb_dtype dt, int F,
+                             int want_lp, int64_t* n_rechecked, cudaStream_t st) {
+  RSegArgs a{};
+  a.groups = groups;
+  a.hdr = hdr;
+  for (int i = 0; i < n_models && i < kSegMaxModels; ++i) {
+    const nb_model* m = models[i];
+    a.md[i] = RModel{m->kind, m->C, m->d.p0, m->d.p1, m->d.log_pi, m->d.gconst};
+  }
+  a.dtype = dt;
+  a.F = F;
+  a.want_lp = want_lp;
+  a.n_rechecked = reinterpret_cast<unsigned long long*>(n_rechecked);
+  count_launch();
+  k_recheck_seg<<<num_sms() * 4, 256, 0, st>>>(a);
+  NB_TRY_CUDA(cudaGetLastError(), "k_recheck_seg launch");
   return NB_OK;
 }
 

@@ -40,19 +40,36 @@ __device__ __forceinline__ float softplusf(float z) {
   return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));
 }
 
-__device__ __forceinline__ void c2_epilogue(const S2Args& a, int64_t row, float d, float tau) {
+// Outputs of one row from its log-odds d and the bound tau on |d - d_exact|:
+// label (or the recheck mark), margin |d|, log posteriors -softplus(-+d).
+__device__ __forceinline__ void c2_store(uint8_t* label, float* margin, float* logpost,
+                                         int want_lp, int recheck, int64_t row, float d,
+                                         float tau) {
   bool flag = false;
   const float ad = fabsf(d);
-  if (a.recheck != NB_RECHECK_OFF) {
+  if (recheck != NB_RECHECK_OFF) {
     flag = !(ad > tau);  // also true for NaN
-    if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, ad)) flag = true;
+    if (recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, ad)) flag = true;
   }
-  a.label[row] = flag ? kLabelRecheck : (d > 0.f ? 1 : 0);
-  a.margin[row] = ad;
-  if (a.want_lp) {
-    a.logpost[2 * row] = -softplusf(d);
-    a.logpost[2 * row + 1] = -softplusf(-d);
+  label[row] = flag ? kLabelRecheck : (d > 0.f ? 1 : 0);
+  margin[row] = ad;
+  if (want_lp) {
+    logpost[2 * row] = -softplusf(d);
+    logpost[2 * row + 1] = -softplusf(-d);
   }
+}
+
+__device__ __forceinline__ void c2_epilogue(const S2Args& a, int64_t row, float d, float tau) {
+  c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, row, d, tau);
+}
+
+// Rigorous bound on |d_gpu - d_exact| of the fixed-point u8 path: the Delta
+// quantisation (half a step per unit count), the int64 -> FP32 conversion and
+// the final add, and slack for the FP64 reference's own rounding.
+__device__ __forceinline__ float c2_tau_u8(float T, float Dsum, float b, float inv_scale,
+                                           float maxabs) {
+  return 0.5f * T * inv_scale * 1.0001f + 2.4e-7f * (fabsf(Dsum) + fabsf(b)) +
+         1e-12f * (T * maxabs + fabsf(b)) + 1e-30f;
 }
 
 // ---------------------------------------------------------------------------

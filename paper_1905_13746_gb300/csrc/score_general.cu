@@ -18,6 +18,7 @@
 
 #include "device.cuh"
 #include "internal.cuh"
+#include "seg.cuh"
 
 namespace nbg {
 
@@ -101,8 +102,8 @@ __device__ __forceinline__ void decode16(int dt, const uint4& x, float* v, int& 
   }
 }
 
-__global__ void __launch_bounds__(256) k_score_gen(const GArgs a) {
-  extern __shared__ __align__(16) float gsm[];
+// One tile of GBM rows starting at r0 (all class blocks, epilogue included).
+__device__ __forceinline__ void gen_tile(const GArgs& a, int64_t r0, float* gsm) {
   float* Xs = gsm;                         // [GBK][GBM + 4]
   float* Ws = Xs + GBK * (GBM + 4);        // [GBK][GCB + 4]
   float* Ss = Ws + GBK * (GCB + 4);        // [GBM][C_pad]
@@ -113,173 +114,174 @@ __global__ void __launch_bounds__(256) k_score_gen(const GArgs a) {
   const int es = a.dtype == NB_F32 ? 4 : ((a.dtype == NB_U16 || a.dtype == NB_BF16) ? 2 : 1);
   const int epv = 16 / es;
   const int vpr = GBK / epv;               // vectors per row per chunk (2, 4 or 8)
-  const int64_t ntile = (a.n + GBM - 1) / GBM;
   const float wmax = *a.wmax;
   float bmax = 0.f;
   for (int c = 0; c < a.C; ++c) bmax = fmaxf(bmax, fabsf(a.bias[c]));
   const int nchunk = (a.F + GBK - 1) / GBK;
-
-  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int64_t r0 = tile * GBM;
-    float tpart[2] = {0.f, 0.f};   // |x| sums of the (row, vector) slots this thread loads
-    for (int cb = 0; cb < a.C; cb += GCB) {
-      float run[4][4];
+  float tpart[2] = {0.f, 0.f};   // |x| sums of the (row, vector) slots this thread loads
+  for (int cb = 0; cb < a.C; cb += GCB) {
+    float run[4][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) run[i][j] = 0.f;
-      for (int ch = 0; ch < nchunk; ++ch) {
-        const int k0 = ch * GBK;
-        // X tile -> Xs[k][row] (FP32)
-        for (int s = 0, slot = tid; slot < GBM * vpr; ++s, slot += 256) {
-          const int row = slot / vpr, vv = slot % vpr;
-          const int64_t gr = r0 + row;
-          float v[16];
-          int cnt = epv;
-          const int kb = k0 + vv * epv;
-          if (gr < a.n) {
-            const char* rp = a.X + gr * a.ld * es;
-            if (a.aligned && kb + epv <= a.F) {
-              decode16(a.dtype, ld_stream16(rp + (int64_t)kb * es), v, cnt);
-            } else {
-              for (int e = 0; e < epv; ++e) v[e] = kb + e < a.F ? gload1(a.dtype, rp, kb + e) : 0.f;
-            }
-            if (a.dtype == NB_FP8E4M3 && a.row_exp) {
-              const float sc = exp2f((float)a.row_exp[gr]);
-              for (int e = 0; e < epv; ++e) v[e] *= sc;
-            }
-          } else {
-            for (int e = 0; e < epv; ++e) v[e] = 0.f;
-          }
-          float tsum = 0.f;
-          for (int e = 0; e < epv; ++e) {
-            Xs[(vv * epv + e) * (GBM + 4) + row] = v[e];
-            tsum += fabsf(v[e]);
-          }
-          if (cb == 0) tpart[s] += tsum;
-        }
-        // W tile -> Ws[k][c]
-        for (int slot = tid; slot < GCB * (GBK / 4); slot += 256) {
-          const int c = slot / (GBK / 4), kq = slot % (GBK / 4);
-          float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (cb + c < a.C)
-            wv = *reinterpret_cast<const float4*>(a.w + (int64_t)(cb + c) * a.F_pad + k0 + kq * 4);
-          Ws[(kq * 4 + 0) * (GCB + 4) + c] = wv.x;
-          Ws[(kq * 4 + 1) * (GCB + 4) + c] = wv.y;
-          Ws[(kq * 4 + 2) * (GCB + 4) + c] = wv.z;
-          Ws[(kq * 4 + 3) * (GCB + 4) + c] = wv.w;
-        }
-        __syncthreads();
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < GBK; ++k) {
-          const float4 ra = *reinterpret_cast<const float4*>(&Xs[k * (GBM + 4) + ty * 4]);
-          const float4 rb = *reinterpret_cast<const float4*>(&Ws[k * (GCB + 4) + tx * 4]);
-          const float A[4] = {ra.x, ra.y, ra.z, ra.w};
-          const float B[4] = {rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(A[i], B[j], acc[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) run[i][j] += acc[i][j];
-        __syncthreads();
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = cb + tx * 4 + j;
-          if (c < a.C) Ss[(ty * 4 + i) * C_pad + c] = run[i][j];
-        }
-    }
-    // row |x| totals, summed over the row's slots in a fixed order
-    for (int s = 0, slot = tid; slot < GBM * vpr; ++s, slot += 256) Tslot[slot] = tpart[s];
-    __syncthreads();
-    if (tid < GBM) {
-      float t = 0.f;
-      for (int vv = 0; vv < vpr; ++vv) t += Tslot[tid * vpr + vv];
-      Ts[tid] = t;
-    }
-    __syncthreads();
-    // overflow entries (u8 storage): one thread per (row, class), entries in order
-    if (a.dtype == NB_U8 && a.ovf_ptr) {
-      for (int q = tid; q < GBM * a.C; q += 256) {
-        const int row = q / a.C, c = q % a.C;
+      for (int j = 0; j < 4; ++j) run[i][j] = 0.f;
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int k0 = ch * GBK;
+      // X tile -> Xs[k][row] (FP32)
+      for (int s = 0, slot = tid; slot < GBM * vpr; ++s, slot += 256) {
+        const int row = slot / vpr, vv = slot % vpr;
         const int64_t gr = r0 + row;
-        if (gr >= a.n) continue;
-        float s = Ss[row * C_pad + c];
-        float t = 0.f;
-        for (int64_t k = a.ovf_ptr[gr]; k < a.ovf_ptr[gr + 1]; ++k) {
-          const int j = a.ovf_col[k];
-          if (j >= a.F) continue;
-          const float add = (float)a.ovf_add[k];
-          s = fmaf(add, a.w[(int64_t)c * a.F_pad + j], s);
-          t += add;
+        float v[16];
+        int cnt = epv;
+        const int kb = k0 + vv * epv;
+        if (gr < a.n) {
+          const char* rp = a.X + gr * a.ld * es;
+          if (a.aligned && kb + epv <= a.F) {
+            decode16(a.dtype, ld_stream16(rp + (int64_t)kb * es), v, cnt);
+          } else {
+            for (int e = 0; e < epv; ++e) v[e] = kb + e < a.F ? gload1(a.dtype, rp, kb + e) : 0.f;
+          }
+          if (a.dtype == NB_FP8E4M3 && a.row_exp) {
+            const float sc = exp2f((float)a.row_exp[gr]);
+            for (int e = 0; e < epv; ++e) v[e] *= sc;
+          }
+        } else {
+          for (int e = 0; e < epv; ++e) v[e] = 0.f;
         }
-        Ss[row * C_pad + c] = s;
-        if (c == 0) Tslot[row] = t;
+        float tsum = 0.f;
+        for (int e = 0; e < epv; ++e) {
+          Xs[(vv * epv + e) * (GBM + 4) + row] = v[e];
+          tsum += fabsf(v[e]);
+        }
+        if (cb == 0) tpart[s] += tsum;
+      }
+      // W tile -> Ws[k][c]
+      for (int slot = tid; slot < GCB * (GBK / 4); slot += 256) {
+        const int c = slot / (GBK / 4), kq = slot % (GBK / 4);
+        float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cb + c < a.C)
+          wv = *reinterpret_cast<const float4*>(a.w + (int64_t)(cb + c) * a.F_pad + k0 + kq * 4);
+        Ws[(kq * 4 + 0) * (GCB + 4) + c] = wv.x;
+        Ws[(kq * 4 + 1) * (GCB + 4) + c] = wv.y;
+        Ws[(kq * 4 + 2) * (GCB + 4) + c] = wv.z;
+        Ws[(kq * 4 + 3) * (GCB + 4) + c] = wv.w;
       }
       __syncthreads();
-      if (tid < GBM) Ts[tid] += Tslot[tid];
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < GBK; ++k) {
+        const float4 ra = *reinterpret_cast<const float4*>(&Xs[k * (GBM + 4) + ty * 4]);
+        const float4 rb = *reinterpret_cast<const float4*>(&Ws[k * (GCB + 4) + tx * 4]);
+        const float A[4] = {ra.x, ra.y, ra.z, ra.w};
+        const float B[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(A[i], B[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) run[i][j] += acc[i][j];
       __syncthreads();
     }
-    // epilogue: a warp per row
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int row = warp; row < GBM; row += 8) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = cb + tx * 4 + j;
+        if (c < a.C) Ss[(ty * 4 + i) * C_pad + c] = run[i][j];
+      }
+  }
+  // row |x| totals, summed over the row's slots in a fixed order
+  for (int s = 0, slot = tid; slot < GBM * vpr; ++s, slot += 256) Tslot[slot] = tpart[s];
+  __syncthreads();
+  if (tid < GBM) {
+    float t = 0.f;
+    for (int vv = 0; vv < vpr; ++vv) t += Tslot[tid * vpr + vv];
+    Ts[tid] = t;
+  }
+  __syncthreads();
+  // overflow entries (u8 storage): one thread per (row, class), entries in order
+  if (a.dtype == NB_U8 && a.ovf_ptr) {
+    for (int q = tid; q < GBM * a.C; q += 256) {
+      const int row = q / a.C, c = q % a.C;
       const int64_t gr = r0 + row;
       if (gr >= a.n) continue;
-      float best = -INFINITY;
-      int bi = 0x7FFFFFFF;
-      for (int c = lane; c < a.C; c += 32) {
-        const float s = Ss[row * C_pad + c] + a.bias[c];
-        if (s > best) { best = s; bi = c; }
+      float s = Ss[row * C_pad + c];
+      float t = 0.f;
+      for (int64_t k = a.ovf_ptr[gr]; k < a.ovf_ptr[gr + 1]; ++k) {
+        const int j = a.ovf_col[k];
+        if (j >= a.F) continue;
+        const float add = (float)a.ovf_add[k];
+        s = fmaf(add, a.w[(int64_t)c * a.F_pad + j], s);
+        t += add;
       }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
-        const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      float second = -INFINITY, se = 0.f;
-      for (int c = lane; c < a.C; c += 32) {
-        const float s = Ss[row * C_pad + c] + a.bias[c];
-        if (c != bi) second = fmaxf(second, s);
-        se += expf(s - best);
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        second = fmaxf(second, __shfl_xor_sync(0xFFFFFFFFu, second, off));
-        se += __shfl_xor_sync(0xFFFFFFFFu, se, off);
-      }
-      const float lse = best + logf(se);
-      const float margin = best - second;
-      const int64_t novf = (a.dtype == NB_U8 && a.ovf_ptr) ? a.ovf_ptr[gr + 1] - a.ovf_ptr[gr] : 0;
-      const float k = (float)(GBK + nchunk + 3 + novf);
-      const float gam = k * 5.9604645e-8f / (1.f - k * 5.9604645e-8f);
-      const float tau = 2.f * (gam * (Ts[row] * wmax + bmax) * 1.01f + 1e-12f * (Ts[row] * wmax + bmax)) + 1e-30f;
-      bool flag = false;
-      if (a.recheck != NB_RECHECK_OFF) {
-        flag = !(margin > tau);
-        if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
-      }
-      if (lane == 0) {
-        a.label[gr] = flag ? kLabelRecheck : (uint8_t)bi;
-        a.margin[gr] = margin;
-      }
-      if (a.want_lp)
-        for (int c = lane; c < a.C; c += 32)
-          a.logpost[gr * a.C + c] = Ss[row * C_pad + c] + a.bias[c] - lse;
+      Ss[row * C_pad + c] = s;
+      if (c == 0) Tslot[row] = t;
     }
     __syncthreads();
+    if (tid < GBM) Ts[tid] += Tslot[tid];
+    __syncthreads();
   }
+  // epilogue: a warp per row
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int row = warp; row < GBM; row += 8) {
+    const int64_t gr = r0 + row;
+    if (gr >= a.n) continue;
+    float best = -INFINITY;
+    int bi = 0x7FFFFFFF;
+    for (int c = lane; c < a.C; c += 32) {
+      const float s = Ss[row * C_pad + c] + a.bias[c];
+      if (s > best) { best = s; bi = c; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+      const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    float second = -INFINITY, se = 0.f;
+    for (int c = lane; c < a.C; c += 32) {
+      const float s = Ss[row * C_pad + c] + a.bias[c];
+      if (c != bi) second = fmaxf(second, s);
+      se += expf(s - best);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      second = fmaxf(second, __shfl_xor_sync(0xFFFFFFFFu, second, off));
+      se += __shfl_xor_sync(0xFFFFFFFFu, se, off);
+    }
+    const float lse = best + logf(se);
+    const float margin = best - second;
+    const int64_t novf = (a.dtype == NB_U8 && a.ovf_ptr) ? a.ovf_ptr[gr + 1] - a.ovf_ptr[gr] : 0;
+    const float k = (float)(GBK + nchunk + 3 + novf);
+    const float gam = k * 5.9604645e-8f / (1.f - k * 5.9604645e-8f);
+    const float tau = 2.f * (gam * (Ts[row] * wmax + bmax) * 1.01f + 1e-12f * (Ts[row] * wmax + bmax)) + 1e-30f;
+    bool flag = false;
+    if (a.recheck != NB_RECHECK_OFF) {
+      flag = !(margin > tau);
+      if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
+    }
+    if (lane == 0) {
+      a.label[gr] = flag ? kLabelRecheck : (uint8_t)bi;
+      a.margin[gr] = margin;
+    }
+    if (a.want_lp)
+      for (int c = lane; c < a.C; c += 32)
+        a.logpost[gr * a.C + c] = Ss[row * C_pad + c] + a.bias[c] - lse;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_score_gen(const GArgs a) {
+  extern __shared__ __align__(16) float gsm[];
+  const int64_t ntile = (a.n + GBM - 1) / GBM;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) gen_tile(a, tile * GBM, gsm);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,6 +358,94 @@ __global__ void __launch_bounds__(256) k_score_gauss(const GGArgs a) {
     }
     __syncwarp();
   }
+}
+
+// ---------------------------------------------------------------------------
+// segmented general scorer: 64-row tiles of a group list, each group scored
+// with its own model slot (one launch per batch)
+// ---------------------------------------------------------------------------
+struct GModel {
+  int C, F_pad;
+  const float* w;
+  const float* bias;
+  const float* wmax;
+};
+
+struct GSegArgs {
+  const SegGroup* groups;
+  const SegHeader* hdr;
+  GModel md[kSegMaxModels];
+  int F, dtype, want_lp, recheck;
+  int* status;
+};
+
+__global__ void __launch_bounds__(256) k_score_gen_seg(const GSegArgs s) {
+  extern __shared__ __align__(16) float gsm[];
+  const int n_groups = s.hdr->n_groups;
+  const long long tiles = s.hdr->tiles;
+  const SegGroup* gr = s.groups;
+  const int es = s.dtype == NB_F32 ? 4 : ((s.dtype == NB_U16 || s.dtype == NB_BF16) ? 2 : 1);
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int g = seg_find(n_groups, t, [gr](int i) { return gr[i].tile0; });
+    const SegGroup& G = gr[g];
+    const GModel& M = s.md[G.model];
+    GArgs a{};
+    a.X = G.X;
+    a.ld = G.ld_bytes / es;
+    a.n = G.n;
+    a.F = s.F;
+    a.F_pad = M.F_pad;
+    a.C = M.C;
+    a.dtype = s.dtype;
+    a.aligned = ((reinterpret_cast<uintptr_t>(G.X) & 15) == 0) && (G.ld_bytes % 16 == 0);
+    a.ovf_ptr = G.ovf_ptr;
+    a.ovf_col = G.ovf_col;
+    a.ovf_add = G.ovf_add;
+    a.row_exp = G.row_exp;
+    a.w = M.w;
+    a.bias = M.bias;
+    a.wmax = M.wmax;
+    a.label = G.label;
+    a.margin = G.margin;
+    a.logpost = G.logpost;
+    a.want_lp = s.want_lp;
+    a.recheck = s.recheck;
+    a.status = s.status;
+    gen_tile(a, (t - G.tile0) * GBM, gsm);
+  }
+}
+
+nb_status launch_score_gen_seg(const SegGroup* groups, const SegHeader* hdr,
+                               const nb_model* const* models, int n_models, nb_dtype dt, int F,
+                               int want_lp, int recheck, int* status, cudaStream_t st) {
+  GSegArgs s{};
+  s.groups = groups;
+  s.hdr = hdr;
+  int C_max = 2;
+  for (int i = 0; i < n_models && i < kSegMaxModels; ++i) {
+    const nb_model* m = models[i];
+    s.md[i] = GModel{m->C, m->F_pad, m->d.w, m->d.bias, m->d.wmax};
+    C_max = m->C > C_max ? m->C : C_max;
+  }
+  s.F = F;
+  s.dtype = dt;
+  s.want_lp = want_lp;
+  s.recheck = recheck;
+  s.status = status;
+  const int C_pad = ((C_max + 3) / 4) * 4;
+  const int smem =
+      (int)sizeof(float) * (GBK * (GBM + 4) + GBK * (GCB + 4) + GBM * C_pad + GBM + GBM * 8);
+  if (smem > 48 * 1024)
+    NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gen_seg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem),
+                "cudaFuncSetAttribute(gen_seg)");
+  int occ = 0;
+  NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_gen_seg, 256, smem),
+              "occupancy(gen_seg)");
+  count_launch();
+  k_score_gen_seg<<<num_sms() * (occ > 0 ? occ : 1), 256, smem, st>>>(s);
+  NB_TRY_CUDA(cudaGetLastError(), "k_score_gen_seg launch");
+  return NB_OK;
 }
 
 nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt, int64_t n,
