@@ -209,6 +209,185 @@ def time_e2e(model, host, dev, out, host_out, steps, warmup, stream):
 
 
 # ----------------------------------------------------------------------------
+# serving: Poisson arrivals of file groups, continuous batching
+# ----------------------------------------------------------------------------
+SERVE_F = 2048
+SERVE_CLASSES = (2, 16)
+
+
+def make_serving(device, n_pool=131072, n_fit=100_000):
+    """Two resident models (C=2 and C=16) over F=2048 u8 opcode counts
+    (Dirichlet(0.05) class profiles, 30% shared features, lognormal(8.5, 1)
+    file totals, counts clamped at 255) and a pinned host pool of files,
+    half from each model's profiles, that the arriving groups are cut from."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    import synth
+    seed = synth.seed_for(5)
+    models, half = [], n_pool // 2
+    pool = torch.empty((2 * half, SERVE_F), dtype=torch.uint8).pin_memory()
+    for k, C in enumerate(SERVE_CLASSES):
+        p = synth.dirichlet_profiles(seed + 10 * k, C, SERVE_F, 0.05, shared_frac=0.3)
+        lab = synth.labels_bernoulli if C == 2 else (lambda s, n: synth.labels_zipf(s, n, 16))
+        y = lab(seed + 10 * k + 1, n_fit)
+        X = synth.count_rows(seed + 10 * k + 3, p, y, synth.file_totals(seed + 10 * k + 2, n_fit),
+                             255, out_dtype="uint8", device=device)
+        models.append(nb.fit(nb.Features(X, nb.NB_U8), torch.as_tensor(y, device=device), C))
+        y2 = lab(seed + 10 * k + 4, half)
+        X2 = synth.count_rows(seed + 10 * k + 6, p, y2, synth.file_totals(seed + 10 * k + 5, half),
+                              255, out_dtype="uint8", device=device)
+        pool[k * half:(k + 1) * half].copy_(X2)
+        del X, X2
+    torch.cuda.synchronize()
+    return models, pool
+
+
+class ServeStream:
+    """A seeded stream of groups (sizes lognormal, median 500, 1..50,000 files;
+    model chosen uniformly) with pinned host outputs for every group."""
+
+    def __init__(self, pool, n_groups, seed):
+        import torch
+
+        import synth
+        half = pool.shape[0] // 2
+        self.sizes = synth.group_sizes(seed, n_groups)
+        self.mids = synth.model_choice(seed + 1, n_groups).astype(np.int32)
+        rng = np.random.default_rng(seed + 2)
+        self.offs = self.mids.astype(np.int64) * half + rng.integers(0, half - self.sizes + 1)
+        self.unit_gaps = synth.poisson_arrivals(seed + 3, n_groups, 1.0)   # rate 1/s
+        C = np.array(SERVE_CLASSES)[self.mids]
+        cum = np.concatenate([[0], np.cumsum(self.sizes)])
+        cumc = np.concatenate([[0], np.cumsum(self.sizes * C)])
+        self.files = int(cum[-1])
+        self.label = torch.empty(self.files, dtype=torch.uint8).pin_memory()
+        self.margin = torch.empty(self.files, dtype=torch.float32).pin_memory()
+        self.logpost = torch.empty(int(cumc[-1]), dtype=torch.float32).pin_memory()
+        self.x_ptr = (pool.data_ptr() + self.offs * SERVE_F).astype(np.uint64)
+        self.l_ptr = (self.label.data_ptr() + cum[:-1]).astype(np.uint64)
+        self.m_ptr = (self.margin.data_ptr() + 4 * cum[:-1]).astype(np.uint64)
+        self.p_ptr = (self.logpost.data_ptr() + 4 * cumc[:-1]).astype(np.uint64)
+        self.cum, self.cumc = cum, cumc
+
+    def arrivals(self, t0_us, files_per_s):
+        """Poisson arrivals offering ``files_per_s`` (None: all at t0)."""
+        if files_per_s is None:
+            return np.full(len(self.sizes), t0_us)
+        rate = files_per_s / float(self.sizes.mean())          # groups per second
+        return t0_us + 1e6 * self.unit_gaps / rate
+
+
+def serve_replay(server, st, files_per_s):
+    """Replays the stream in real time (bursts of the groups that have
+    arrived); latency counts from each group's scheduled arrival."""
+    import paper_1905_13746_gb300 as nb
+    clock = nb.Server.clock_us
+    sched = st.arrivals(clock() + 2000.0, files_per_s)
+    n, i, tickets = len(sched), 0, []
+    while i < n:
+        now = clock()
+        j = int(np.searchsorted(sched, now, side="right"))
+        if j > i:
+            tickets.append(server.submit_raw(st.mids[i:j], st.x_ptr[i:j], st.sizes[i:j],
+                                             st.l_ptr[i:j], st.m_ptr[i:j], st.p_ptr[i:j],
+                                             sched[i:j]))
+            i = j
+        elif sched[i] - now > 400.0:
+            time.sleep((sched[i] - now - 300.0) * 1e-6)
+    for tk in tickets:
+        for t in tk:
+            server.wait(int(t), 120_000_000)
+    return server.stats()
+
+
+def serve_ours(models, st, files_per_s, budget=4 << 30, slots=64):
+    import paper_1905_13746_gb300 as nb
+    server = nb.Server(models, nb.NB_U8, mem_budget=budget, max_slots=slots,
+                       want_logpost=True, recheck=nb.NB_RECHECK_LP)
+    try:
+        r = serve_replay(server, st, files_per_s)
+    finally:
+        server.close()
+    return r
+
+
+def serve_per_group_fp32(models, pool32, st, files_per_s, device):
+    """Baseline: one group at a time with plain FP32 storage -- H2D of the
+    group's FP32 rows, one nb_score_group call, D2H of the results, wait."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    nmax = int(st.sizes.max())
+    cmax = max(SERVE_CLASSES)
+    xd = torch.empty((nmax, SERVE_F), dtype=torch.float32, device=device)
+    ld = torch.empty(nmax, dtype=torch.uint8, device=device)
+    md = torch.empty(nmax, dtype=torch.float32, device=device)
+    pd = torch.empty(nmax * cmax, dtype=torch.float32, device=device)
+    stream = torch.cuda.Stream(device)
+    clock = nb.Server.clock_us
+    sched = st.arrivals(clock() + 2000.0, files_per_s)
+    lat = np.zeros(len(sched))
+    first = sched[0]
+    with torch.cuda.stream(stream):
+        for g in range(len(sched)):
+            while clock() < sched[g]:
+                pass
+            n, mid = int(st.sizes[g]), int(st.mids[g])
+            C = SERVE_CLASSES[mid]
+            o = int(st.offs[g])
+            xd[:n].copy_(pool32[o:o + n], non_blocking=True)
+            nb.nb_score_group(models[mid].handle, xd.data_ptr(), nb.NB_F32, n, SERVE_F,
+                              ld.data_ptr(), md.data_ptr(), pd.data_ptr(), want_logpost=True,
+                              stream=stream)
+            c0, cc = int(st.cum[g]), int(st.cumc[g])
+            st.label[c0:c0 + n].copy_(ld[:n], non_blocking=True)
+            st.margin[c0:c0 + n].copy_(md[:n], non_blocking=True)
+            st.logpost[cc:cc + n * C].copy_(pd[:n * C], non_blocking=True)
+            stream.synchronize()
+            lat[g] = clock() - sched[g]
+        last = clock()
+    return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+            "files_per_s": st.files / ((last - first) * 1e-6)}
+
+
+def run_serving(device, n_groups, loads, seed_off=0):
+    """Capacity and latency of the server, and of per-group FP32 launches."""
+    import torch
+
+    import synth
+    models, pool = make_serving(device)
+    st = ServeStream(pool, n_groups, synth.seed_for(5) + 100 + seed_off)
+    serve_ours(models, st, None)                                     # warm-up
+    cap = serve_ours(models, st, None)
+    out = {"workload": f"Poisson arrivals of {n_groups} groups, sizes lognormal(median 500, "
+                       f"sigma 1.49) clipped to 1..50000 files, F={SERVE_F} u8 counts, models "
+                       f"C=2 and C=16 chosen uniformly, pinned host inputs and outputs, "
+                       f"labels + margins + log posteriors with FP64 recheck",
+           "groups": n_groups, "files": st.files, "mean_group_files": float(st.sizes.mean()),
+           "capacity_files_per_s": cap["files_per_s"], "loads": []}
+    for f in loads:
+        r = serve_ours(models, st, f * cap["files_per_s"])
+        out["loads"].append({"offered_frac": f, "offered_files_per_s": f * cap["files_per_s"],
+                             "files_per_s": r["files_per_s"], "p50_ms": r["p50_us"] / 1e3,
+                             "p99_ms": r["p99_us"] / 1e3})
+    pool32 = pool.to(torch.float32).pin_memory()
+    bcap = serve_per_group_fp32(models, pool32, st, None, device)
+    eq = 0.5 * bcap["files_per_s"]
+    b_eq = serve_per_group_fp32(models, pool32, st, eq, device)
+    o_eq = serve_ours(models, st, eq)
+    out["per_group_fp32"] = {
+        "capacity_files_per_s": bcap["files_per_s"],
+        "at_equal_load": {"offered_files_per_s": eq,
+                          "per_group_fp32": {"p50_ms": b_eq["p50_us"] / 1e3,
+                                             "p99_ms": b_eq["p99_us"] / 1e3},
+                          "server": {"p50_ms": o_eq["p50_us"] / 1e3,
+                                     "p99_ms": o_eq["p99_us"] / 1e3}}}
+    del pool32
+    return out
+
+
+# ----------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample of the same workload)
 # ----------------------------------------------------------------------------
 def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_total):
@@ -295,6 +474,10 @@ def main():
     ap.add_argument("--ref-score-rows", type=int, default=40_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-groups", type=int, default=4000)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="print only the serving sweep (loads 0.25/0.5/0.75/0.9)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -312,6 +495,11 @@ def main():
     device = torch.device("cuda", local)
     nb.build()
     nb.lib()
+    if args.serving_only:
+        sv = run_serving(device, args.serving_groups, [0.25, 0.5, 0.75, 0.9])
+        if rank == 0:
+            print(json.dumps({"serving": sv}), flush=True)
+        return 0
 
     W = make_workload(args, device)
     N, F, C = args.n, args.F, 2
@@ -392,6 +580,11 @@ def main():
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
         del host, devb, dev
 
+    # ---- serving under Poisson arrivals (N = 1 only) ------------------------
+    serving = None
+    if ws == 1 and not args.no_serving:
+        serving = run_serving(device, args.serving_groups, [0.5, 0.9])
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) -----------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -433,6 +626,7 @@ def main():
                        "score_gbs": plain_ach, "score_frac": plain_ach / hbm_peak,
                        "n_rechecked": p_rechecked},
         "e2e": e2e,
+        "serving": serving,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "gpu_launches": launches,

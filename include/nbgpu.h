@@ -224,6 +224,107 @@ NB_API nb_status nb_score_group(const nb_model* model, const void* X, nb_dtype d
                          float* logpost, const nb_score_opts* opts,
                          void* cuda_stream, int64_t* n_rechecked);
 
+/* ---- batches of groups: one persistent launch per kernel family ----------
+ * The paper scores files group by group, each group with its own model
+ * (Sec. 3 size groups, Sec. 4 per-group models).  A batch scores many groups
+ * of uneven size (1 to 10^5+ files) at once: the groups of two-class models
+ * in one launch of the pipelined two-class kernel, the groups of many-class
+ * models in one launch of the general kernel, then one FP64 recheck launch
+ * per family -- independent of the number of groups.  Each row's arithmetic
+ * is that of nb_score_group, so a group's results are the same bits alone
+ * and inside any batch.
+ *
+ * nb_batch_create: models[0..n_models) (multinomial, all with the same F,
+ *   n_models <= 8), the storage dtype of every group (two-class models: U8 or
+ *   F32), the largest leading dimension a group will use, the largest number
+ *   of groups per call, and the score options (want_logpost, recheck; aux is
+ *   ignored -- each group carries its own).  Allocates the batch's device and
+ *   pinned host work lists.
+ * nb_batch_score: scores groups[0..n_groups) on the stream (asynchronous).
+ *   X must be 16-byte aligned with ld * element size a multiple of 16.
+ *   n_rechecked: device int64 or NULL.  Successive calls on one batch must be
+ *   ordered (one stream); the host buffer of a call is reused two calls later,
+ *   after waiting for that call's copy to finish.
+ * nb_batch_capture: records the batch's launch sequence (work-list copy, the
+ *   scoring launches, the recheck launches) into CUDA graphs on the stream
+ *   (which must not be capturing already); later nb_batch_score calls replay
+ *   them instead of launching -- the work list is read from device memory, so
+ *   one graph serves every batch.
+ * nb_batch_destroy: waits for the batch's work and frees it. */
+typedef struct {
+  int model;              /* slot in the batch's model list */
+  const void* X;          /* n x ld elements of the batch's dtype (device) */
+  int64_t n;
+  int64_t ld;
+  nb_aux aux;             /* the group's side arrays (zero when none) */
+  uint8_t* label;         /* n */
+  float* margin;          /* n */
+  float* logpost;         /* n x C, or NULL when want_logpost is 0 */
+} nb_group;
+
+typedef struct nb_batch nb_batch;
+
+NB_API nb_status nb_batch_create(const nb_model* const* models, int n_models, nb_dtype dtype,
+                                 int64_t max_ld, int max_groups, const nb_score_opts* opts,
+                                 nb_batch** out);
+NB_API nb_status nb_batch_score(nb_batch* batch, const nb_group* groups, int n_groups,
+                                void* cuda_stream, int64_t* n_rechecked);
+NB_API nb_status nb_batch_capture(nb_batch* batch, void* cuda_stream);
+NB_API void nb_batch_destroy(nb_batch* batch);
+
+/* ---- serving: continuous batching of arriving groups ----------------------
+ * The paper classifies the files of each group with the group's model
+ * (Sec. 3, Sec. 4); a server keeps the models resident and classifies groups
+ * as they arrive.  It owns a device memory budget and a host worker thread.
+ * Groups are submitted with nb_classify_stream (asynchronous: it returns a
+ * ticket at once) and admitted in arrival order while the budget has room for
+ * their staged bytes; a group whose X is host memory is copied to the device
+ * on a copy stream as soon as it is admitted.  Each step of the worker scores
+ * the groups admitted since the last step (at most max_slots) in one batch
+ * (nb_batch_*, replayed from a captured graph) while up to one earlier step
+ * still runs on the GPU, copies results bound for host memory back, and
+ * completes the tickets of finished steps.  Results equal nb_score_group on
+ * the group alone.
+ *
+ * nb_server_create: models (multinomial, same F, <= 8), the storage dtype of
+ *   submitted groups (dense rows, ld = F, no side arrays), the device memory
+ *   budget in bytes for staged inputs and outputs (0 = 1 GiB), the most
+ *   groups per step (max_slots, the batch size bound), score options.
+ * nb_classify_stream: model_id = slot in models; X host or device (n x F);
+ *   label / margin / logpost (n x C, or NULL) all device memory (written by
+ *   the kernels), all page-locked host memory (written by copies), or host
+ *   memory of any kind (staged in the server's page-locked pool and copied
+ *   by the worker); they must stay valid until the ticket completes.
+ *   NB_EBUSY if the group alone exceeds the budget; NB_EINVAL for outputs
+ *   that mix device and host memory.
+ * nb_wait: waits for a ticket; NB_ETIMEOUT after timeout_us (< 0: no limit).
+ * nb_server_stats: latency percentiles (arrival to completion, microseconds)
+ *   and files per second over the completed tickets (any pointer may be NULL).
+ * nb_server_destroy: drains the queue, stops the worker, frees everything. */
+NB_API nb_status nb_server_create(const nb_model* const* models, int n_models, nb_dtype dtype,
+                                  size_t mem_budget, int max_slots, const nb_score_opts* opts,
+                                  nb_server** out);
+NB_API nb_status nb_classify_stream(nb_server* server, int model_id, const void* X, int64_t n,
+                                    int32_t F, uint8_t* label, float* margin, float* logpost,
+                                    uint64_t* ticket);
+/* Submit `count` groups in one call (same rules as nb_classify_stream, one
+ * entry per group in each array; logpost may be NULL).  arrival_us (or NULL
+ * = now) gives each group's arrival time on nb_clock_us()'s clock, so a
+ * caller replaying an arrival schedule in bursts gets latencies measured from
+ * the scheduled arrivals.  On an error, groups before the failing one stay
+ * submitted and *submitted tells how many. */
+NB_API nb_status nb_classify_stream_batch(nb_server* server, int count, const int* model_ids,
+                                          const void* const* X, const int64_t* n,
+                                          uint8_t* const* label, float* const* margin,
+                                          float* const* logpost, const double* arrival_us,
+                                          uint64_t* tickets, int* submitted);
+/* The servers' steady clock in microseconds. */
+NB_API double nb_clock_us(void);
+NB_API nb_status nb_wait(nb_server* server, uint64_t ticket, int64_t timeout_us);
+NB_API nb_status nb_server_stats(nb_server* server, double* p50_us, double* p99_us,
+                                 double* files_per_s);
+NB_API void nb_server_destroy(nb_server* server);
+
 /* ---- tile configuration and autotuning -----------------------------------
  * nb_set_tile_config / nb_get_tile_config: set or read a model's scorer
  * configuration (see nb_tile_config).

@@ -53,6 +53,11 @@ class NbTileConfig(ctypes.Structure):
 NB_VARIANT_AUTO, NB_VARIANT_PIPELINED, NB_VARIANT_REGISTER = 0, 1, 2
 
 
+class NbGroup(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("X", _P), ("n", _i64), ("ld", _i64), ("aux", NbAux),
+                ("label", _P), ("margin", _P), ("logpost", _P)]
+
+
 class NbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -83,6 +88,25 @@ _SIGS = [
                                          ctypes.POINTER(NbAux), _P,
                                          ctypes.POINTER(NbTileConfig),
                                          ctypes.POINTER(ctypes.c_float)]),
+    ("nb_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, _i64,
+                                       ctypes.c_int, ctypes.POINTER(NbScoreOpts),
+                                       ctypes.POINTER(_P)]),
+    ("nb_batch_score", ctypes.c_int, [_P, ctypes.POINTER(NbGroup), ctypes.c_int, _P, _P]),
+    ("nb_batch_capture", ctypes.c_int, [_P, _P]),
+    ("nb_batch_destroy", None, [_P]),
+    ("nb_server_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.POINTER(NbScoreOpts), ctypes.POINTER(_P)]),
+    ("nb_classify_stream", ctypes.c_int, [_P, ctypes.c_int, _P, _i64, _i32, _P, _P, _P,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    ("nb_classify_stream_batch", ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
+                                                _P, ctypes.POINTER(ctypes.c_int)]),
+    ("nb_clock_us", ctypes.c_double, []),
+    ("nb_wait", ctypes.c_int, [_P, ctypes.c_uint64, _i64]),
+    ("nb_server_stats", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    ("nb_server_destroy", None, [_P]),
     ("nb_pack_u8_count", ctypes.c_int, [_P, _i64, _i32, _i64, _P, ctypes.POINTER(_i64), _P]),
     ("nb_pack_u8_fill", ctypes.c_int, [_P, _i64, _i32, _i64, _P, _i64, _P, _P, _P, _P]),
     ("nb_pack_bf16", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _P, _i64, _P]),
@@ -328,6 +352,167 @@ def score(model, X, want_logpost=True, recheck=NB_RECHECK_LP, stream=None, out=N
                    want_logpost=want_logpost, recheck=recheck, aux=Xf.aux(), stream=stream,
                    n_rechecked=out["n_rechecked"].data_ptr())
     return out
+
+
+# ---- batches of groups -----------------------------------------------------
+class Batch:
+    """Many groups (each with its own model slot and outputs) per launch.
+
+    ``models``: Model objects (same F; two-class ones share one pipelined
+    launch, many-class ones one general launch).  ``score(groups)`` takes a list
+    of (slot, Features, out) where out is a dict of device tensors label,
+    margin, logpost (as returned by ``outputs``).
+    """
+
+    def __init__(self, models, dtype_code, max_ld, max_groups, want_logpost=True,
+                 recheck=NB_RECHECK_LP):
+        self.models = list(models)
+        arr = (_P * len(self.models))(*[m.handle for m in self.models])
+        opts = NbScoreOpts(int(want_logpost), int(recheck), None)
+        h = _P()
+        _check(lib().nb_batch_create(arr, len(self.models), dtype_code, max_ld, max_groups,
+                                     ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h.value
+        self.want_logpost = want_logpost
+        self._keep = []
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().nb_batch_destroy(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+    def outputs(self, slot, n, device="cuda"):
+        import torch
+        C = self.models[slot].C
+        return {"label": torch.empty(n, dtype=torch.uint8, device=device),
+                "margin": torch.empty(n, dtype=torch.float32, device=device),
+                "logpost": torch.empty((n, C), dtype=torch.float32, device=device)
+                if self.want_logpost else None}
+
+    def score(self, groups, stream=None, n_rechecked=None):
+        arr = (NbGroup * max(1, len(groups)))()
+        for i, (slot, f, out) in enumerate(groups):
+            aux = f.aux() or NbAux()
+            arr[i] = NbGroup(slot, f.data.data_ptr(), f.n, f.ld, aux, out["label"].data_ptr(),
+                             out["margin"].data_ptr(),
+                             out["logpost"].data_ptr() if out.get("logpost") is not None else None)
+        _check(lib().nb_batch_score(self.handle, arr, len(groups), _stream_ptr(stream),
+                                    n_rechecked.data_ptr() if n_rechecked is not None else None))
+
+    def capture(self, stream):
+        _check(lib().nb_batch_capture(self.handle, _stream_ptr(stream)))
+
+
+# ---- serving ----------------------------------------------------------------
+class Server:
+    """Continuous-batching server over resident models (see nb_server_create)."""
+
+    def __init__(self, models, dtype_code, mem_budget=0, max_slots=64, want_logpost=True,
+                 recheck=NB_RECHECK_LP):
+        self.models = list(models)
+        arr = (_P * len(self.models))(*[m.handle for m in self.models])
+        opts = NbScoreOpts(int(want_logpost), int(recheck), None)
+        h = _P()
+        _check(lib().nb_server_create(arr, len(self.models), dtype_code, int(mem_budget),
+                                      int(max_slots), ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h.value
+        self.want_logpost = want_logpost
+        self.F = self.models[0].F
+
+    def close(self):
+        if self.handle:
+            lib().nb_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, model_id, n, device="cpu", pin=True):
+        import torch
+        C = self.models[model_id].C
+        kw = {"device": device}
+        mk = (lambda t: t.pin_memory()) if (device == "cpu" and pin) else (lambda t: t)
+        return {"label": mk(torch.empty(n, dtype=torch.uint8, **kw)),
+                "margin": mk(torch.empty(n, dtype=torch.float32, **kw)),
+                "logpost": mk(torch.empty((n, C), dtype=torch.float32, **kw))
+                if self.want_logpost else None}
+
+    def submit(self, model_id, X, out):
+        """X: (n x F) tensor on the host (pinned preferred) or the device."""
+        t = ctypes.c_uint64(0)
+        lp = out["logpost"].data_ptr() if out.get("logpost") is not None else None
+        _check(lib().nb_classify_stream(self.handle, model_id, X.data_ptr(), X.shape[0],
+                                        X.shape[1], out["label"].data_ptr(),
+                                        out["margin"].data_ptr(), lp, ctypes.byref(t)))
+        return t.value
+
+    def submit_many(self, items, arrival_us=None):
+        """items: list of (model_id, X, out) as for submit; arrival_us: optional
+        list of scheduled arrival times on clock_us()'s clock.  Returns tickets."""
+        k = len(items)
+        if k == 0:
+            return []
+        mids = (ctypes.c_int * k)(*[m for m, _, _ in items])
+        xs = (_P * k)(*[X.data_ptr() for _, X, _ in items])
+        ns = (_i64 * k)(*[X.shape[0] for _, X, _ in items])
+        for _, X, _ in items:
+            if X.dim() != 2 or X.shape[1] != self.F:
+                raise NbError(NB_EINVAL, "submit_many: every X must be (n x F)")
+        lab = (_P * k)(*[o["label"].data_ptr() for _, _, o in items])
+        mar = (_P * k)(*[o["margin"].data_ptr() for _, _, o in items])
+        lps = (_P * k)(*[o["logpost"].data_ptr() if o.get("logpost") is not None else None
+                         for _, _, o in items]) if self.want_logpost else None
+        arr = (ctypes.c_double * k)(*arrival_us) if arrival_us is not None else None
+        tk = (ctypes.c_uint64 * k)()
+        done = ctypes.c_int(0)
+        _check(lib().nb_classify_stream_batch(self.handle, k, mids, xs, ns, lab, mar, lps, arr,
+                                              tk, ctypes.byref(done)))
+        return list(tk)
+
+    def submit_raw(self, model_ids, x_ptrs, n, label_ptrs, margin_ptrs, logpost_ptrs,
+                   arrival_us=None):
+        """Low-overhead burst submission from contiguous numpy arrays (int32
+        model ids, uint64 pointers, int64 row counts, float64 arrival times);
+        every pointer must address memory of the required size."""
+        import numpy as np
+        k = int(len(model_ids))
+        if k == 0:
+            return np.zeros(0, dtype=np.uint64)
+        arrs = [np.ascontiguousarray(a, dtype=t) for a, t in
+                ((model_ids, np.int32), (x_ptrs, np.uint64), (n, np.int64),
+                 (label_ptrs, np.uint64), (margin_ptrs, np.uint64))]
+        if any(len(a) != k for a in arrs):
+            raise NbError(NB_EINVAL, "submit_raw: arrays of different lengths")
+        lp = (np.ascontiguousarray(logpost_ptrs, dtype=np.uint64)
+              if logpost_ptrs is not None else None)
+        arr = (np.ascontiguousarray(arrival_us, dtype=np.float64)
+               if arrival_us is not None else None)
+        tk = np.zeros(k, dtype=np.uint64)
+        done = ctypes.c_int(0)
+        _check(lib().nb_classify_stream_batch(
+            self.handle, k, *[a.ctypes.data for a in arrs[:3]], arrs[3].ctypes.data,
+            arrs[4].ctypes.data, lp.ctypes.data if lp is not None else None,
+            arr.ctypes.data if arr is not None else None, tk.ctypes.data, ctypes.byref(done)))
+        return tk
+
+    @staticmethod
+    def clock_us():
+        return lib().nb_clock_us()
+
+    def wait(self, ticket, timeout_us=-1):
+        _check(lib().nb_wait(self.handle, ticket, int(timeout_us)))
+
+    def stats(self):
+        a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(lib().nb_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                     ctypes.byref(c)))
+        return {"p50_us": a.value, "p99_us": b.value, "files_per_s": c.value}
 
 
 # ---- packing ---------------------------------------------------------------
