@@ -119,10 +119,14 @@ typedef struct {
 typedef struct nb_model nb_model;
 typedef struct nb_server nb_server;
 
-/* Kernel configuration of a model's two-class scorer.
- *   variant  NB_VARIANT_AUTO: TMA-pipelined kernel when the row fits a stage,
- *            else the register-streaming kernel;
+/* Kernel configuration of a model's scorer.
+ *   variant  two classes: NB_VARIANT_AUTO: TMA-pipelined kernel when the row
+ *            fits a stage, else the register-streaming kernel;
  *            NB_VARIANT_PIPELINED / NB_VARIANT_REGISTER: force one.
+ *            3..64 classes with u8 storage, F and ld multiples of 16:
+ *            NB_VARIANT_AUTO / NB_VARIANT_PIPELINED take the tensor-core
+ *            scorer (fixed-point weights, exact accumulation),
+ *            NB_VARIANT_REGISTER the CUDA-core scorer.
  *   stages, rows_per_stage: pipeline depth and rows per shared-memory stage
  *            (0 = defaults: stages of 16-48 KB filling ~100-180 KB per block);
  *   rows_per_warp: 1 (32 lanes per row) or 2 (16 lanes per row, more table

@@ -75,6 +75,10 @@ static nb_status alloc_model(nb_model* m) {
   const size_t o_gmu = take(m->kind == NB_GAUSSIAN ? sizeof(float) * C * Fp : 0);
   const size_t o_giv = take(m->kind == NB_GAUSSIAN ? sizeof(float) * C * Fp : 0);
   const size_t o_gk = take(sizeof(float) * C);
+  const bool tc = tc_tables(m->kind, m->C, m->F);
+  const size_t o_tcw = take(tc ? tc_w_bytes(m->C, m->F) : 0);
+  const size_t o_tcq = take(tc ? sizeof(int32_t) * C * F : 0);
+  const size_t o_tch = take(tc ? sizeof(TcHeader) : 0);
   void* mem = nullptr;
   cudaError_t e = cudaMalloc(&mem, off);
   if (e != cudaSuccess) return cuda_status(e, "cudaMalloc(model)");
@@ -102,6 +106,9 @@ static nb_status alloc_model(nb_model* m) {
   d.g_mu = m->kind == NB_GAUSSIAN ? reinterpret_cast<float*>(b + o_gmu) : nullptr;
   d.g_ivar = m->kind == NB_GAUSSIAN ? reinterpret_cast<float*>(b + o_giv) : nullptr;
   d.g_const = reinterpret_cast<float*>(b + o_gk);
+  d.tc_w = tc ? reinterpret_cast<uint8_t*>(b + o_tcw) : nullptr;
+  d.tc_q = tc ? reinterpret_cast<int32_t*>(b + o_tcq) : nullptr;
+  d.tc_hdr = tc ? reinterpret_cast<TcHeader*>(b + o_tch) : nullptr;
   return NB_OK;
 }
 
@@ -414,6 +421,8 @@ extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype d
       ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ld * es) % 16 == 0);
   if (m->kind == NB_MULTINOMIAL && m->C == 2 && aligned)
     s = launch_score2(m, X, dtype, n, ld, aux, o, st);
+  else if (tc_eligible(m, dtype, X, ld))
+    s = launch_score_tc(m, X, n, ld, aux, o, st);
   else
     s = launch_score_general(m, X, dtype, n, ld, aux, o, st);
   if (s != NB_OK) return s;

@@ -656,6 +656,7 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
         d.p0, d.log_pi, C, F, m->F_pad, d.w, d.bias, d.wmax, d.status);
     NB_TRY_CUDA(cudaGetLastError(), "k_derive_general");
   }
+  if (d.tc_w) return launch_derive_tc(m, st);
   return NB_OK;
 }
 

@@ -55,6 +55,18 @@ struct C2Header {
   int32_t pad;
 };
 
+// fixed-point scalars of the many-class tensor-core tables (one struct in HBM)
+struct TcHeader {
+  float scale;        // 2^-S: step of the fixed-point weights Q = round(w 2^S)
+  float tau_unit;     // 2^-(S+1): largest rounding error of one weight
+  int32_t S;
+  int32_t pad;
+};
+
+// tensor-core scorer limits: classes, features
+constexpr int kTcMaxC = 64;
+constexpr int kTcMaxF = 32768;
+
 // ---------------------------------------------------------------------------
 // model (library-owned)
 // ---------------------------------------------------------------------------
@@ -77,6 +89,10 @@ struct ModelDev {
   float* w;            // C x F_pad  centred weights log theta_cj - mean_c log theta_cj
   float* bias;         // C          log pi_c
   float* wmax;         // 1          max |w|
+  // many-class tensor-core tables (3 <= C <= kTcMaxC), else nullptr
+  uint8_t* tc_w;       // ceil(F/64) stages x 3*Cp x 64 FP16 limbs (MMA operand layout)
+  int32_t* tc_q;       // C x F fixed-point weights
+  TcHeader* tc_hdr;    // 1
   // Gaussian FP32 tables
   float* g_mu;         // C x F_pad
   float* g_ivar;       // C x F_pad  1 / var
@@ -135,6 +151,19 @@ nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt,
 nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt,
                          int64_t n, int64_t ld, const nb_aux* aux,
                          const ScoreOut& o, cudaStream_t st);
+
+// many-class tensor-core scorer (score_tc.cu)
+inline int tc_classes_padded(int C) { return (C + 15) / 16 * 16; }
+inline size_t tc_w_bytes(int C, int F) {
+  return (size_t)((F + 63) / 64) * 3 * tc_classes_padded(C) * 128;
+}
+inline bool tc_tables(nb_kind kind, int C, int F) {
+  return kind == NB_MULTINOMIAL && C >= 3 && C <= kTcMaxC && F <= kTcMaxF;
+}
+bool tc_eligible(const nb_model* m, nb_dtype dt, const void* X, int64_t ld);
+nb_status launch_derive_tc(nb_model* m, cudaStream_t st);
+nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t ld,
+                          const nb_aux* aux, const ScoreOut& o, cudaStream_t st);
 
 int num_sms();
 // process-wide count of kernels this library has launched

@@ -61,10 +61,6 @@ struct PipeSrc {
   int* status;
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 // Layout of the per-stage side areas after RS rows of ld_bytes each.
 inline void pipe_layout(PipeArgs& p, int rs, int stages, long long ld_bytes, bool stage_entries,
                         bool want_y, uint32_t tab_bytes, long long n) {

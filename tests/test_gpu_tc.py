@@ -1,0 +1,86 @@
+"""The many-class tensor-core scorer (tcgen05, 3 <= C <= 64 classes, u8
+storage with or without the overflow list, F a multiple of 16) against the
+FP64 oracle, element by element, and against the CUDA-core scorer of the same
+model.  Its fixed-point weights make the FP32 accumulation exact, so the
+rigorous error bound stays small and the FP64 recheck rare even in the
+log-posterior mode (Sec. 4 posterior and decision rule)."""
+import numpy as np
+import pytest
+import torch
+
+from tests._common import compare, count_matrix, oracle_mn, stored, to_np
+
+pytestmark = pytest.mark.gpu
+
+nb = pytest.importorskip("paper_1905_13746_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    nb.build()
+    nb.lib()
+
+
+def _model(fmt, X, y, C):
+    f, v = stored(X, fmt)
+    return nb.fit(f, torch.from_numpy(y).cuda(), C), v
+
+
+# (classes, features, files scored): one to several 128-file tiles with ragged
+# tails, a single 64-feature stage, partial 64- and 256-feature stages, and the
+# 64-class / 8192-feature shape of the many-class workload
+CASES = [(3, 64, 1), (3, 528, 777), (16, 2048, 3001), (17, 1024, 129), (33, 1040, 1000),
+         (64, 4096, 2560), (64, 8192, 1500)]
+
+
+@pytest.mark.parametrize("C,F,n", CASES)
+def test_tensor_scorer_matches_oracle(C, F, n):
+    X, y, _ = count_matrix(900 + C + F, 2500 + n, F, C=C, conc=0.1, clip=255)
+    model, vfit = _model("u8", X[:2500], y[:2500], C)
+    fsc, vsc = stored(X[2500:], "u8")
+    res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
+    _, ref = oracle_mn(vfit, y[:2500], C, vsc)
+    compare(res, ref)
+    # exact accumulation: only the weight quantisation bound remains
+    assert res["n_rechecked"] <= max(3, n // 100), res["n_rechecked"]
+
+
+@pytest.mark.parametrize("C,F", [(16, 1024), (5, 256)])
+def test_tensor_scorer_with_overflow_list(C, F):
+    X, y, _ = count_matrix(950 + C, 4000, F, C=C, conc=0.1, clip=65535)
+    assert (X > 255).any()
+    model, vfit = _model("u8ovf", X[:2000], y[:2000], C)
+    fsc, vsc = stored(X[2000:], "u8ovf")
+    res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
+    _, ref = oracle_mn(vfit, y[:2000], C, vsc)
+    compare(res, ref)
+
+
+@pytest.mark.parametrize("C,F", [(16, 512), (64, 1024)])
+def test_tensor_and_cuda_core_scorers_agree(C, F):
+    X, y, _ = count_matrix(970 + C, 5000, F, C=C, conc=0.1, clip=255)
+    model, vfit = _model("u8", X[:2000], y[:2000], C)
+    fsc, vsc = stored(X[2000:], "u8")
+    tc = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LABEL))
+    model.set_tile_config(nb.NB_VARIANT_REGISTER, 0, 0, 0)   # CUDA-core scorer
+    cc = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LABEL))
+    model.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
+    assert (tc["label"] == cc["label"]).all()
+    d = np.abs(tc["lp"].astype(np.float64) - cc["lp"]) / np.maximum(1.0, np.abs(cc["lp"]))
+    assert d.max() < 1e-4
+    _, ref = oracle_mn(vfit, y[:2000], C, vsc)
+    compare(tc, ref, check_lp=False)
+
+
+def test_tensor_scorer_zero_rows_and_ties():
+    # all-zero rows score the log priors alone; identical class profiles tie
+    C, F = 4, 256
+    X, y, _ = count_matrix(990, 3000, F, C=C, conc=0.1, clip=255)
+    model, vfit = _model("u8", X, y, C)
+    Z = np.zeros((300, F), np.uint8)
+    Z[::3] = X[:100]
+    fsc, vsc = stored(Z, "u8")
+    res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
+    _, ref = oracle_mn(vfit, y, C, vsc)
+    compare(res, ref)
