@@ -388,6 +388,103 @@ def run_serving(device, n_groups, loads, seed_off=0):
 
 
 # ----------------------------------------------------------------------------
+# many-class workload: C = 64 classes, F = 8192 counts, N = 2M files
+# ----------------------------------------------------------------------------
+def run_many_class(args, device):
+    """Fit on the 2:1 per-class split + score all N files on the tensor-core
+    scorer (u8 counts, fixed-point limbs); the CUDA-core scorer of the same
+    model and the plain FP32 path are timed on a subset beside it."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    import synth
+    seed = synth.seed_for(4)
+    C, F, N = 64, 8192, args.mc_n
+    p = synth.dirichlet_profiles(seed, C, F, 0.1)
+    y = synth.labels_zipf(seed + 1, N, C)
+    T = synth.file_totals(seed + 2, N, 8.5, 1.0)
+    X = torch.empty((N, F), dtype=torch.uint8, device=device)
+    synth.count_rows(seed + 3, p, y, T, 255, out_dtype="uint8", device=device, out=X,
+                     chunk_rows=1 << 15)
+    tr, _ = synth.split_per_class(seed + 4, y)
+    tr_dev = torch.as_tensor(tr, device=device)
+    Xtr = X.index_select(0, tr_dev)
+    y_dev = torch.as_tensor(y, device=device)
+    y_tr = y_dev.index_select(0, tr_dev).contiguous()
+    ftr, fall = nb.Features(Xtr, nb.NB_U8), nb.Features(X, nb.NB_U8)
+    stream = torch.cuda.Stream(device)
+    with torch.cuda.stream(stream):
+        model = nb.fit(ftr, y_tr, C, stream=stream)
+    stream.synchronize()
+    out = _out(N, C, device)
+    with ClockSampler(device.index or 0) as clk:
+        total, fit_ms, sc_ms, launches = time_steps(model, ftr, y_tr, fall, out, args.steps,
+                                                    args.warmup, stream)
+    n_rechecked = int(out["n_rechecked"].item())
+    hbm_peak, peak_kind = _peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            tflops = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        tflops = 1900.0
+    sc = statistics.mean(sc_ms)
+    bytes_ = N * F + N * (1 + 4 + 4 * C)
+    flops = 2.0 * N * F * C
+    Cp = (C + 15) // 16 * 16
+    t_mem = bytes_ / (hbm_peak * 1e9) * 1e3
+    t_flop = flops / (tflops * 1e12) * 1e3
+    # CUDA-core scorer of the same model and the plain FP32 path, on a subset
+    sub = min(N, args.mc_sub)
+    fsub = nb.Features(X[:sub], nb.NB_U8)
+    osub = _out(sub, C, device)
+
+    def time_score(f, o, reps=3):
+        with torch.cuda.stream(stream):
+            nb.score(model, f, out=o, stream=stream, recheck=nb.NB_RECHECK_LABEL)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                nb.score(model, f, out=o, stream=stream, recheck=nb.NB_RECHECK_LABEL)
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    tc_sub = time_score(fsub, osub)
+    model.set_tile_config(nb.NB_VARIANT_REGISTER, 0, 0, 0)
+    cc_sub = time_score(fsub, osub)
+    cc_rechecked = int(osub["n_rechecked"].item())
+    model.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
+    f32 = nb.Features(X[:sub].to(torch.float32), nb.NB_F32)
+    f32_sub = time_score(f32, osub)
+    del f32
+    line = {
+        "workload": f"multinomial NB, C={C} (Zipf 1.1 priors), N={N} files x F={F} counts "
+                    f"(Dirichlet(0.1) profiles, lognormal(8.5, 1) totals, clamped at 255, "
+                    f"stored u8); fit on the 2:1 split ({len(tr)} files) + score all N with "
+                    f"log posteriors and FP64 recheck",
+        "steps": args.steps, "ms_per_step": total / args.steps,
+        "files_per_s": N / (total / args.steps * 1e-3),
+        "fit_ms": statistics.mean(fit_ms), "score_ms": sc,
+        "score_files_per_s": N / (sc * 1e-3), "n_rechecked": n_rechecked,
+        "roofline": {"bound": "ridge", "kernel": "k_score_tc",
+                     "t_mem_ms": t_mem, "t_alg_flops_ms": t_flop,
+                     "frac": max(t_mem, t_flop) / sc, "hbm_peak_gbs": hbm_peak,
+                     "tensor_peak_tflops": tflops, "peak_kind": peak_kind,
+                     "achieved_gbs": bytes_ / (sc * 1e-3) / 1e9,
+                     "achieved_alg_tflops": flops / (sc * 1e-3) / 1e12,
+                     "executed_tensor_tflops": 2.0 * N * 64 * ((F + 63) // 64) * 3 * Cp
+                     / (sc * 1e-3) / 1e12},
+        "subset": {"files": sub, "tensor_core_ms": tc_sub, "cuda_core_ms": cc_sub,
+                   "cuda_core_n_rechecked_label_mode": cc_rechecked,
+                   "plain_fp32_ms": f32_sub},
+        "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    return line
+
+
+# ----------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample of the same workload)
 # ----------------------------------------------------------------------------
 def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_total):
@@ -476,6 +573,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-groups", type=int, default=4000)
+    ap.add_argument("--many-class", action="store_true",
+                    help="print only the C=64, F=8192 many-class measurement")
+    ap.add_argument("--mc-n", type=int, default=2_000_000)
+    ap.add_argument("--mc-sub", type=int, default=131072)
     ap.add_argument("--serving-only", action="store_true",
                     help="print only the serving sweep (loads 0.25/0.5/0.75/0.9)")
     args = ap.parse_args()
@@ -495,6 +596,11 @@ def main():
     device = torch.device("cuda", local)
     nb.build()
     nb.lib()
+    if args.many_class:
+        r = run_many_class(args, device)
+        if rank == 0:
+            print(json.dumps({"many_class": r}), flush=True)
+        return 0
     if args.serving_only:
         sv = run_serving(device, args.serving_groups, [0.25, 0.5, 0.75, 0.9])
         if rank == 0:

@@ -15,9 +15,9 @@
 // partial sum of one limb over 512 features is an integer of magnitude below
 // 255 * 512 * 128 < 2^24: the FP32 accumulator holds it exactly, whatever the
 // order of the tensor core's additions.  Every 512 features the accumulators
-// are drained into int32 registers (exact: |sum_j x_j q_j| <= 255 F 128 <
-// 2^31 for F <= 32768) and the limbs are combined exactly in int64 at the end,
-// overflow-list entries (counts above 255) added exactly on the CUDA cores.
+// are drained and the limbs joined into one exact int64 sum per class, kept in
+// tensor memory next to the two accumulator buffers (2 x 192 + 128 columns);
+// overflow-list entries (counts above 255) are added exactly on the CUDA cores.
 // The only errors are the weight quantisation, at most T 2^-(S+1) with T the
 // file's token count, and two FP32 roundings when the score is formed; the
 // epilogue bounds both and marks the row for the FP64 recheck when the bound
@@ -26,11 +26,15 @@
 // Roles of one persistent CTA per SM (352 threads):
 //   warps 0-7  convert u8 rows to FP16 operand tiles, drain the accumulators,
 //              run the epilogue (arg-max, top-2 margin, log-sum-exp);
-//   warp 8     streams the rows of each tile into shared memory (bulk copies);
+//   warp 8     streams each tile's rows into shared memory (2-D tensor TMA,
+//              128 rows x 128 features per box, 128-byte swizzle, zero fill
+//              past the last row and feature);
 //   warp 9     allocates tensor memory and issues the MMAs (one thread);
 //   warp 10    streams the weight-limb stages (bulk copies).
 // Every wait is bounded; a wait that runs out raises ST_TIMEOUT, all roles
 // stop, outstanding copies and MMAs are waited for, and tensor memory is freed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -43,12 +47,17 @@ namespace nbg {
 
 constexpr int TC_M = 128;                  // files per tile (tensor-memory lanes)
 constexpr int TC_KS = 64;                  // features per MMA stage (4 MMAs, K = 16)
-constexpr int TC_KR = 256;                 // features per row copy
-constexpr int TC_RAW_PITCH = TC_KR + 16;   // padded row pitch of a row stage
-constexpr int TC_CHUNK = 8;                // MMA stages per exact accumulation chunk
-constexpr int TC_NAB = 3;                  // operand stages
+constexpr int TC_KR = 128;                 // features per row stage (one TMA box)
+constexpr int TC_BOX = 128;                // features per TMA box (128-byte swizzle span)
+constexpr uint32_t TC_RAW_BYTES = TC_M * TC_KR;   // 16 KB
+constexpr int TC_CHUNK = 8;                // MMA stages per chunk of the exact mode
+constexpr float TC_T_EXACT = 131072.f;     // 128 T < 2^24: one accumulator is exact
+constexpr int TC_REDO_CAP = 64;            // tiles a CTA can queue for the exact pass
+constexpr int TC_PF = 6;                   // row stages prefetched into L2 ahead of the loads
+constexpr int TC_NAB = 4;                  // operand stages
 constexpr int TC_MAX_RAW = 4;              // row stages
-constexpr int TC_ACC_COLS = 256;           // tensor-memory columns per accumulator
+constexpr int TC_ACC_COLS = 192;           // tensor-memory columns per FP32 accumulator
+constexpr int TC_SUM_COL = 2 * TC_ACC_COLS; // exact int64 sums: 2 columns per class
 constexpr int TC_WORK = 16;                // converter / epilogue warps (4 per lane quadrant)
 constexpr int TC_PARTS = TC_WORK / 4;      // class parts per row
 constexpr int TC_CLS = 16;                 // classes per part (kTcMaxC = TC_PARTS * TC_CLS)
@@ -66,27 +75,36 @@ struct TcModelArg {
 };
 
 struct TcArgs {
+  CUtensorMap tmap;         // u8 rows of the group (single-group launch)
   const SegGroup* groups;   // group list on the device, or nullptr: g0 alone
   const SegHeader* hdr;     // its header (tiles = 128-row tiles of the list)
   SegGroup g0;
   long long tiles0;
   TcModelArg models[kSegMaxModels];
   int F, nks, nraw, want_lp, recheck;
+  int single;               // 1: one accumulation per row, heavy rows redone exactly
+  int cs;                   // CTAs per cluster sharing each weight stage (multicast)
   uint32_t b_bytes;         // bytes of one weight stage (largest model)
   int* status;
 };
 
-struct TcXch {               // per row and half: partial epilogue results
-  float best, second, se, smax, bmax, T;
-  int idx, pad;
+struct TcXch {               // partial epilogue results of each class part and row
+  float best[TC_PARTS][TC_M], second[TC_PARTS][TC_M], se[TC_PARTS][TC_M];
+  float smax[TC_PARTS][TC_M], bmax[TC_PARTS][TC_M], T[TC_PARTS][TC_M], Tplane[TC_PARTS][TC_M];
+  int idx[TC_PARTS][TC_M];
 };
 
 struct TcShared {
   uint64_t raw_full[TC_MAX_RAW], raw_empty[TC_MAX_RAW];
   uint64_t b_full[TC_NAB], a_full[TC_NAB], ab_empty[TC_NAB];
-  uint64_t acc_full[2], acc_empty[2], xb[2], fin;
+  uint64_t acc_full[2], acc_empty[2], fin, redo_ready;
+  uint64_t xfull, xfree;        // exchange written by all parts / read by all parts
+  uint64_t bclu_empty[TC_NAB];  // cluster leader: weight stage consumed by every CTA
   uint32_t tmem;
   int abort;
+  int redo_flag[2];
+  int redo_n;                   // tiles queued for the exact pass (phase 1)
+  int redo_list[TC_REDO_CAP];
 };
 
 struct TcTile {
@@ -107,7 +125,7 @@ __device__ __forceinline__ TcTile tc_tile(const TcArgs& a, int n_groups, long lo
   r.g = g;
   r.row0 = (t - G.tile0) * TC_M;
   const long long left = G.n - r.row0;
-  r.nr = (int)(left < TC_M ? left : TC_M);
+  r.nr = (int)(left <= 0 ? 0 : (left < TC_M ? left : TC_M));
   return r;
 }
 
@@ -135,8 +153,17 @@ __device__ __forceinline__ uint32_t u8x2_to_f16x2(uint32_t w, uint32_t sel) {
   return r;
 }
 
+// bounded wait that sleeps in the barrier instead of polling
+__device__ __forceinline__ bool tc_wait_sleep(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait_sleep(bar, parity, 100000u)) {
+    if (clock64() - t0 > TC_WAIT) return false;
+  }
+  return true;
+}
+
 __device__ __forceinline__ bool tc_wait(TcShared& sh, uint64_t* bar, uint32_t parity, int* status) {
-  if (mbar_wait_bounded(bar, parity, TC_WAIT)) return true;
+  if (tc_wait_sleep(bar, parity)) return true;
   atomicOr(status, ST_TIMEOUT);
   *reinterpret_cast<volatile int*>(&sh.abort) = 1;
   return false;
@@ -150,7 +177,7 @@ __device__ __forceinline__ bool tc_aborted(TcShared& sh) {
 // guards); the warp follows the outcome together
 __device__ __forceinline__ bool tc_wait_warp(TcShared& sh, uint64_t* bar, uint32_t parity,
                                              int* status) {
-  const bool mine = mbar_wait_bounded(bar, parity, TC_WAIT);
+  const bool mine = tc_wait_sleep(bar, parity);
   const bool all = __all_sync(0xFFFFFFFFu, mine) != 0;
   if (!all && (threadIdx.x & 31) == 0) {
     atomicOr(status, ST_TIMEOUT);
@@ -163,144 +190,147 @@ struct TcDrain {
   long long row0;
   uint32_t T;
   int trigger;
-  int nr, g;
+  int nr, g, tile;
   int bits;        // accumulator buffer | phase << 1 | last chunk of the tile << 2
 };
 
-// Drain one accumulation chunk into the int32 limb sums of this thread's row
-// and 16 classes; after the last chunk of a tile, form the scores and write
-// label, margin and log posteriors.
-__device__ __forceinline__ bool tc_drain(const TcArgs& a, TcShared& sh, TcXch* xch,
-                                         const TcDrain& p, int qd, int part, int lane,
-                                         uint32_t tmem, int& ep, int (&a0)[TC_CLS],
-                                         int (&a1)[TC_CLS], int (&a2)[TC_CLS]) {
+// score of class c from its exact sum q: q = hi 2^24 + lo exactly, one
+// rounding to FP32, one in the FMA with the prior
+__device__ __forceinline__ float tc_score(uint32_t lo, uint32_t hi, float scale, float b) {
+  const long long q = (long long)(((unsigned long long)hi << 32) | lo);
+  const float v = fmaf((float)(int)(q >> 24), 16777216.f, (float)(int)(q & 0xFFFFFF));
+  return fmaf(v, scale, b);
+}
+
+// Epilogue of a tile: the thread's exact sums stay in its tensor-memory lane
+// until it starts its next tile, so they are read twice, 8 classes at a time
+// (pass 1: arg-max, second best and sum of exponentials; pass 2: log
+// posteriors), which keeps the epilogue's registers small.
+__device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch* xch,
+                                            long long row0, int nr, int g, int tile,
+                                            bool check_heavy, uint32_t Tpart,
+                                            int qd, int part, int lane, uint32_t tmem,
+                                            int& ep) {
   const int r = 32 * qd + lane;
   const int F = a.F;
   const int c0 = TC_CLS * part;
-  const int buf = p.bits & 1;
-  if (!tc_wait_warp(sh, &sh.acc_full[buf], (uint32_t)(p.bits >> 1) & 1u, a.status)) return false;
-  tc_fence_after();
-  const SegGroup& G = tc_group(a, p.g);
+  const SegGroup& G = tc_group(a, g);
   const TcModelArg& M = a.models[G.model];
-  if (c0 < M.Cp) {
-    const uint32_t base =
-        tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * TC_ACC_COLS + c0);
-    uint32_t v[TC_CLS];
-    tmem_ld16(base, v);
-    tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < TC_CLS; ++i) a0[i] += __float2int_rn(__uint_as_float(v[i]));
-    tmem_ld16(base + (uint32_t)M.Cp, v);
-    tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < TC_CLS; ++i) a1[i] += __float2int_rn(__uint_as_float(v[i]));
-    tmem_ld16(base + (uint32_t)(2 * M.Cp), v);
-    tmem_ld_wait();
-#pragma unroll
-    for (int i = 0; i < TC_CLS; ++i) a2[i] += __float2int_rn(__uint_as_float(v[i]));
-  }
-  tc_fence_before();
-  __syncwarp();
-  if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
-  if (!(p.bits & 4)) return true;
-
-  // ---- epilogue of the tile: scores, arg-max, margin, log-sum-exp ----------
-  const long long gr = p.row0 + r;
-  const bool valid = r < p.nr;
-  const float scale = M.hdr->scale, tau_unit = M.hdr->tau_unit;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+  const long long gr = row0 + r;
+  const bool valid = r < nr;
   long long k0 = 0, k1 = 0;
   if (valid && G.ovf_ptr) {
     k0 = G.ovf_ptr[gr];
     k1 = G.ovf_ptr[gr + 1];
   }
-  // overflow entries (counts above 255) join the limb sums exactly: add * q_l
-  // is below 2^23, and the sums stay below 2^31 while the row has fewer than
-  // 2^24 tokens (rows with more are sent to the recheck below)
-  float T = (float)p.T;
+  const float scale = M.hdr->scale, tau_unit = M.hdr->tau_unit;
+  float T = (float)Tpart;
+  // overflow entries (counts above 255) join the sums exactly (rare path)
+  if (__any_sync(0xFFFFFFFFu, k1 > k0)) {
 #pragma unroll 1
-  for (long long k = k0; k < k1; ++k) {
-    const int j = G.ovf_col[k];
-    if (j >= F) continue;
-    const int add = G.ovf_add[k];
-    if (part == 0) T += (float)add;
+    for (int hh = 0; hh < 2; ++hh) {
+      const int cb = c0 + 8 * hh;
+      if (cb >= M.Cp) break;
+      uint32_t sw[16];
+      const uint32_t addr = lane_base + (uint32_t)(TC_SUM_COL + 2 * cb);
+      tmem_ld16(addr, sw);
+      tmem_ld_wait();
+#pragma unroll 1
+      for (long long k = k0; k < k1; ++k) {
+        const int j = G.ovf_col[k];
+        if (j >= F) continue;
+        const long long add = G.ovf_add[k];
+        if (part == 0 && hh == 0) T += (float)add;
 #pragma unroll
-    for (int i = 0; i < TC_CLS; ++i) {
-      if (c0 + i >= M.C) break;
-      const int Q = M.q[(long long)(c0 + i) * F + j];
-      const int q0 = ((Q + 128) & 255) - 128;
-      const int Q1 = (Q - q0) >> 8;
-      const int q1 = ((Q1 + 128) & 255) - 128;
-      a0[i] += add * q0;
-      a1[i] += add * q1;
-      a2[i] += add * ((Q1 - q1) >> 8);
+        for (int i = 0; i < 8; ++i) {
+          if (cb + i >= M.C) break;
+          unsigned long long x = ((unsigned long long)sw[2 * i + 1] << 32) | sw[2 * i];
+          x += (unsigned long long)(add * M.q[(long long)(cb + i) * F + j]);
+          sw[2 * i] = (uint32_t)x;
+          sw[2 * i + 1] = (uint32_t)(x >> 32);
+        }
+      }
+      __syncwarp();   // the lanes' overflow loops differ in length
+      tmem_st16(addr, sw);
+      tmem_st_wait();
     }
   }
-  // the scores replace the limb sums in a0 (as float bits)
-  float best = -INFINITY, second = -INFINITY, smax = 0.f, bmax = 0.f;
+  // pass 1
+  float best = -INFINITY, second = -INFINITY, smax = 0.f, bmax = 0.f, se = 0.f;
   int bidx = 0x7FFFFFFF;
+#pragma unroll 1
+  for (int hh = 0; hh < 2; ++hh) {
+    const int cb = c0 + 8 * hh;
+    if (cb >= M.Cp) break;
+    uint32_t sw[16];
+    tmem_ld16(lane_base + (uint32_t)(TC_SUM_COL + 2 * cb), sw);
+    tmem_ld_wait();
 #pragma unroll
-  for (int i = 0; i < TC_CLS; ++i) {
-    const int c = c0 + i;
-    float sc = -INFINITY;
-    if (c < M.C) {
-      const long long q =
-          ((long long)a2[i] << 16) + ((long long)a1[i] << 8) + (long long)a0[i];
-      // q = hi 2^24 + lo exactly; one rounding to FP32, one in the FMA
-      const float v = fmaf((float)(int)(q >> 24), 16777216.f, (float)(int)(q & 0xFFFFFF));
+    for (int i = 0; i < 8; ++i) {
+      const int c = cb + i;
+      if (c >= M.C) break;
       const float b = M.bias[c];
-      sc = fmaf(v, scale, b);
+      const float sc = tc_score(sw[2 * i], sw[2 * i + 1], scale, b);
       smax = fmaxf(smax, fabsf(sc));
       bmax = fmaxf(bmax, fabsf(b));
-      if (sc > best) {
+      if (sc > best) {            // running sum of exp(s - best)
+        se = se * expf(best - sc) + 1.f;
         second = best;
         best = sc;
         bidx = c;
-      } else if (sc > second) {
-        second = sc;
+      } else {
+        se += expf(sc - best);
+        if (sc > second) second = sc;
       }
     }
-    a0[i] = __float_as_int(sc);
-    a1[i] = 0;
-    a2[i] = 0;
   }
-  float se = 0.f;
-#pragma unroll
-  for (int i = 0; i < TC_CLS; ++i)
-    if (c0 + i < M.C) se += expf(__int_as_float(a0[i]) - best);
-  TcXch* xe = xch + (size_t)(ep & 1) * TC_M * TC_PARTS;
-  xe[r * TC_PARTS + part] = TcXch{best, second, se, smax, bmax, T, bidx, 0};
+  TcXch& xe = *xch;
+  const int eph = ep & 1;
+  // the exchange of the previous tile must have been read by every part
+  if (!tc_wait_warp(sh, &sh.xfree, (uint32_t)eph ^ 1u, a.status)) return false;
+  // the flag of the next tile of the other parity is free once xfull passes
+  if (r == 0 && part == 0) sh.redo_flag[eph ^ 1] = 0;
+  xe.best[part][r] = best;
+  xe.second[part][r] = second;
+  xe.se[part][r] = se;
+  xe.smax[part][r] = smax;
+  xe.bmax[part][r] = bmax;
+  xe.T[part][r] = T;
+  xe.Tplane[part][r] = (float)Tpart;
+  xe.idx[part][r] = bidx;
   __syncwarp();
-  if (lane == 0) mbar_arrive(&sh.xb[ep & 1]);
-  if (!tc_wait_warp(sh, &sh.xb[ep & 1], (uint32_t)((ep >> 1) & 1), a.status)) return false;
+  if (lane == 0) mbar_arrive(&sh.xfull);
+  if (!tc_wait_warp(sh, &sh.xfull, (uint32_t)eph, a.status)) return false;
   ++ep;
-  if (!valid) {
-#pragma unroll
-    for (int i = 0; i < TC_CLS; ++i) a0[i] = 0;
-    return true;
-  }
-  // combine the parts in class order (ties go to the lower class index)
-  float Bv = -INFINITY, S2 = -INFINITY, sm = 0.f, bm = 0.f, Tt = 0.f;
+  // combine the parts in class order (ties go to the lower class index); every
+  // lane stays to the end, since the tensor-memory loads below need the warp
+  // converged, and only rows of the tile store results
+  float Bv = -INFINITY, S2 = -INFINITY, sm = 0.f, bm = 0.f, Tt = 0.f, Tp = 0.f;
   int Bi = 0x7FFFFFFF;
 #pragma unroll 1
   for (int k = 0; k < TC_PARTS; ++k) {
-    const TcXch x = xe[r * TC_PARTS + k];
-    if (x.best > Bv) {
-      S2 = fmaxf(Bv, x.second);
-      Bv = x.best;
-      Bi = x.idx;
+    const float xb = xe.best[k][r];
+    Tp += xe.Tplane[k][r];
+    if (xb > Bv) {
+      S2 = fmaxf(Bv, xe.second[k][r]);
+      Bv = xb;
+      Bi = xe.idx[k][r];
     } else {
-      S2 = fmaxf(S2, x.best);
+      S2 = fmaxf(S2, xb);
     }
-    sm = fmaxf(sm, x.smax);
-    bm = fmaxf(bm, x.bmax);
-    Tt += x.T;
+    sm = fmaxf(sm, xe.smax[k][r]);
+    bm = fmaxf(bm, xe.bmax[k][r]);
+    Tt += xe.T[k][r];
   }
   float sum = 0.f;
 #pragma unroll 1
   for (int k = 0; k < TC_PARTS; ++k) {
-    const TcXch x = xe[r * TC_PARTS + k];
-    if (x.se > 0.f) sum += x.se * expf(x.best - Bv);
+    const float xs = xe.se[k][r];
+    if (xs > 0.f) sum += xs * expf(xe.best[k][r] - Bv);
   }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&sh.xfree);   // this tile's exchange is read
   const float lse = Bv + logf(sum);
   const float margin = Bv - S2;
   // |s_c - exact| <= T 2^-(S+1) (weight quantisation) + 2^-23 (|s| + |b|) (the
@@ -309,30 +339,127 @@ __device__ __forceinline__ bool tc_drain(const TcArgs& a, TcShared& sh, TcXch* x
       2.f * Tt * tau_unit * (1.f + 1.f / 1048576.f) + 2.3841858e-7f * (sm + bm) + 1e-30f;
   bool flag = false;
   if (a.recheck != NB_RECHECK_OFF) {
-    flag = !(margin > tau) || !(Tt < 16777216.f);
+    flag = !(margin > tau);
     if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
   }
-  if (part == 0) {
-    G.label[gr] = flag ? kLabelRecheck : (uint8_t)Bi;
+  // A row of 2^17 or more stored counts may have rounded in the single
+  // accumulation: it is marked for the FP64 recheck and its tile queued for the
+  // exact (chunked) pass, which overwrites the tile's results.
+  const bool heavy = check_heavy && !(Tp < TC_T_EXACT);
+  if (valid && part == 0) {
+    G.label[gr] = (flag || heavy) ? kLabelRecheck : (uint8_t)Bi;
     G.margin[gr] = margin;
+    if (heavy && atomicExch(&sh.redo_flag[eph], 1) == 0) {
+      const int k = atomicAdd(&sh.redo_n, 1);
+      if (k < TC_REDO_CAP) sh.redo_list[k] = tile;   // beyond: the FP64 recheck
+    }
   }
   if (a.want_lp && G.logpost) {
-    float* lp = G.logpost + gr * M.C;
+    // pass 2
+    float* lp = G.logpost + (valid ? gr : 0) * M.C;
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh) {
+      const int cb = c0 + 8 * hh;
+      if (cb >= M.Cp) break;
+      uint32_t sw[16];
+      tmem_ld16(lane_base + (uint32_t)(TC_SUM_COL + 2 * cb), sw);
+      tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < TC_CLS; ++i)
-      if (c0 + i < M.C) lp[c0 + i] = __int_as_float(a0[i]) - lse;
+      for (int i = 0; i < 8; ++i) {
+        const int c = cb + i;
+        if (c >= M.C) break;
+        if (valid) lp[c] = tc_score(sw[2 * i], sw[2 * i + 1], scale, M.bias[c]) - lse;
+      }
+    }
   }
-#pragma unroll
-  for (int i = 0; i < TC_CLS; ++i) a0[i] = 0;
   return true;
+}
+
+// Drain one accumulation chunk: add its three limb sums (exact integers
+// below 2^24 in FP32) into this thread's 16 exact int64 sums, which live in
+// tensor memory (2 columns per class, low word first), 8 classes at a time.
+// After the last chunk of a tile, run the epilogue.
+__device__ __forceinline__ bool tc_drain(const TcArgs& a, TcShared& sh, TcXch* xch,
+                                         const TcDrain& p, int qd, int part, int lane,
+                                         uint32_t tmem, int& ep) {
+  const int c0 = TC_CLS * part;
+  const int buf = p.bits & 1;
+  if (!tc_wait_warp(sh, &sh.acc_full[buf], (uint32_t)(p.bits >> 1) & 1u, a.status)) return false;
+  tc_fence_after();
+  const int Cp = a.models[tc_group(a, p.g).model].Cp;
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const int cb = c0 + 8 * hh;
+    if (cb < Cp) {
+      uint32_t sw[16];
+      const uint32_t sum_addr = lane_base + (uint32_t)(TC_SUM_COL + 2 * cb);
+      if (p.bits & 8) {        // first chunk of the tile
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sw[i] = 0;
+      } else {
+        tmem_ld16(sum_addr, sw);
+        tmem_ld_wait();
+      }
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        uint32_t v[8];
+        tmem_ld8(lane_base + (uint32_t)(buf * TC_ACC_COLS + l * Cp + cb), v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          unsigned long long x = ((unsigned long long)sw[2 * i + 1] << 32) | sw[2 * i];
+          x += (unsigned long long)((long long)__float2int_rn(__uint_as_float(v[i])) << (8 * l));
+          sw[2 * i] = (uint32_t)x;
+          sw[2 * i + 1] = (uint32_t)(x >> 32);
+        }
+      }
+      tmem_st16(sum_addr, sw);
+      tmem_st_wait();
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
+  if (!(p.bits & 4)) return true;
+  return tc_epilogue(a, sh, xch, p.row0, p.nr, p.g, p.tile, (p.bits & 16) != 0, p.T, qd,
+                     part, lane, tmem, ep);
+}
+
+// Tiles of this CTA: phase 0 its share of all tiles (blockIdx.x + i gridDim.x),
+// phase 1 the tiles it queued for the exact pass.
+// Phase 0 deals groups of cs consecutive tiles to the clusters in turn; CTA r
+// of a cluster takes tile r of each group (a tile past the end is a dummy that
+// reads zeros and writes nothing), so every CTA of a cluster runs through the
+// same weight stages.
+__device__ __forceinline__ long long tc_ntiles(const TcArgs& a, TcShared& sh, long long n_tiles,
+                                               int phase) {
+  if (phase) {
+    const int c = *reinterpret_cast<volatile int*>(&sh.redo_n);
+    return c < TC_REDO_CAP ? c : TC_REDO_CAP;
+  }
+  const long long ncl = gridDim.x / a.cs, k = blockIdx.x / a.cs;
+  const long long groups = (n_tiles + a.cs - 1) / a.cs;
+  return k < groups ? (groups - k + ncl - 1) / ncl : 0;
+}
+__device__ __forceinline__ long long tc_tile_at(const TcArgs& a, TcShared& sh, int phase,
+                                                long long i) {
+  if (phase) return (long long)sh.redo_list[i];
+  const long long ncl = gridDim.x / a.cs, k = blockIdx.x / a.cs;
+  return (k + i * ncl) * a.cs + blockIdx.x % a.cs;
+}
+// MMA stages per accumulation chunk: the whole row in the single-accumulation
+// phase, 512 features (always exact) otherwise
+__device__ __forceinline__ int tc_chunk(const TcArgs& a, int phase) {
+  return (a.single && phase == 0) ? a.nks : TC_CHUNK;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   TcShared& sh = *reinterpret_cast<TcShared*>(tc_smem);
-  TcXch* xch = reinterpret_cast<TcXch*>(tc_smem + 1024);   // [2][128][TC_PARTS]
-  uint8_t* raw = tc_smem + 1024 + 2 * TC_M * TC_PARTS * sizeof(TcXch);
-  uint8_t* A = raw + (size_t)a.nraw * TC_M * TC_RAW_PITCH;
+  TcXch* xch = reinterpret_cast<TcXch*>(tc_smem + 1024);
+  uint8_t* raw = tc_smem + 1024 + sizeof(TcXch);            // 1 KB aligned
+  uint8_t* A = raw + (size_t)a.nraw * TC_RAW_BYTES;
   uint8_t* B = A + (size_t)TC_NAB * TC_A_BYTES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_groups = a.groups ? a.hdr->n_groups : 1;
@@ -352,86 +479,160 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sh.acc_full[i], 1);
       mbar_init(&sh.acc_empty[i], TC_WORK);
-      mbar_init(&sh.xb[i], TC_WORK);
+
     }
     mbar_init(&sh.fin, 1);
+    mbar_init(&sh.xfull, TC_WORK);
+    mbar_init(&sh.xfree, TC_WORK);
+    mbar_init(&sh.redo_ready, TC_WORK);
+    for (int i = 0; i < TC_NAB; ++i) mbar_init(&sh.bclu_empty[i], (uint32_t)a.cs);
     sh.abort = 0;
+    sh.redo_flag[0] = sh.redo_flag[1] = 0;
+    sh.redo_n = 0;
   }
-  if (warp == TC_WORK + 1) tmem_alloc(&sh.tmem, 2 * TC_ACC_COLS);
+  if (warp == TC_WORK + 1) tmem_alloc(&sh.tmem, 512);
   tc_fence_before();
   __syncthreads();
+  if (a.cs > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
 
   if (warp == TC_WORK) {
     // ---- row producer -------------------------------------------------
     long long ri = 0, last[TC_MAX_RAW] = {-1, -1, -1, -1};
-    for (long long t = blockIdx.x; t < n_tiles && !tc_aborted(sh); t += gridDim.x) {
-      const TcTile tl = tc_tile(a, n_groups, t);
-      const SegGroup& G = tc_group(a, tl.g);
-      const char* X = G.X + tl.row0 * G.ld_bytes;
-      bool ok = true;
-      for (int f0 = 0; f0 < F; f0 += TC_KR, ++ri) {
-        const int slot = (int)(ri % a.nraw);
-        if (!tc_wait_warp(sh, &sh.raw_empty[slot], (uint32_t)((ri / a.nraw) & 1) ^ 1u,
-                          a.status)) {
-          ok = false;
-          break;
-        }
-        const uint32_t bytes = (uint32_t)(F - f0 < TC_KR ? F - f0 : TC_KR);
-        if (lane == 0) mbar_expect_tx(&sh.raw_full[slot], bytes * (uint32_t)tl.nr);
-        __syncwarp();
-        uint8_t* dst = raw + (size_t)slot * TC_M * TC_RAW_PITCH;
-        for (int r = lane; r < tl.nr; r += 32)
-          bulk_g2s(dst + r * TC_RAW_PITCH, X + r * G.ld_bytes + f0, bytes, &sh.raw_full[slot]);
-        last[slot] = ri;
+    uint32_t lastp[TC_MAX_RAW] = {0, 0, 0, 0};
+    int rs = 0;          // slot of the next row stage
+    uint32_t rp = 0;     // its phase parity
+    if ((smem_addr(raw) & 1023u) != 0) {   // the swizzled reads assume 1 KB alignment
+      if (lane == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        *reinterpret_cast<volatile int*>(&sh.abort) = 1;
       }
-      if (!ok) break;
     }
-    // the phases of a slot complete in order: wait for its last copies
-    if (lane == 0)
-      for (int s = 0; s < a.nraw; ++s)
-        if (last[s] >= 0) tc_wait(sh, &sh.raw_full[s], (uint32_t)((last[s] / a.nraw) & 1), a.status);
-  } else if (warp == TC_WORK + 2) {
-    // ---- weight-limb producer -----------------------------------------
-    long long bi = 0, last[TC_NAB] = {-1, -1, -1};
-    for (long long t = blockIdx.x; t < n_tiles && !tc_aborted(sh); t += gridDim.x) {
+    bool ok = true;
+    const uint64_t map = reinterpret_cast<uint64_t>(&a.tmap);
+    // L2 prefetch cursor of phase 0, TC_PF row stages ahead of the loads: the
+    // shared-memory stages then fill from L2, so few of them keep HBM busy
+    long long pit = 0, npf = 0;
+    int pf0 = 0;
+    const long long nt0 = tc_ntiles(a, sh, n_tiles, 0);
+    for (int phase = 0; phase < 2 && ok; ++phase) {
+     if (phase == 1 && !tc_wait_warp(sh, &sh.redo_ready, 0, a.status)) break;
+     const long long nt = tc_ntiles(a, sh, n_tiles, phase);
+     for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
+      const long long t = tc_tile_at(a, sh, phase, it);
       const TcTile tl = tc_tile(a, n_groups, t);
-      const TcModelArg& M = a.models[tc_group(a, tl.g).model];
-      const uint32_t sb = (uint32_t)M.N * 128u;
-      bool ok = true;
-      for (int ks = 0; ks < nks; ++ks, ++bi) {
-        const int slot = (int)(bi % TC_NAB);
-        if (!tc_wait_warp(sh, &sh.ab_empty[slot], (uint32_t)((bi / TC_NAB) & 1) ^ 1u,
-                          a.status)) {
+      for (int f0 = 0; f0 < F; f0 += TC_KR, ++ri) {
+        if (phase == 0 && lane == 0)
+          for (; npf < ri + TC_PF && pit < nt0; ++npf) {
+            const TcTile pt = tc_tile(a, n_groups, tc_tile_at(a, sh, 0, pit));
+#pragma unroll
+            for (int b = 0; b < TC_KR / TC_BOX; ++b)
+              asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                               map),
+                           "r"(pf0 + b * TC_BOX), "r"((int)pt.row0)
+                           : "memory");
+            pf0 += TC_KR;
+            if (pf0 >= F) {
+              pf0 = 0;
+              ++pit;
+            }
+          }
+        const int slot = rs;
+        const uint32_t rpar = rp;
+        if (++rs == a.nraw) {
+          rs = 0;
+          rp ^= 1u;
+        }
+        if (!tc_wait_warp(sh, &sh.raw_empty[slot], rpar ^ 1u, a.status)) {
           ok = false;
           break;
         }
         if (lane == 0) {
-          mbar_expect_tx(&sh.b_full[slot], sb);
-          bulk_g2s(B + (size_t)slot * a.b_bytes, M.wlay + (size_t)ks * sb, sb, &sh.b_full[slot]);
+          mbar_expect_tx(&sh.raw_full[slot], TC_RAW_BYTES);
+          uint8_t* dst = raw + (size_t)slot * TC_RAW_BYTES;
+          const int y = (int)tl.row0;
+#pragma unroll
+          for (int b = 0; b < TC_KR / TC_BOX; ++b)
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst + b * (TC_M * TC_BOX))),
+                "l"(map), "r"(f0 + b * TC_BOX), "r"(y), "r"(smem_addr(&sh.raw_full[slot]))
+                : "memory");
         }
-        last[slot] = bi;
+        last[slot] = ri;
+        lastp[slot] = rpar;
         __syncwarp();
       }
-      if (!ok) break;
+     }
+    }
+    // the phases of a slot complete in order: wait for its last copies
+    if (lane == 0)
+      for (int s = 0; s < a.nraw; ++s)
+        if (last[s] >= 0) tc_wait(sh, &sh.raw_full[s], lastp[s], a.status);
+  } else if (warp == TC_WORK + 2) {
+    // ---- weight-limb producer -----------------------------------------
+    long long bi = 0, last[TC_NAB] = {-1, -1, -1, -1};
+    bool ok = true;
+    for (int phase = 0; phase < 2 && ok; ++phase) {
+     if (phase == 1 && !tc_wait_warp(sh, &sh.redo_ready, 0, a.status)) break;
+     const long long nt = tc_ntiles(a, sh, n_tiles, phase);
+     for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
+      const TcTile tl = tc_tile(a, n_groups, tc_tile_at(a, sh, phase, it));
+      const TcModelArg& M = a.models[tc_group(a, tl.g).model];
+      const uint32_t sb = (uint32_t)M.N * 128u;
+      for (int ks = 0; ks < nks; ++ks, ++bi) {
+        const int slot = (int)((unsigned long long)bi & (TC_NAB - 1));
+        const uint32_t bpar = (uint32_t)(((unsigned long long)bi / TC_NAB) & 1);
+        if (!tc_wait_warp(sh, &sh.ab_empty[slot], bpar ^ 1u, a.status)) {
+          ok = false;
+          break;
+        }
+        int okl = 1;
+        if (lane == 0) {
+          mbar_expect_tx(&sh.b_full[slot], sb);
+          const void* src = M.wlay + (size_t)ks * sb;
+          if (a.cs == 1 || phase == 1) {
+            bulk_g2s(B + (size_t)slot * a.b_bytes, src, sb, &sh.b_full[slot]);
+          } else if (cluster_rank() == 0) {
+            // the leader refills a slot once every CTA of the cluster consumed it
+            if (tc_wait(sh, &sh.bclu_empty[slot], bpar ^ 1u, a.status))
+              bulk_g2s_multicast(B + (size_t)slot * a.b_bytes, src, sb, &sh.b_full[slot],
+                                 (uint16_t)((1u << a.cs) - 1u));
+            else
+              okl = 0;
+          }
+        }
+        last[slot] = bi;
+        if (!__shfl_sync(0xFFFFFFFFu, okl, 0)) {
+          ok = false;
+          break;
+        }
+      }
+     }
     }
     if (lane == 0)
       for (int s = 0; s < TC_NAB; ++s)
-        if (last[s] >= 0) tc_wait(sh, &sh.b_full[s], (uint32_t)((last[s] / TC_NAB) & 1), a.status);
+        if (last[s] >= 0)
+          tc_wait(sh, &sh.b_full[s], (uint32_t)(((unsigned long long)last[s] / TC_NAB) & 1),
+                  a.status);
   } else if (warp == TC_WORK + 1) {
     // ---- MMA issuer ---------------------------------------------------
     if (lane == 0) {
       long long bi = 0, di = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < n_tiles && ok && !tc_aborted(sh); t += gridDim.x) {
-        const TcTile tl = tc_tile(a, n_groups, t);
+      for (int phase = 0; phase < 2 && ok; ++phase) {
+       if (phase == 1 && !tc_wait(sh, &sh.redo_ready, 0, a.status)) break;
+       const long long nt = tc_ntiles(a, sh, n_tiles, phase);
+       const int chunk = tc_chunk(a, phase);
+       for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
+        const TcTile tl = tc_tile(a, n_groups, tc_tile_at(a, sh, phase, it));
         const TcModelArg& M = a.models[tc_group(a, tl.g).model];
         const uint32_t idesc = tc_idesc_f16(TC_M, M.N);
         uint32_t d = tmem;
-        int buf = 0;
+        int buf = 0, kc = 0;   // kc: MMA stage within the accumulation chunk
         for (int ks = 0; ks < nks; ++ks, ++bi) {
-          if (ks % TC_CHUNK == 0) {
+          if (kc == 0) {
             buf = (int)(di & 1);
             if (!tc_wait(sh, &sh.acc_empty[buf], (uint32_t)((di >> 1) & 1) ^ 1u, a.status)) {
               ok = false;
@@ -440,8 +641,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             tc_fence_after();
             d = tmem + (uint32_t)(buf * TC_ACC_COLS);
           }
-          const int slot = (int)(bi % TC_NAB);
-          const uint32_t par = (uint32_t)((bi / TC_NAB) & 1);
+          const int slot = (int)((unsigned long long)bi & (TC_NAB - 1));
+          const uint32_t par = (uint32_t)(((unsigned long long)bi / TC_NAB) & 1);
           if (!tc_wait(sh, &sh.b_full[slot], par, a.status) ||
               !tc_wait(sh, &sh.a_full[slot], par, a.status)) {
             ok = false;
@@ -453,13 +654,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
 #pragma unroll
           for (int j = 0; j < TC_KS / 16; ++j)
             tc_mma_f16(d, tc_desc(as + 256u * j, 128u, 1024u), tc_desc(bs + 256u * j, 128u, 1024u),
-                       idesc, (uint32_t)((ks % TC_CHUNK) | j));
+                       idesc, (uint32_t)(kc | j));
           tc_commit(&sh.ab_empty[slot]);
-          if (ks % TC_CHUNK == TC_CHUNK - 1 || ks == nks - 1) {
+          if (a.cs > 1 && phase == 0) tc_commit_multicast(&sh.bclu_empty[slot], 1);
+          if (++kc == chunk || ks == nks - 1) {
             tc_commit(&sh.acc_full[buf]);
             ++di;
+            kc = 0;
           }
         }
+       }
       }
       // every MMA issued so far has completed once this arrives
       tc_commit(&sh.fin);
@@ -470,45 +674,65 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
     // ---- converters / drain / epilogue (warps 0 .. TC_WORK-1) ----------
     const int qd = warp & 3, part = warp >> 2;
     const int r = 32 * qd + lane;          // tile row = tensor-memory lane
-    int a0[TC_CLS], a1[TC_CLS], a2[TC_CLS];
-#pragma unroll
-    for (int i = 0; i < TC_CLS; ++i) a0[i] = a1[i] = a2[i] = 0;
     TcDrain p0{}, p1{};      // pending drains, oldest first
     int np = 0;
     int ri = 0, bi = 0, di = 0, gs = 0, ep = 0;   // ring counters of this CTA
+    int rs = 0;          // slot of the next row stage
+    uint32_t rp = 0;     // its phase parity
     const uint32_t raw_s = smem_addr(raw), a_s = smem_addr(A);
     bool ok = true;
 
 
-    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    for (int phase = 0; phase < 2 && ok; ++phase) {
+     if (phase == 1) {
+      // every epilogue of phase 0 is done once all converter warps arrive
+      while (ok && np > 0) {
+        if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) ok = false;
+        p0 = p1;
+        --np;
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.redo_ready);
+      if (!tc_wait_warp(sh, &sh.redo_ready, 0, a.status)) break;
+     }
+     const long long nt = tc_ntiles(a, sh, n_tiles, phase);
+     const int chunk = tc_chunk(a, phase);
+     const int heavy_bit = (a.single && phase == 0) ? 16 : 0;
+     for (long long it = 0; it < nt && ok; ++it) {
+      const long long t = tc_tile_at(a, sh, phase, it);
       const TcTile tl = tc_tile(a, n_groups, t);
-      uint32_t T = 0;
-      int rslot = 0;
+      uint32_t T = 0, rpar = 0;
+      int rslot = 0, kc = 0;
       for (int ks = 0; ks < nks; ++ks) {
         if (tc_aborted(sh)) {
           ok = false;
           break;
         }
-        const int sub = ks & 3;
+        const int sub = ks & 1;   // MMA stage within the row stage
         if (sub == 0) {
-          rslot = (int)(ri % a.nraw);
-          if (!tc_wait_warp(sh, &sh.raw_full[rslot], (uint32_t)((ri / a.nraw) & 1), a.status)) {
+          rslot = rs;
+          rpar = rp;
+          if (++rs == a.nraw) {
+            rs = 0;
+            rp ^= 1u;
+          }
+          if (!tc_wait_warp(sh, &sh.raw_full[rslot], rpar, a.status)) {
             ok = false;
             break;
           }
         }
-        const int slot = (int)(bi % TC_NAB);
-        if (!tc_wait_warp(sh, &sh.ab_empty[slot], (uint32_t)((bi / TC_NAB) & 1) ^ 1u,
-                          a.status)) {
+        const int slot = bi & (TC_NAB - 1);
+        if (!tc_wait_warp(sh, &sh.ab_empty[slot], ((uint32_t)bi / TC_NAB & 1u) ^ 1u, a.status)) {
           ok = false;
           break;
         }
         // row r, features ks*64 + 16 part .. +15 -> core matrices 2 part, 2 part + 1
-        const int f0 = ks * TC_KS + 16 * part;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (r < tl.nr && f0 < F)
-          v = lds16(raw_s + (uint32_t)(rslot * TC_M * TC_RAW_PITCH + r * TC_RAW_PITCH +
-                                       sub * TC_KS + 16 * part));
+        // 16-byte chunk sub*4 + part of row r, swizzled by r & 7; rows and
+        // features past the end arrive as zeros
+        const int c16 = (sub << 2) + part;
+        const uint4 v = lds16(raw_s + (uint32_t)rslot * TC_RAW_BYTES +
+                              (uint32_t)(r * TC_BOX + ((c16 ^ (r & 7)) << 4)));
         T = dp4a_uu(v.x, 0x01010101u, T);
         T = dp4a_uu(v.y, 0x01010101u, T);
         T = dp4a_uu(v.z, 0x01010101u, T);
@@ -530,13 +754,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.a_full[slot]);
         ++bi;
-        if (sub == 3 || ks == nks - 1) {
+        if (sub == 1 || ks == nks - 1) {
           if (lane == 0) mbar_arrive(&sh.raw_empty[rslot]);
           ++ri;
         }
         ++gs;
         while (np > 0 && p0.trigger <= gs) {
-          if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep, a0, a1, a2)) {
+          if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) {
             ok = false;
             break;
           }
@@ -544,9 +768,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
           --np;
         }
         if (!ok) break;
-        if (ks % TC_CHUNK == TC_CHUNK - 1 || ks == nks - 1) {
+        const bool chunk_end = ++kc == chunk || ks == nks - 1;
+        if (chunk_end) {
           if (np == 2) {   // very short rows: drain the oldest before queueing
-            if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep, a0, a1, a2)) {
+            if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) {
               ok = false;
               break;
             }
@@ -557,7 +782,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
           p.row0 = tl.row0;
           p.nr = tl.nr;
           p.g = tl.g;
-          p.bits = (di & 1) | (((di >> 1) & 1) << 1) | ((ks == nks - 1) ? 4 : 0);
+          p.tile = (int)t;
+          p.bits = (di & 1) | (((di >> 1) & 1) << 1) | ((ks == nks - 1) ? 4 : 0) |
+                   (ks < chunk ? 8 : 0) | heavy_bit;
+          kc = 0;
           p.T = T;
           p.trigger = gs + TC_LAG;
           if (np == 0) p0 = p; else p1 = p;
@@ -565,17 +793,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
           ++di;
         }
       }
+     }
     }
     while (ok && np > 0) {
-      if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep, a0, a1, a2)) break;
+      if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) break;
       p0 = p1;
       --np;
     }
   }
   tc_fence_before();
   __syncthreads();
+  if (a.cs > 1) cluster_sync_all();   // no CTA leaves while others may still signal it
   tc_fence_after();
-  if (warp == TC_WORK + 1) tmem_dealloc(tmem, 2 * TC_ACC_COLS);
+  if (warp == TC_WORK + 1) tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,7 +874,7 @@ nb_status launch_derive_tc(nb_model* m, cudaStream_t st) {
 // launch
 // ---------------------------------------------------------------------------
 bool tc_eligible(const nb_model* m, nb_dtype dt, const void* X, int64_t ld) {
-  return m->kind == NB_MULTINOMIAL && m->d.tc_w != nullptr && dt == NB_U8 && m->F % 16 == 0 &&
+  return m->kind == NB_MULTINOMIAL && m->d.tc_w != nullptr && dt == NB_U8 &&
          ld % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
          m->tile.variant != NB_VARIANT_REGISTER;
 }
@@ -663,7 +893,7 @@ static TcModelArg tc_model_arg(const nb_model* m) {
 
 // shared memory of a launch whose largest model has N limb rows
 static size_t tc_smem_bytes(int nraw, int N) {
-  return 1024 + 2 * TC_M * TC_PARTS * sizeof(TcXch) + (size_t)nraw * TC_M * TC_RAW_PITCH +
+  return 1024 + sizeof(TcXch) + (size_t)nraw * TC_RAW_BYTES +
          (size_t)TC_NAB * (TC_A_BYTES + (uint32_t)N * 128u);
 }
 
@@ -684,17 +914,89 @@ static nb_status run_tc(TcArgs& a, int maxN, long long tiles_hint, cudaStream_t 
   NB_TRY_CUDA(cudaFuncSetAttribute(k_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)launch_smem),
               "cudaFuncSetAttribute(k_score_tc)");
-  long long grid = num_sms();
-  if (tiles_hint > 0 && tiles_hint < grid) grid = tiles_hint;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = launch_smem;
+  cfg.stream = st;
+  // clusters of cs CTAs share each weight stage (multicast from the leader)
+  int cs = a.cs < 1 ? 1 : a.cs;
+  int max_clusters = 0;
+  if (cs > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(num_sms() / cs * cs));
+    if (cudaOccupancyMaxActiveClusters(&max_clusters, k_score_tc, &cfg) != cudaSuccess ||
+        max_clusters < 1) {
+      cudaGetLastError();
+      cs = 1;
+    }
+  }
+  a.cs = cs;
+  if (cs == 1) {
+    long long grid = num_sms();
+    if (tiles_hint > 0 && tiles_hint < grid) grid = tiles_hint;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+  } else {
+    long long ncl = (tiles_hint + cs - 1) / cs;
+    if (ncl > max_clusters) ncl = max_clusters;
+    cfg.gridDim = dim3((unsigned)(ncl * cs));
+  }
   count_launch();
-  k_score_tc<<<(unsigned)grid, TC_THREADS, launch_smem, st>>>(a);
-  NB_TRY_CUDA(cudaGetLastError(), "k_score_tc launch");
+  NB_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_score_tc, a), "k_score_tc launch");
+  return NB_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, fetched once through the runtime
+static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D map of n rows x F u8 features (row pitch ld bytes): 128 x 128 boxes,
+// 128-byte swizzle, zero fill out of bounds
+static nb_status tc_row_map(CUtensorMap* map, const void* X, int64_t n, int F, int64_t ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tc_encode_fn();
+  if (!enc) {
+    set_error("tensor-core scorer: cuTensorMapEncodeTiled is not available");
+    return NB_ECUDA;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)F, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BOX, (cuuint32_t)TC_M};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(X), dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("tensor-core scorer: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return NB_ECUDA;
+  }
   return NB_OK;
 }
 
 nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t ld,
                           const nb_aux* aux, const ScoreOut& o, cudaStream_t st) {
   TcArgs a{};
+  nb_status ms = tc_row_map(&a.tmap, X, n, m->F, ld);
+  if (ms != NB_OK) return ms;
   a.groups = nullptr;
   a.hdr = nullptr;
   SegGroup& g = a.g0;
@@ -719,6 +1021,8 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
   a.status = m->d.status;
+  a.single = 1;
+  a.cs = a.tiles0 >= 8 ? 4 : (a.tiles0 >= 4 ? 2 : 1);
   return run_tc(a, a.models[0].N, a.tiles0, st);
 }
 

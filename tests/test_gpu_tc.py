@@ -1,5 +1,5 @@
 """The many-class tensor-core scorer (tcgen05, 3 <= C <= 64 classes, u8
-storage with or without the overflow list, F a multiple of 16) against the
+storage with or without the overflow list, row pitch a multiple of 16 bytes) against the
 FP64 oracle, element by element, and against the CUDA-core scorer of the same
 model.  Its fixed-point weights make the FP32 accumulation exact, so the
 rigorous error bound stays small and the FP64 recheck rare even in the
@@ -30,8 +30,8 @@ def _model(fmt, X, y, C):
 # (classes, features, files scored): one to several 128-file tiles with ragged
 # tails, a single 64-feature stage, partial 64- and 256-feature stages, and the
 # 64-class / 8192-feature shape of the many-class workload
-CASES = [(3, 64, 1), (3, 528, 777), (16, 2048, 3001), (17, 1024, 129), (33, 1040, 1000),
-         (64, 4096, 2560), (64, 8192, 1500)]
+CASES = [(3, 64, 1), (3, 528, 777), (5, 1000, 300), (16, 2048, 3001), (17, 1024, 129),
+         (33, 1040, 1000), (64, 4096, 2560), (64, 8192, 1500)]
 
 
 @pytest.mark.parametrize("C,F,n", CASES)
@@ -84,3 +84,21 @@ def test_tensor_scorer_zero_rows_and_ties():
     res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
     _, ref = oracle_mn(vfit, y, C, vsc)
     compare(res, ref)
+
+
+def test_tensor_scorer_heavy_rows_redone_exactly():
+    # rows with 2^17 or more stored counts leave the single-accumulation pass
+    # and are scored again with exact 512-feature chunks
+    C, F = 8, 1024
+    X, y, _ = count_matrix(995, 6000, F, C=C, conc=0.1, clip=255)
+    rng = np.random.default_rng(7)
+    heavy = rng.choice(np.arange(3000, 6000), 400, replace=False)
+    X[heavy] = rng.integers(150, 256, size=(400, F))        # >= 153,600 counts
+    model, vfit = _model("u8", X[:3000], y[:3000], C)
+    fsc, vsc = stored(X[3000:], "u8")
+    _, ref = oracle_mn(vfit, y[:3000], C, vsc)
+    res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
+    compare(res, ref)
+    lab = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LABEL))
+    compare(lab, ref, check_lp=False)
+    assert lab["n_rechecked"] <= 30, lab["n_rechecked"]
