@@ -1,8 +1,11 @@
 // Batches of file groups: the host side of the segmented launches.
 //
 // A batch holds the resident models (two-class ones go to the pipelined
-// two-class kernel, the others to the general kernel), a device work list
-// (two headers + two descriptor lists) and two pinned host copies of it.
+// two-class kernel; the others to the tensor-core kernel when the group
+// allows it -- u8 rows, 16-byte aligned, a model with tensor tables -- else to
+// the general kernel), a device work list (three headers, three descriptor
+// lists and the tensor maps of the tensor-core groups) and two pinned host
+// copies of it.
 // nb_batch_score writes the groups into the next host copy, copies it to the
 // device and launches (or replays the captured graphs of) the scoring kernels
 // and the FP64 recheck: a fixed number of launches whatever the number of
@@ -17,9 +20,12 @@
 
 namespace nbg {
 
+constexpr int kFamilies = 3;
+
 struct WorkList {   // device and host layout of one work list buffer
-  SegHeader hdr[2];
-  // followed by SegGroup lists[2][max_groups]
+  SegHeader hdr[kFamilies];
+  // followed by SegGroup lists[kFamilies][max_groups], then 128-byte tensor
+  // maps [max_groups] (128-byte aligned)
 };
 
 }  // namespace nbg
@@ -31,9 +37,11 @@ struct nb_batch {
   int F, F_pad;
   int max_groups;
   int want_lp, recheck;
-  // family 0 (two-class pipelined) and family 1 (general) models
-  std::vector<const nb_model*> fam[2];
-  std::vector<int> slot_family, slot_index;   // batch slot -> (family, index)
+  // family 0 (two-class pipelined), 1 (general) and 2 (tensor-core) models;
+  // a many-class slot sits in family 1 and, with tensor tables, in family 2
+  std::vector<const nb_model*> fam[kFamilies];
+  std::vector<int> slot_family, slot_index, slot_index2;   // slot -> family, indices
+  size_t maps_off = 0;
   // two-class launch plan
   PipeArgs plan{};
   int kv = 0, ncw = 0, smem = 0;
@@ -53,7 +61,7 @@ struct nb_batch {
 
 static SegHeader* hdr_of(void* base) { return static_cast<SegHeader*>(base); }
 static SegGroup* list_of(void* base, int fam, int max_groups) {
-  return reinterpret_cast<SegGroup*>(static_cast<char*>(base) + 2 * sizeof(SegHeader)) +
+  return reinterpret_cast<SegGroup*>(static_cast<char*>(base) + kFamilies * sizeof(SegHeader)) +
          (size_t)fam * max_groups;
 }
 
@@ -75,8 +83,15 @@ static nb_status batch_launch(nb_batch* b, cudaStream_t st) {
                                        b->want_lp, b->recheck, b->status, st);
     if (s != NB_OK) return s;
   }
+  if (!b->fam[2].empty()) {
+    nb_status s = launch_score_tc_seg(list_of(b->dev, 2, b->max_groups), dh + 2,
+                                      static_cast<char*>(b->dev) + b->maps_off,
+                                      b->fam[2].data(), (int)b->fam[2].size(), b->F, b->want_lp,
+                                      b->recheck, b->status, st);
+    if (s != NB_OK) return s;
+  }
   if (b->recheck != NB_RECHECK_OFF) {
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < kFamilies; ++f) {
       if (b->fam[f].empty()) continue;
       nb_status s = launch_recheck_seg(list_of(b->dev, f, b->max_groups), dh + f,
                                        b->fam[f].data(), (int)b->fam[f].size(), b->dtype, b->F,
@@ -124,6 +139,12 @@ extern "C" nb_status nb_batch_create(const nb_model* const* models, int n_models
     b->slot_family.push_back(f);
     b->slot_index.push_back((int)b->fam[f].size());
     b->fam[f].push_back(models[i]);
+    int i2 = -1;
+    if (f == 1 && dtype == NB_U8 && models[i]->d.tc_w) {
+      i2 = (int)b->fam[2].size();
+      b->fam[2].push_back(models[i]);
+    }
+    b->slot_index2.push_back(i2);
   }
   auto fail = [&](nb_status s) {
     nb_batch_destroy(b);
@@ -135,7 +156,9 @@ extern "C" nb_status nb_batch_create(const nb_model* const* models, int n_models
                             &b->kv, &b->ncw, &b->smem);
     if (s != NB_OK) return fail(s);
   }
-  b->bytes = 2 * sizeof(SegHeader) + 2 * (size_t)max_groups * sizeof(SegGroup);
+  b->maps_off = (kFamilies * sizeof(SegHeader) + kFamilies * (size_t)max_groups * sizeof(SegGroup) +
+                 127) / 128 * 128;
+  b->bytes = b->maps_off + (b->fam[2].empty() ? 0 : (size_t)max_groups * kTcMapBytes);
   cudaError_t e = cudaMalloc(&b->dev, b->bytes + 64);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(batch)"));
   b->counter = reinterpret_cast<int64_t*>(static_cast<char*>(b->dev) + b->bytes);
@@ -185,8 +208,8 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
   NB_TRY_CUDA(cudaEventSynchronize(b->done[b->cur]), "cudaEventSynchronize");
   void* h = b->host[b->cur];
   SegHeader* hh = hdr_of(h);
-  memset(hh, 0, 2 * sizeof(SegHeader));
-  long long tiles[2] = {0, 0}, chunks[2] = {0, 0};
+  memset(hh, 0, kFamilies * sizeof(SegHeader));
+  long long tiles[kFamilies] = {0, 0, 0}, chunks[kFamilies] = {0, 0, 0};
   const long long rs = b->fam[0].empty() ? 1 : b->plan.RS;
   for (int i = 0; i < n_groups; ++i) {
     const nb_group& g = groups[i];
@@ -196,7 +219,12 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
       set_error("nb_batch_score: group %d: bad model slot, sizes or pointers", i);
       return NB_EINVAL;
     }
-    const int f = b->slot_family[g.model];
+    int f = b->slot_family[g.model];
+    // a many-class group takes the tensor-core kernel exactly when scoring it
+    // alone would, so both give the same bits
+    if (f == 1 && g.n > 0 && b->slot_index2[g.model] >= 0 &&
+        tc_group_eligible(b->fam[1][b->slot_index[g.model]], g.X, g.ld))
+      f = 2;
     if (f == 0 && g.n > 0 &&
         (((reinterpret_cast<uintptr_t>(g.X) & 15) != 0) || ((g.ld * es) % 16) != 0 ||
          g.ld * es > b->plan.xs_bytes / (rs > 0 ? rs : 1))) {
@@ -223,12 +251,18 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
     d.logpost = b->want_lp ? g.logpost : nullptr;
     d.tile0 = tiles[f];
     d.chunk0 = chunks[f];
-    d.model = b->slot_index[g.model];
+    d.model = f == 2 ? b->slot_index2[g.model] : b->slot_index[g.model];
     d.family = f;
-    tiles[f] += f == 0 ? (g.n + rs - 1) / rs : (g.n + 63) / 64;
+    if (f == 2) {
+      nb_status ms = tc_encode_rows(static_cast<char*>(h) + b->maps_off +
+                                        (size_t)(hh[2].n_groups - 1) * kTcMapBytes,
+                                    g.X, g.n, b->F, g.ld);
+      if (ms != NB_OK) return ms;
+    }
+    tiles[f] += f == 0 ? (g.n + rs - 1) / rs : (f == 1 ? (g.n + 63) / 64 : (g.n + 127) / 128);
     chunks[f] += (g.n + 31) / 32;
   }
-  for (int f = 0; f < 2; ++f) {
+  for (int f = 0; f < kFamilies; ++f) {
     hh[f].tiles = tiles[f];
     hh[f].chunks = chunks[f];
   }

@@ -141,4 +141,25 @@ struct Decode<NB_FP8E4M3> {
   }
 };
 
+// Sums four int32 values over the LPR lanes of a lane group (LPR = 16 or 32)
+// with 6 (5) shuffles instead of 4 x 5 (4): the first two steps halve the set
+// of values each lane carries.  Returns the lane's share: lanes [0, LPR/4) of
+// the group hold the sum of a0, then a1, a2 and a3 by quarter.  Integer sums
+// are exact, so the order does not matter.
+template <int LPR>
+__device__ __forceinline__ int sum4_transposed(int a0, int a1, int a2, int a3, int li) {
+  const bool h1 = (li & (LPR / 2)) != 0;
+  int k0 = h1 ? a2 : a0, k1 = h1 ? a3 : a1;
+  const int s0 = h1 ? a0 : a2, s1 = h1 ? a1 : a3;
+  k0 += __shfl_xor_sync(0xFFFFFFFFu, s0, LPR / 2);
+  k1 += __shfl_xor_sync(0xFFFFFFFFu, s1, LPR / 2);
+  const bool h2 = (li & (LPR / 4)) != 0;
+  int k = h2 ? k1 : k0;
+  const int s = h2 ? k0 : k1;
+  k += __shfl_xor_sync(0xFFFFFFFFu, s, LPR / 4);
+#pragma unroll
+  for (int off = LPR / 8; off > 0; off >>= 1) k += __shfl_xor_sync(0xFFFFFFFFu, k, off);
+  return k;
+}
+
 }  // namespace nbg

@@ -158,34 +158,37 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
       const unsigned char* rp = st + (size_t)(valid ? r : 0) * a.ld_bytes;
       RowSum mine{0, 0, 0, 0u, 0.f, 0.f};
       if (DT == NB_U8) {
-        int a0 = 0, a1 = 0, a2 = 0;
-        uint32_t tt = 0;
+        // two independent sets of the four dp4a chains (even / odd vectors)
+        int c0[2] = {0, 0}, c1[2] = {0, 0}, c2[2] = {0, 0};
+        uint32_t ct[2] = {0u, 0u};
 #pragma unroll
         for (int kv = 0; kv < KV; ++kv) {
-          const int v = li + LPR * kv;
+          const int v = li + LPR * kv, e = kv & 1;
           if (v < nv) {
             uint4 x = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
             if (v == tail_v) {
               x.x &= tm[0]; x.y &= tm[1]; x.z &= tm[2]; x.w &= tm[3];
             }
-            a0 = dp4a_us(x.x, q0[kv].x, a0);
-            a1 = dp4a_us(x.x, q1[kv].x, a1);
-            a2 = dp4a_us(x.x, q2[kv].x, a2);
-            tt = dp4a_uu(x.x, 0x01010101u, tt);
-            a0 = dp4a_us(x.y, q0[kv].y, a0);
-            a1 = dp4a_us(x.y, q1[kv].y, a1);
-            a2 = dp4a_us(x.y, q2[kv].y, a2);
-            tt = dp4a_uu(x.y, 0x01010101u, tt);
-            a0 = dp4a_us(x.z, q0[kv].z, a0);
-            a1 = dp4a_us(x.z, q1[kv].z, a1);
-            a2 = dp4a_us(x.z, q2[kv].z, a2);
-            tt = dp4a_uu(x.z, 0x01010101u, tt);
-            a0 = dp4a_us(x.w, q0[kv].w, a0);
-            a1 = dp4a_us(x.w, q1[kv].w, a1);
-            a2 = dp4a_us(x.w, q2[kv].w, a2);
-            tt = dp4a_uu(x.w, 0x01010101u, tt);
+            c0[e] = dp4a_us(x.x, q0[kv].x, c0[e]);
+            c1[e] = dp4a_us(x.x, q1[kv].x, c1[e]);
+            c2[e] = dp4a_us(x.x, q2[kv].x, c2[e]);
+            ct[e] = dp4a_uu(x.x, 0x01010101u, ct[e]);
+            c0[e] = dp4a_us(x.y, q0[kv].y, c0[e]);
+            c1[e] = dp4a_us(x.y, q1[kv].y, c1[e]);
+            c2[e] = dp4a_us(x.y, q2[kv].y, c2[e]);
+            ct[e] = dp4a_uu(x.y, 0x01010101u, ct[e]);
+            c0[e] = dp4a_us(x.z, q0[kv].z, c0[e]);
+            c1[e] = dp4a_us(x.z, q1[kv].z, c1[e]);
+            c2[e] = dp4a_us(x.z, q2[kv].z, c2[e]);
+            ct[e] = dp4a_uu(x.z, 0x01010101u, ct[e]);
+            c0[e] = dp4a_us(x.w, q0[kv].w, c0[e]);
+            c1[e] = dp4a_us(x.w, q1[kv].w, c1[e]);
+            c2[e] = dp4a_us(x.w, q2[kv].w, c2[e]);
+            ct[e] = dp4a_uu(x.w, 0x01010101u, ct[e]);
           }
         }
+        int a0 = c0[0] + c0[1], a1 = c1[0] + c1[1], a2 = c2[0] + c2[1];
+        uint32_t tt = ct[0] + ct[1];
         if (a.ovf_ptr && valid) {
           const long long k0 = sp[r], k1 = sp[r + 1];
           for (long long e = k0 + li; e < k1; e += LPR) {
@@ -202,10 +205,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
             }
           }
         }
-        mine.a0 = group_sum<LPR>(a0);
-        mine.a1 = group_sum<LPR>(a1);
-        mine.a2 = group_sum<LPR>(a2);
-        mine.t = group_sum<LPR>(tt);
+        // the group's sums end up in its four lane quarters (see sum4_transposed)
+        mine.a0 = sum4_transposed<LPR>(a0, a1, a2, (int)tt, li);
       } else {
         float acc[4] = {0.f, 0.f, 0.f, 0.f}, tf = 0.f;
 #pragma unroll
@@ -238,9 +239,18 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
       const int src = (lane - nres) * LPR;
       const bool take = lane >= nres && lane < nres + RPW && r0 + (lane - nres) < nr;
       const int sl = take ? src : 0;
-      const RowSum got{__shfl_sync(0xFFFFFFFFu, mine.a0, sl), __shfl_sync(0xFFFFFFFFu, mine.a1, sl),
-                       __shfl_sync(0xFFFFFFFFu, mine.a2, sl), __shfl_sync(0xFFFFFFFFu, mine.t, sl),
-                       __shfl_sync(0xFFFFFFFFu, mine.s, sl), __shfl_sync(0xFFFFFFFFu, mine.tf, sl)};
+      RowSum got;
+      if (DT == NB_U8) {
+        got.a0 = __shfl_sync(0xFFFFFFFFu, mine.a0, sl);
+        got.a1 = __shfl_sync(0xFFFFFFFFu, mine.a0, sl + LPR / 4);
+        got.a2 = __shfl_sync(0xFFFFFFFFu, mine.a0, sl + LPR / 2);
+        got.t = (uint32_t)__shfl_sync(0xFFFFFFFFu, mine.a0, sl + 3 * LPR / 4);
+        got.s = 0.f;
+        got.tf = 0.f;
+      } else {
+        got = RowSum{0, 0, 0, 0u, __shfl_sync(0xFFFFFFFFu, mine.s, sl),
+                     __shfl_sync(0xFFFFFFFFu, mine.tf, sl)};
+      }
       if (take) {
         res = got;
         rrow = row0 + r0 + (lane - nres);

@@ -190,34 +190,34 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
     for (int r = warp; r < nr; r += NCW) {
       if (nres == 32) finish();
       const unsigned char* rp = st + (size_t)r * ld_bytes;
-      int a0 = 0, a1 = 0, a2 = 0;
-      uint32_t tt = 0;
+      int c0[2] = {0, 0}, c1[2] = {0, 0}, c2[2] = {0, 0};   // even / odd vector chains
+      uint32_t ct[2] = {0u, 0u};
       float acc[4] = {0.f, 0.f, 0.f, 0.f}, tf = 0.f;
 #pragma unroll
       for (int kv = 0; kv < KV; ++kv) {
-        const int v = lane + 32 * kv;
+        const int v = lane + 32 * kv, e = kv & 1;
         if (v < nv) {
           uint4 x = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
           if (DT == NB_U8) {
             if (v == tail_v) {
               x.x &= tm[0]; x.y &= tm[1]; x.z &= tm[2]; x.w &= tm[3];
             }
-            a0 = dp4a_us(x.x, q0[kv].x, a0);
-            a1 = dp4a_us(x.x, q1[kv].x, a1);
-            a2 = dp4a_us(x.x, q2[kv].x, a2);
-            tt = dp4a_uu(x.x, 0x01010101u, tt);
-            a0 = dp4a_us(x.y, q0[kv].y, a0);
-            a1 = dp4a_us(x.y, q1[kv].y, a1);
-            a2 = dp4a_us(x.y, q2[kv].y, a2);
-            tt = dp4a_uu(x.y, 0x01010101u, tt);
-            a0 = dp4a_us(x.z, q0[kv].z, a0);
-            a1 = dp4a_us(x.z, q1[kv].z, a1);
-            a2 = dp4a_us(x.z, q2[kv].z, a2);
-            tt = dp4a_uu(x.z, 0x01010101u, tt);
-            a0 = dp4a_us(x.w, q0[kv].w, a0);
-            a1 = dp4a_us(x.w, q1[kv].w, a1);
-            a2 = dp4a_us(x.w, q2[kv].w, a2);
-            tt = dp4a_uu(x.w, 0x01010101u, tt);
+            c0[e] = dp4a_us(x.x, q0[kv].x, c0[e]);
+            c1[e] = dp4a_us(x.x, q1[kv].x, c1[e]);
+            c2[e] = dp4a_us(x.x, q2[kv].x, c2[e]);
+            ct[e] = dp4a_uu(x.x, 0x01010101u, ct[e]);
+            c0[e] = dp4a_us(x.y, q0[kv].y, c0[e]);
+            c1[e] = dp4a_us(x.y, q1[kv].y, c1[e]);
+            c2[e] = dp4a_us(x.y, q2[kv].y, c2[e]);
+            ct[e] = dp4a_uu(x.y, 0x01010101u, ct[e]);
+            c0[e] = dp4a_us(x.z, q0[kv].z, c0[e]);
+            c1[e] = dp4a_us(x.z, q1[kv].z, c1[e]);
+            c2[e] = dp4a_us(x.z, q2[kv].z, c2[e]);
+            ct[e] = dp4a_uu(x.z, 0x01010101u, ct[e]);
+            c0[e] = dp4a_us(x.w, q0[kv].w, c0[e]);
+            c1[e] = dp4a_us(x.w, q1[kv].w, c1[e]);
+            c2[e] = dp4a_us(x.w, q2[kv].w, c2[e]);
+            ct[e] = dp4a_uu(x.w, 0x01010101u, ct[e]);
           } else {
             float val[EPV];
             Dec::run(x, val);
@@ -238,6 +238,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
           }
         }
       }
+      int a0 = c0[0] + c0[1], a1 = c1[0] + c1[1], a2 = c2[0] + c2[1];
+      uint32_t tt = ct[0] + ct[1];
       if (DT == NB_U8 && G.ovf_ptr) {
         const long long k0 = sp[r], k1 = sp[r + 1];
         for (long long e = k0 + lane; e < k1; e += 32) {
@@ -258,14 +260,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
       uint32_t st_ = 0;
       float ss = 0.f, stf = 0.f;
       if (DT == NB_U8) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          a0 += __shfl_xor_sync(0xFFFFFFFFu, a0, off);
-          a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, off);
-          a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, off);
-          tt += __shfl_xor_sync(0xFFFFFFFFu, tt, off);
-        }
-        s0 = a0, s1 = a1, s2 = a2, st_ = tt;
+        const int k = sum4_transposed<32>(a0, a1, a2, (int)tt, lane);
+        s0 = __shfl_sync(0xFFFFFFFFu, k, 0);
+        s1 = __shfl_sync(0xFFFFFFFFu, k, 8);
+        s2 = __shfl_sync(0xFFFFFFFFu, k, 16);
+        st_ = (uint32_t)__shfl_sync(0xFFFFFFFFu, k, 24);
       } else {
         float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll

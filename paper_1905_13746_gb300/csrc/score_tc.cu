@@ -76,6 +76,7 @@ struct TcModelArg {
 
 struct TcArgs {
   CUtensorMap tmap;         // u8 rows of the group (single-group launch)
+  const CUtensorMap* maps;  // group list: one map per group (device), else nullptr
   const SegGroup* groups;   // group list on the device, or nullptr: g0 alone
   const SegHeader* hdr;     // its header (tiles = 128-row tiles of the list)
   SegGroup g0;
@@ -522,6 +523,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
      for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
       const long long t = tc_tile_at(a, sh, phase, it);
       const TcTile tl = tc_tile(a, n_groups, t);
+      // a group's map sits in the work list, rewritten between calls: drop any
+      // stale copy the tensor-map proxy may hold
+      const uint64_t tmap = a.maps ? reinterpret_cast<uint64_t>(a.maps + tl.g) : map;
+      if (a.maps && lane == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
+                     : "memory");
       for (int f0 = 0; f0 < F; f0 += TC_KR, ++ri) {
         if (phase == 0 && lane == 0)
           for (; npf < ri + TC_PF && pit < nt0; ++npf) {
@@ -529,7 +536,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
 #pragma unroll
             for (int b = 0; b < TC_KR / TC_BOX; ++b)
               asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                               map),
+                               a.maps ? reinterpret_cast<uint64_t>(a.maps + pt.g) : map),
                            "r"(pf0 + b * TC_BOX), "r"((int)pt.row0)
                            : "memory");
             pf0 += TC_KR;
@@ -557,7 +564,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                 " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst + b * (TC_M * TC_BOX))),
-                "l"(map), "r"(f0 + b * TC_BOX), "r"(y), "r"(smem_addr(&sh.raw_full[slot]))
+                "l"(tmap), "r"(f0 + b * TC_BOX), "r"(y), "r"(smem_addr(&sh.raw_full[slot]))
                 : "memory");
         }
         last[slot] = ri;
@@ -1024,6 +1031,37 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   a.single = 1;
   a.cs = a.tiles0 >= 8 ? 4 : (a.tiles0 >= 4 ? 2 : 1);
   return run_tc(a, a.models[0].N, a.tiles0, st);
+}
+
+// tensor map of a group's u8 rows for a batch work list (128 bytes at map)
+nb_status tc_encode_rows(void* map, const void* X, int64_t n, int F, int64_t ld_bytes) {
+  return tc_row_map(static_cast<CUtensorMap*>(map), X, n, F, ld_bytes);
+}
+
+bool tc_group_eligible(const nb_model* m, const void* X, int64_t ld_bytes) {
+  return tc_eligible(m, NB_U8, X, ld_bytes);
+}
+
+nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, const void* maps,
+                              const nb_model* const* models, int n_models, int F, int want_lp,
+                              int recheck, int* status, cudaStream_t st) {
+  TcArgs a{};
+  a.maps = static_cast<const CUtensorMap*>(maps);
+  a.groups = groups;
+  a.hdr = hdr;
+  int maxN = 48;
+  for (int i = 0; i < n_models && i < kSegMaxModels; ++i) {
+    a.models[i] = tc_model_arg(models[i]);
+    if (a.models[i].N > maxN) maxN = a.models[i].N;
+  }
+  a.F = F;
+  a.nks = (F + TC_KS - 1) / TC_KS;
+  a.want_lp = want_lp;
+  a.recheck = recheck;
+  a.status = status;
+  a.single = 1;
+  a.cs = 1;   // neighbouring tiles may belong to groups of different models
+  return run_tc(a, maxN, 0, st);
 }
 
 }  // namespace nbg

@@ -24,8 +24,8 @@ struct SegGroup {
   float* logpost;
   long long tile0;    // first tile of the group in its family's launch
   long long chunk0;   // first 32-row chunk of the group (recheck scan)
-  int model;          // model slot within the batch
-  int family;         // 0: two-class pipelined scorer, 1: general scorer
+  int model;          // model index within its family's model list
+  int family;         // 0: two-class pipelined, 1: general CUDA-core, 2: tensor-core
 };
 
 struct SegHeader {
@@ -69,6 +69,12 @@ nb_status launch_score2_seg(const SegArgs& a, const PipeArgs& p, nb_dtype dt, in
 nb_status launch_score_gen_seg(const SegGroup* groups, const SegHeader* hdr,
                                const nb_model* const* models, int n_models, nb_dtype dt, int F,
                                int want_lp, int recheck, int* status, cudaStream_t st);
+nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, const void* maps,
+                              const nb_model* const* models, int n_models, int F, int want_lp,
+                              int recheck, int* status, cudaStream_t st);
+nb_status tc_encode_rows(void* map, const void* X, int64_t n, int F, int64_t ld_bytes);
+bool tc_group_eligible(const nb_model* m, const void* X, int64_t ld_bytes);
+constexpr size_t kTcMapBytes = 128;
 nb_status launch_recheck_seg(const SegGroup* groups, const SegHeader* hdr,
                              const nb_model* const* models, int n_models, nb_dtype dt, int F,
                              int want_lp, int64_t* n_rechecked, cudaStream_t st);
