@@ -121,33 +121,51 @@ __device__ __forceinline__ void pipe_stage_tables(unsigned char* sm, const void*
     }
 }
 
+// Per-tile values the producer reads from global memory (the overflow
+// pointers ptr[row0 + i], i <= nr, and the labels), loaded two tiles ahead so
+// that their latency hides behind the copies of the tiles before.
+struct TilePre {
+  long long pa, pb;   // ptr[row0 + lane], ptr[row0 + 32 + lane]
+  int32_t ya, yb;     // y[row0 + lane], y[row0 + 32 + lane]
+};
+
+__device__ __forceinline__ TilePre pipe_preload(const TileInfo& t, int lane) {
+  TilePre r{0, 0, 0, 0};
+  if (t.ovf_ptr) {
+    r.pa = lane <= t.nr ? t.ovf_ptr[t.row0 + lane] : 0;
+    r.pb = lane + 32 <= t.nr ? t.ovf_ptr[t.row0 + 32 + lane] : 0;
+  }
+  if (t.y) {
+    r.ya = lane < t.nr ? t.y[t.row0 + lane] : 0;
+    r.yb = lane + 32 < t.nr ? t.y[t.row0 + 32 + lane] : 0;
+  }
+  return r;
+}
+
 // Producer warp: the whole warp calls it; lane 0 issues the copies.  `src`
-// describes tiles k = 0 .. ntl-1 of this block.  The overflow pointers of a
-// tile are loaded one tile ahead: lane i holds ptr[row0 + i] and
-// ptr[row0 + 32 + i].
+// describes tiles k = 0 .. ntl-1 of this block.
 template <class Src>
 __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
                                                    unsigned char* sm, uint64_t* full,
                                                    uint64_t* empty, long long ntl, int* status) {
   const int lane = threadIdx.x & 31;
-  long long pa = 0, pb = 0;
-  TileInfo cur;
+  TileInfo cur, nxt;
+  TilePre pc{0, 0, 0, 0}, pn{0, 0, 0, 0};
   if (ntl > 0) {
     cur = src.tile(0);
-    if (cur.ovf_ptr) {
-      pa = lane <= cur.nr ? cur.ovf_ptr[cur.row0 + lane] : 0;
-      pb = lane + 32 <= cur.nr ? cur.ovf_ptr[cur.row0 + 32 + lane] : 0;
-    }
+    pc = pipe_preload(cur, lane);
+  }
+  if (ntl > 1) {
+    nxt = src.tile(1);
+    pn = pipe_preload(nxt, lane);
   }
   for (long long k = 0; k < ntl; ++k) {
-    long long na = 0, nb = 0;
-    TileInfo nxt = cur;
-    if (k + 1 < ntl) {
-      nxt = src.tile(k + 1);
-      if (nxt.ovf_ptr) {
-        na = lane <= nxt.nr ? nxt.ovf_ptr[nxt.row0 + lane] : 0;
-        nb = lane + 32 <= nxt.nr ? nxt.ovf_ptr[nxt.row0 + 32 + lane] : 0;
-      }
+    // tile k + 2: its global values are in flight while tile k is staged
+    TileInfo nn = nxt;
+    TilePre p2{0, 0, 0, 0};
+    if (k + 2 < ntl) {
+      nn = src.tile(k + 2);
+      p2 = pipe_preload(nn, lane);
     }
     const int s = (int)(k % p.S);
     const uint32_t ph = (uint32_t)((k / p.S) & 1);
@@ -166,20 +184,21 @@ __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
     long long e0 = 0, e1 = 0;
     if (ovf) {
       long long* sp = reinterpret_cast<long long*>(st + p.ptr_off);
-      if (lane <= nr) sp[lane] = pa;
-      if (lane + 32 <= nr) sp[lane + 32] = pb;
-      e0 = __shfl_sync(0xFFFFFFFFu, pa, 0);
-      const long long tail_a = __shfl_sync(0xFFFFFFFFu, pa, nr & 31);
-      const long long tail_b = __shfl_sync(0xFFFFFFFFu, pb, nr & 31);
+      if (lane <= nr) sp[lane] = pc.pa;
+      if (lane + 32 <= nr) sp[lane + 32] = pc.pb;
+      e0 = __shfl_sync(0xFFFFFFFFu, pc.pa, 0);
+      const long long tail_a = __shfl_sync(0xFFFFFFFFu, pc.pa, nr & 31);
+      const long long tail_b = __shfl_sync(0xFFFFFFFFu, pc.pb, nr & 31);
       e1 = nr < 32 ? tail_a : tail_b;
     }
     if (cur.y) {
       // labels through registers (rows of a stage need not start 16-byte aligned)
       int32_t* sy = reinterpret_cast<int32_t*>(st + p.y_off);
-      if (lane < nr) sy[lane] = cur.y[cur.row0 + lane];
-      if (lane + 32 < nr) sy[lane + 32] = cur.y[cur.row0 + 32 + lane];
+      if (lane < nr) sy[lane] = pc.ya;
+      if (lane + 32 < nr) sy[lane + 32] = pc.yb;
     }
-    __threadfence_block();
+    // the lanes' shared-memory writes are ordered before lane 0's arrive
+    // (a release) by the warp barrier
     __syncwarp();
     if (lane == 0) {
       StageMeta* m = reinterpret_cast<StageMeta*>(st + p.meta_off);
@@ -206,9 +225,10 @@ __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
         bulk_g2s(st + p.add_off, cur.ovf_add + eb, eb_bytes, &full[s]);
       }
     }
-    pa = na;
-    pb = nb;
     cur = nxt;
+    pc = pn;
+    nxt = nn;
+    pn = p2;
   }
 }
 
