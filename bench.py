@@ -571,6 +571,9 @@ def main():
     ap.add_argument("--ref-score-rows", type=int, default=40_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile-config", default="",
+                    help="variant,stages,rows_per_stage,rows_per_warp for the two-class "
+                         "scorer instead of autotuning (e.g. 1,4,48,2)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-groups", type=int, default=4000)
     ap.add_argument("--many-class", action="store_true",
@@ -614,8 +617,13 @@ def main():
     with torch.cuda.stream(stream):
         model = nb.fit(W["low_tr"], W["y_tr"], C, stream=stream)   # validated fit
     stream.synchronize()
-    tuned, tuned_ms = ((0, 0, 0, 0), 0.0) if args.no_autotune else \
-        model.autotune(W["low_all"], stream=stream)
+    if args.tile_config:
+        tuned = tuple(int(v) for v in args.tile_config.split(","))
+        model.set_tile_config(*tuned)
+        tuned_ms = 0.0
+    else:
+        tuned, tuned_ms = ((0, 0, 0, 0), 0.0) if args.no_autotune else \
+            model.autotune(W["low_all"], stream=stream)
 
     hbm_peak, peak_kind = _peaks()
     # ---- low-precision (u8 + overflow) step, the headline -----------------
@@ -640,7 +648,7 @@ def main():
     with torch.cuda.stream(stream):
         m32 = nb.fit(f32_tr, W["y_tr"], C, stream=stream)
     stream.synchronize()
-    if not args.no_autotune:
+    if not args.no_autotune and not args.tile_config:
         m32.autotune(f32_all, stream=stream)
     p_total, p_fit, p_sc, _ = time_steps(m32, f32_tr, W["y_tr"], f32_all, out, args.steps,
                                          args.warmup, stream)
@@ -716,7 +724,7 @@ def main():
                    "storage": "u8+overflow", "weights": "22-bit fixed-point Delta, int8 limbs",
                    "l2": "inputs larger than L2 (score reads %.2f GB per step)" % (score_bytes / 1e9),
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "hbm", "kernel": "nb_score_group (k_score2_u8 + recheck scan)",
+        "roofline": {"bound": "hbm", "kernel": "nb_score_group (k_score2_pipe u8 + k_recheck scan)",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "peak_kind": peak_kind, "algorithmic_bytes": score_bytes,

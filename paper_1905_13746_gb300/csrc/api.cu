@@ -62,6 +62,7 @@ static nb_status alloc_model(nb_model* m) {
   const size_t o_lpi = take(sizeof(double) * C);
   const size_t o_gc = take(sizeof(double) * C);
   const size_t o_st = take(sizeof(int) * 4);
+  const size_t o_fin = take(sizeof(unsigned long long) * 4);
   const size_t o_c2 = take(sizeof(C2Header));
   const size_t o_delta = take(sizeof(float) * Fp);
   const size_t o_dq = take(sizeof(int32_t) * Fp);
@@ -93,6 +94,7 @@ static nb_status alloc_model(nb_model* m) {
   d.log_pi = reinterpret_cast<double*>(b + o_lpi);
   d.gconst = reinterpret_cast<double*>(b + o_gc);
   d.status = reinterpret_cast<int*>(b + o_st);
+  d.fin = reinterpret_cast<unsigned long long*>(b + o_fin);
   d.c2 = reinterpret_cast<C2Header*>(b + o_c2);
   d.delta = reinterpret_cast<float*>(b + o_delta);
   d.delta_q = reinterpret_cast<int32_t*>(b + o_dq);

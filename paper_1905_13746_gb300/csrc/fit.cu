@@ -486,6 +486,159 @@ __global__ void __launch_bounds__(1024) k_derive_c2(const double* log_theta, con
   }
 }
 
+// Two-class finish of the fit in one launch (Sec. 4 likelihoods, Laplace
+// smoothing): every block of 256 features computes the class totals N_0, N_1
+// from the exact counts, log theta of its features in FP64, Delta =
+// log theta_1 - log theta_0 and its FP32 copies, and the centred weights of
+// the general-C tables (w_c = log theta_c - mean); the blocks' maxima of
+// |Delta| meet in fin[], and the last block to finish derives the fixed-point
+// scale S and writes the integer Delta and its limbs.  fin[] (zero before the
+// launch) is cleared again by that block.
+__global__ void __launch_bounds__(256) k_fit_finish_c2(
+    const unsigned long long* counts, const unsigned long long* nc, int64_t n, int F, int F_pad,
+    int nvec8, double alpha, int prior_given, double* log_theta, double* log_pi, C2Header* hdr,
+    float* delta, int32_t* delta_q, uint4* limbs, float4* il4, float4* il8, float4* il16,
+    float* w, float* bias, float* wmax, unsigned long long* fin, int* status) {
+  __shared__ unsigned long long part[2][256];
+  __shared__ double dmax[256];
+  __shared__ float fmax32[256], wm32[256];
+  __shared__ int last;
+  const int tid = threadIdx.x;
+  unsigned long long s0 = 0, s1 = 0;
+  for (int j = tid; j < F; j += 256) {
+    s0 += counts[j];
+    s1 += counts[(int64_t)F + j];
+  }
+  part[0][tid] = s0;
+  part[1][tid] = s1;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (tid < h) {
+      part[0][tid] += part[0][tid + h];
+      part[1][tid] += part[1][tid + h];
+    }
+    __syncthreads();
+  }
+  const double ld0 = log((double)part[0][0] + alpha * (double)F);
+  const double ld1 = log((double)part[1][0] + alpha * (double)F);
+  if (blockIdx.x == 0 && tid < 2) {
+    if (!prior_given) {
+      if (nc[tid] == 0) {
+        atomicOr(status, ST_BAD_LABEL);
+        log_pi[tid] = 0.0;
+      } else {
+        log_pi[tid] = log((double)nc[tid]) - log((double)n);
+      }
+    }
+  }
+  const int j = blockIdx.x * 256 + tid;
+  double ad = 0.0;
+  float a32 = 0.f, aw = 0.f;
+  if (j < F_pad) {
+    double d = 0.0;
+    float w0 = 0.f, w1 = 0.f;
+    if (j < F) {
+      const double lt0 = log((double)counts[j] + alpha) - ld0;
+      const double lt1 = log((double)counts[(int64_t)F + j] + alpha) - ld1;
+      log_theta[j] = lt0;
+      log_theta[(int64_t)F + j] = lt1;
+      d = lt1 - lt0;
+      if (!isfinite(d)) atomicOr(status, ST_BAD_TABLE);
+      const double m = (lt0 + lt1) / 2.0;
+      w0 = (float)(lt0 - m);
+      w1 = (float)(lt1 - m);
+      ad = fabs(d);
+    }
+    const float d32 = (float)d;
+    a32 = fabsf(d32);
+    aw = fmaxf(fabsf(w0), fabsf(w1));
+    delta[j] = d32;
+    w[j] = w0;
+    w[(int64_t)F_pad + j] = w1;
+    // FP32 tables for 4 / 8 / 16 elements per vector: quad q of vector v is
+    // slot q * (F_pad / EPV) + v
+    {
+      float* t = reinterpret_cast<float*>(il4);
+      const int epv = 4, vv = j / epv, e = j % epv;
+      t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
+    }
+    {
+      float* t = reinterpret_cast<float*>(il8);
+      const int epv = 8, vv = j / epv, e = j % epv;
+      t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
+    }
+    {
+      float* t = reinterpret_cast<float*>(il16);
+      const int epv = 16, vv = j / epv, e = j % epv;
+      t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
+    }
+  }
+  dmax[tid] = ad;
+  fmax32[tid] = a32;
+  wm32[tid] = aw;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (tid < h) {
+      dmax[tid] = fmax(dmax[tid], dmax[tid + h]);
+      fmax32[tid] = fmaxf(fmax32[tid], fmax32[tid + h]);
+      wm32[tid] = fmaxf(wm32[tid], wm32[tid + h]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    // non-negative floating-point values order like their bit patterns
+    atomicMax(&fin[0], (unsigned long long)__double_as_longlong(dmax[0]));
+    atomicMax(reinterpret_cast<unsigned int*>(&fin[1]), __float_as_uint(fmax32[0]));
+    atomicMax(reinterpret_cast<unsigned int*>(&fin[1]) + 1, __float_as_uint(wm32[0]));
+    __threadfence();
+    last = atomicAdd(&fin[2], 1ull) == (unsigned long long)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const double maxabs64 = __longlong_as_double((long long)atomicAdd(&fin[0], 0ull));
+  const unsigned long long m1 = atomicAdd(&fin[1], 0ull);
+  int S = 0;
+  if (maxabs64 > 0.0) {
+    int e;
+    frexp(maxabs64, &e);   // maxabs64 < 2^e
+    S = 22 - e;
+  }
+  const double scale = ldexp(1.0, S);
+  for (int jj = tid; jj < F_pad; jj += 256) {
+    const double d = jj < F ? log_theta[(int64_t)F + jj] - log_theta[jj] : 0.0;
+    const int32_t q = (int32_t)llrint(d * scale);   // |q| <= 2^22
+    delta_q[jj] = q;
+    // balanced base-256 digits q = q2*65536 + q1*256 + q0, each in [-128, 127]
+    const int32_t q0 = ((q + 128) & 255) - 128;
+    const int32_t r1 = (q - q0) >> 8;
+    const int32_t q1 = ((r1 + 128) & 255) - 128;
+    const int32_t q2 = (r1 - q1) >> 8;
+    // u8 vectors hold 16 features; limb L of vector v is slot L * nvec8 + v,
+    // byte (jj % 16) of it
+    const int v = jj >> 4, b = jj & 15;
+    unsigned char* L = reinterpret_cast<unsigned char*>(limbs);
+    L[((size_t)0 * nvec8 + v) * 16 + b] = (unsigned char)(q0 & 255);
+    L[((size_t)1 * nvec8 + v) * 16 + b] = (unsigned char)(q1 & 255);
+    L[((size_t)2 * nvec8 + v) * 16 + b] = (unsigned char)(q2 & 255);
+  }
+  if (tid < 2) bias[tid] = (float)log_pi[tid];
+  if (tid == 0) {
+    const double b = log_pi[1] - log_pi[0];
+    hdr->b = (float)b;
+    hdr->b64 = b;
+    hdr->maxabs = __uint_as_float((unsigned int)(m1 & 0xFFFFFFFFull));
+    hdr->S = S;
+    hdr->inv_scale = (float)ldexp(1.0, -S);
+    hdr->maxabs_q = (float)maxabs64;
+    hdr->pad = 0;
+    *wmax = __uint_as_float((unsigned int)(m1 >> 32));
+    fin[0] = 0ull;
+    fin[1] = 0ull;
+    fin[2] = 0ull;
+  }
+}
+
 // general-C tables: w_cj = log theta_cj - mean_c log theta_cj (FP32), bias_c =
 // log pi_c (FP32), wmax = max |w|.  The class-independent shift cancels in
 // the margin and the log posterior.
@@ -636,6 +789,16 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
           reinterpret_cast<unsigned long long*>(d.counts), d.status);
       NB_TRY_CUDA(cudaGetLastError(), "k_counts_ovf");
     }
+  }
+  if (C == 2) {
+    count_launch();
+    k_fit_finish_c2<<<(m->F_pad + 255) / 256, 256, 0, st>>>(
+        reinterpret_cast<unsigned long long*>(d.counts),
+        reinterpret_cast<unsigned long long*>(d.nc), n, F, m->F_pad, m->nvec8, m->alpha,
+        log_prior_dev != nullptr, d.p0, d.log_pi, d.c2, d.delta, d.delta_q, d.limbs, d.il[0],
+        d.il[1], d.il[2], d.w, d.bias, d.wmax, d.fin, d.status);
+    NB_TRY_CUDA(cudaGetLastError(), "k_fit_finish_c2");
+    return NB_OK;
   }
   count_launch();
   k_finalize_mn<<<C, 256, 0, st>>>(reinterpret_cast<unsigned long long*>(d.counts),

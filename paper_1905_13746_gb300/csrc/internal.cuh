@@ -79,6 +79,7 @@ struct ModelDev {
   double* log_pi;      // C
   double* gconst;      // C          Gaussian: log pi_c - 1/2 sum_j log(2 pi var_cj)
   int* status;         // 1 int: ST_* bits raised while fitting
+  unsigned long long* fin;   // 4 words of the two-class fit finish (zero between fits)
   // two-class multinomial tables
   C2Header* c2;        // 1
   float* delta;        // F_pad      FP32 Delta, plain order
