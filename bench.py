@@ -34,6 +34,12 @@ if ROOT not in sys.path:
 METRIC = ("files/sec & HBM-roofline % at F=1024, plain FP32 vs low-prec; "
           "serving p99 latency")
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# u8 two-class scorer on the default workload, from an ncu capture of this
+# kernel at full size (summarised under profiles/); reported only for that
+# workload and tile configuration.
+SCORE_TRAFFIC = {(1_000_000, 1024, (1, 4, 48, 2)): 1_047_915_264 + 14_503_168}
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -726,7 +732,8 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": "nb_score_group (k_score2_pipe u8 + k_recheck scan)",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": SCORE_TRAFFIC.get((N, F, tuple(tuned))),
                      "peak_kind": peak_kind, "algorithmic_bytes": score_bytes,
                      "ms": sc_avg},
         "fit": {"ms": fit_avg, "algorithmic_bytes": fit_bytes,
