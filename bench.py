@@ -215,6 +215,140 @@ def time_e2e(model, host, dev, out, host_out, steps, warmup, stream):
 
 
 # ----------------------------------------------------------------------------
+# feature-count sweep and the small Gaussian workload
+# ----------------------------------------------------------------------------
+def _time_score(model, f, stream, reps=5, warm=2, recheck=None):
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    rc = nb.NB_RECHECK_LP if recheck is None else recheck
+    out = _out(f.n, model.C, f.data.device)
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            nb.score(model, f, out=out, stream=stream, recheck=rc)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            nb.score(model, f, out=out, stream=stream, recheck=rc)
+        e1.record(stream)
+        stream.synchronize()
+    return e0.elapsed_time(e1) / reps, int(out["n_rechecked"].item())
+
+
+def run_fsweep(args, device):
+    """Two classes, F in {64 .. 16384}: u8 (counts clamped at 255), FP8 E4M3 with a
+    per-row exponent, and plain FP32 rows, scored with log posteriors and the
+    FP64 recheck.  Dirichlet(0.05) profiles with 30% of the features shared."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    import synth
+    hbm_peak, _ = _peaks()
+    seed = synth.seed_for(3)
+    stream = torch.cuda.Stream(device)
+    rows = []
+    for F in (64, 256, 1024, 4096, 16384):
+        N = args.fs_n if F <= 4096 else args.fs_n // 4
+        p = synth.dirichlet_profiles(seed + F, 2, F, 0.05, shared_frac=0.3)
+        y = synth.labels_bernoulli(seed + F + 1, N)
+        T = synth.file_totals(seed + F + 2, N, 8.5, 1.0)
+        X = torch.empty((N, F), dtype=torch.uint8, device=device)
+        synth.count_rows(seed + F + 3, p, y, T, 255, out_dtype="uint8", device=device, out=X,
+                         chunk_rows=max(1024, (1 << 27) // F))
+        y_dev = torch.as_tensor(y, device=device)
+        ntr = N // 3
+        with torch.cuda.stream(stream):
+            m = nb.fit(nb.Features(X[:ntr], nb.NB_U8), y_dev[:ntr], 2, stream=stream)
+        stream.synchronize()
+        fu8 = nb.Features(X, nb.NB_U8)
+        tune_err = None
+        try:
+            m.autotune(fu8, stream=stream)
+        except nb.NbError as e:       # keep the default shape, say why
+            tune_err = str(e)
+            m.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
+        u8_ms, u8_re = _time_score(m, fu8, stream)
+        tuned = list(m.tile_config())
+        m.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
+        f8 = nb.pack_fp8(X.to(torch.float32) if N * F * 4 <= (16 << 30) else
+                         X.to(torch.int32).to(torch.uint16), stream=stream)
+        stream.synchronize()
+        # FP32 accumulation: labels guaranteed (label-mode recheck); the rows a
+        # log-posterior guarantee would send to FP64 are counted separately
+        fp8_ms, fp8_re = _time_score(m, f8, stream, recheck=nb.NB_RECHECK_LABEL)
+        _, fp8_lp = _time_score(m, f8, stream, reps=1, warm=0)
+        del f8
+        n32 = min(N, (48 << 30) // (4 * F))
+        f32 = nb.Features(X[:n32].to(torch.float32), nb.NB_F32)
+        f32_ms, f32_re = _time_score(m, f32, stream, recheck=nb.NB_RECHECK_LABEL)
+        _, f32_lp = _time_score(m, f32, stream, reps=1, warm=0)
+        del f32
+        torch.cuda.empty_cache()
+        lp = 13
+        rows.append({
+            "F": F, "N": N, "tile_config": tuned, "autotune_error": tune_err,
+            "u8": {"ms": u8_ms, "files_per_s": N / (u8_ms * 1e-3),
+                   "gbs": N * (F + lp) / (u8_ms * 1e-3) / 1e9,
+                   "frac": N * (F + lp) / (u8_ms * 1e-3) / 1e9 / hbm_peak, "n_rechecked": u8_re},
+            "fp8": {"ms": fp8_ms, "files_per_s": N / (fp8_ms * 1e-3),
+                    "gbs": N * (F + 1 + lp) / (fp8_ms * 1e-3) / 1e9,
+                    "frac": N * (F + 1 + lp) / (fp8_ms * 1e-3) / 1e9 / hbm_peak,
+                    "recheck": "label", "n_rechecked": fp8_re, "n_rechecked_lp_mode": fp8_lp},
+            "f32": {"files": n32, "ms": f32_ms, "files_per_s": n32 / (f32_ms * 1e-3),
+                    "gbs": n32 * (4 * F + lp) / (f32_ms * 1e-3) / 1e9,
+                    "frac": n32 * (4 * F + lp) / (f32_ms * 1e-3) / 1e9 / hbm_peak,
+                    "recheck": "label", "n_rechecked": f32_re, "n_rechecked_lp_mode": f32_lp}})
+        del X, fu8, m
+        torch.cuda.empty_cache()
+    return {"workload": "two classes, Dirichlet(0.05) profiles with 30% shared features, "
+                        "lognormal(8.5, 1) totals, counts clamped at 255; score with log "
+                        "posteriors; u8 with the log-posterior recheck, FP8 and FP32 with "
+                        "the label recheck", "rows": rows}
+
+
+def run_gaussian(args, device, reps=200):
+    """Gaussian NB, C = 2, F = 64: refit on 2,000 files, score 10,000 (latency-bound)."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    import synth
+    w = synth.gaussian_workload(synth.seed_for(1))
+    Xf = torch.from_numpy(w["X_fit"]).to(device)
+    yf = torch.from_numpy(w["y_fit"]).to(device)
+    Xs = torch.from_numpy(w["X_score"]).to(device)
+    stream = torch.cuda.Stream(device)
+    with torch.cuda.stream(stream):
+        m = nb.fit(nb.Features(Xf, nb.NB_F32), yf, 2, kind=nb.NB_GAUSSIAN,
+                   log_prior=list(w["log_prior"]), stream=stream)
+    stream.synchronize()
+    fs = nb.Features(Xs, nb.NB_F32)
+    out = _out(Xs.shape[0], 2, device)
+    with torch.cuda.stream(stream):
+        for _ in range(10):
+            nb.refit(m, nb.Features(Xf, nb.NB_F32), yf, log_prior=list(w["log_prior"]),
+                     no_sync=True, stream=stream)
+            nb.score(m, fs, out=out, stream=stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            nb.refit(m, nb.Features(Xf, nb.NB_F32), yf, log_prior=list(w["log_prior"]),
+                     no_sync=True, stream=stream)
+        ev[1].record(stream)
+        for _ in range(reps):
+            nb.score(m, fs, out=out, stream=stream)
+        ev[2].record(stream)
+        stream.synchronize()
+    acc = float((out["label"].cpu().numpy() == w["y_score"]).mean())
+    return {"workload": "Gaussian NB, C = 2, F = 64: fit 2,000 files, score 10,000",
+            "refit_us": ev[0].elapsed_time(ev[1]) * 1e3 / reps,
+            "score_us": ev[1].elapsed_time(ev[2]) * 1e3 / reps,
+            "score_files_per_s": Xs.shape[0] / (ev[1].elapsed_time(ev[2]) / reps * 1e-3),
+            "accuracy_vs_generating_class": acc,
+            "n_rechecked": int(out["n_rechecked"].item())}
+
+
+# ----------------------------------------------------------------------------
 # serving: Poisson arrivals of file groups, continuous batching
 # ----------------------------------------------------------------------------
 SERVE_F = 2048
@@ -582,6 +716,11 @@ def main():
                          "scorer instead of autotuning (e.g. 1,4,48,2)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-groups", type=int, default=4000)
+    ap.add_argument("--fsweep", action="store_true",
+                    help="print only the feature-count sweep (u8 / FP8 / FP32)")
+    ap.add_argument("--fs-n", type=int, default=4_000_000)
+    ap.add_argument("--gaussian", action="store_true",
+                    help="print only the small Gaussian workload")
     ap.add_argument("--many-class", action="store_true",
                     help="print only the C=64, F=8192 many-class measurement")
     ap.add_argument("--mc-n", type=int, default=2_000_000)
@@ -605,6 +744,16 @@ def main():
     device = torch.device("cuda", local)
     nb.build()
     nb.lib()
+    if args.fsweep:
+        r = run_fsweep(args, device)
+        if rank == 0:
+            print(json.dumps({"fsweep": r}), flush=True)
+        return 0
+    if args.gaussian:
+        r = run_gaussian(args, device)
+        if rank == 0:
+            print(json.dumps({"gaussian": r}), flush=True)
+        return 0
     if args.many_class:
         r = run_many_class(args, device)
         if rank == 0:

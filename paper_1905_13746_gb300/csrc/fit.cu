@@ -778,7 +778,7 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
       const size_t bins = sizeof(unsigned int) * (size_t)C * F;
       const int use_smem = bins <= 96 * 1024;
       const int smem = use_smem ? (int)bins : 0;
-      if (smem > 48 * 1024)
+      if (smem > kSmemOptIn)
         NB_TRY_CUDA(cudaFuncSetAttribute(k_counts_ovf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem),
                     "cudaFuncSetAttribute");
@@ -970,7 +970,7 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
   double* mu_all = partial + part_elems;
   double* m2_all = mu_all + F;
   const int smem = (int)(sizeof(double) * 8 * S * kGTile);
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(k_gauss_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem),
                 "cudaFuncSetAttribute");

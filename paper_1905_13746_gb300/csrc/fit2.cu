@@ -240,7 +240,7 @@ template <int DT, int KV, int kFitNCW>
 static nb_status run_fit2(const Fit2Args& f, const PipeArgs& p, int smem, cudaStream_t st) {
   auto kern = k_fit2_pipe<DT, KV, kFitNCW>;
   static int configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
+  if (smem > kSmemOptIn && configured < smem) {
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(fit2)");
     configured = smem;

@@ -31,6 +31,12 @@ enum : int {
 
 constexpr uint8_t kLabelRecheck = 255;   // internal marker in label[]
 
+// Dynamic shared memory above this size is requested through the kernel's
+// max-dynamic-shared-memory attribute; the default limit of 48 KB covers
+// dynamic and static shared memory together, and the kernels declare a few
+// static barriers.
+constexpr int kSmemOptIn = 32 * 1024;
+
 inline int elem_size(nb_dtype d) {
   switch (d) {
     case NB_F32: return 4;

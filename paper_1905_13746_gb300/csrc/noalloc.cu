@@ -106,7 +106,7 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
       y, n, C, reinterpret_cast<unsigned long long*>(d.nc), d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_label_hist");
   const int smem = (int)(sizeof(double) * 8 * S * kGTile);
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(k_gauss_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem),
                 "cudaFuncSetAttribute");

@@ -265,7 +265,7 @@ static nb_status launch_persistent(K kernel, int smem, int64_t ntiles_warp, cons
                                    cudaStream_t st) {
   static thread_local const void* last_k = nullptr;
   static thread_local int last_smem = -1, last_occ = 0;
-  if (smem > 48 * 1024) {
+  if (smem > kSmemOptIn) {
     NB_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute");
   }

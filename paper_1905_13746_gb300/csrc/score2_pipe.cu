@@ -275,7 +275,7 @@ template <int DT, int KV, int RPW, int NCW>
 static nb_status run_pipe(const S2Args& a, const PipeArgs& p, int smem, cudaStream_t st) {
   auto kern = k_score2_pipe<DT, KV, RPW, NCW>;
   static int configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
+  if (smem > kSmemOptIn && configured < smem) {
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(pipe)");
     configured = smem;

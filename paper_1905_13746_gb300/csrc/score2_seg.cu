@@ -293,7 +293,7 @@ template <int DT, int KV, int NCW>
 static nb_status run_seg(const SegArgs& a, const PipeArgs& p, int smem, int* grid,
                          cudaStream_t st) {
   auto kern = k_score2_seg<DT, KV, NCW>;
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(seg)");
   int occ = 0;

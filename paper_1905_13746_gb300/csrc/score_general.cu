@@ -435,7 +435,7 @@ nb_status launch_score_gen_seg(const SegGroup* groups, const SegHeader* hdr,
   const int C_pad = ((C_max + 3) / 4) * 4;
   const int smem =
       (int)sizeof(float) * (GBK * (GBM + 4) + GBK * (GCB + 4) + GBM * C_pad + GBM + GBM * 8);
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gen_seg, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem),
                 "cudaFuncSetAttribute(gen_seg)");
@@ -506,7 +506,7 @@ nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt, in
   const int smem =
       (int)sizeof(float) * (GBK * (GBM + 4) + GBK * (GCB + 4) + GBM * C_pad + GBM + GBM * 8);
   static int configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
+  if (smem > kSmemOptIn && configured < smem) {
     NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem > 96 * 1024 ? smem : 96 * 1024),
                 "cudaFuncSetAttribute");

@@ -278,8 +278,9 @@ def test_group_alone_equals_group_in_batch():
 # ----------------------------------------------------------------------------
 # scorer variants: pipelined (TMA stages) vs register-streaming, autotuner
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("fmt,F", [("u8ovf", 1024), ("u8ovf", 2048), ("u8", 300),
-                                   ("f32", 1024), ("u16", 1000), ("bf16", 512), ("fp8", 777)])
+@pytest.mark.parametrize("fmt,F", [("u8ovf", 1024), ("u8ovf", 2048), ("u8", 300), ("u8", 64),
+                                   ("u8", 16), ("u8", 16384), ("f32", 1024), ("f32", 64),
+                                   ("u16", 1000), ("bf16", 512), ("fp8", 777), ("fp8", 200)])
 def test_scorer_variants_agree_and_match_oracle(fmt, F):
     X, y, _ = count_matrix(800 + F, 9000, F, clip=255 if fmt == "u8" else 65535,
                            mu=6.0 if fmt == "fp8" else 8.5)
