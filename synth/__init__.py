@@ -164,3 +164,37 @@ def poisson_arrivals(seed, n, rate_per_s):
 def model_choice(seed, n, n_models=2):
     rng = np.random.default_rng(seed)
     return rng.integers(0, n_models, size=n).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# Group-wise workload: files with sizes, grouped opcode profiles
+# ----------------------------------------------------------------------------
+def groupwise_workload(seed, n, F, n_bins=100, bin_bytes=5 * 1024, C=2, conc=0.1, mix=0.5,
+                       bytes_per_opcode=16, p_malware=0.827, bin_median=12.0,
+                       bin_sigma=1.0, clip=255, out_dtype="uint8", device="cpu"):
+    """Files of Sec. 3's kind: a size window, a class, an opcode histogram.
+
+    * window w_i of ``bin_bytes`` drawn with weights ~ lognormal in the window
+      index (median ``bin_median``, log-sd ``bin_sigma``): most files are small,
+      as the paper's population below 500 KB;  size_i = w_i * bin_bytes +
+      U[0, bin_bytes);
+    * class: malware with probability ``p_malware`` (11,305 of 13,665 files in
+      the paper's data set);
+    * opcode profile of (window, class): ``mix`` x a class profile common to
+      all windows + (1 - mix) x a window-specific one, each Dirichlet(conc);
+    * opcode total T_i = max(1, size_i // bytes_per_opcode), counts
+      x_ij ~ Poisson(T_i p_j) clipped to ``clip`` (u8: 255).
+    Returns (X torch tensor n x F, y int32 numpy, sizes int64 numpy).
+    """
+    rng = np.random.default_rng(seed)
+    idx = np.arange(n_bins) + 0.5
+    w = np.exp(-0.5 * ((np.log(idx) - math.log(bin_median)) / bin_sigma) ** 2) / idx
+    win = rng.choice(n_bins, size=n, p=w / w.sum())
+    sizes = (win * bin_bytes + rng.integers(0, bin_bytes, size=n)).astype(np.int64)
+    y = (rng.random(n) < p_malware).astype(np.int32)
+    base = dirichlet_profiles(seed + 1, C, F, conc)
+    local = np.random.default_rng(seed + 2).dirichlet(np.full(F, conc), size=(n_bins, C))
+    prof = (mix * base[None, :, :] + (1.0 - mix) * local).reshape(n_bins * C, F)
+    T = np.maximum(1, sizes // bytes_per_opcode)
+    X = count_rows(seed + 3, prof, win * C + y, T, clip, out_dtype=out_dtype, device=device)
+    return X, y, sizes
