@@ -239,7 +239,9 @@ NB_API nb_status nb_score_group(const nb_model* model, const void* X, nb_dtype d
  * and inside any batch.
  *
  * nb_batch_create: models[0..n_models) (multinomial, all with the same F,
- *   n_models <= 8), the storage dtype of every group (two-class models: U8 or
+ *   n_models <= 128; the two-class models' tables, 3 bytes per feature (u8
+ *   storage) or 4 (F32), must fit one block's shared memory together, else
+ *   NB_EINVAL), the storage dtype of every group (two-class models: U8 or
  *   F32), the largest leading dimension a group will use, the largest number
  *   of groups per call, and the score options (want_logpost, recheck; aux is
  *   ignored -- each group carries its own).  Allocates the batch's device and
@@ -290,7 +292,7 @@ NB_API void nb_batch_destroy(nb_batch* batch);
  * completes the tickets of finished steps.  Results equal nb_score_group on
  * the group alone.
  *
- * nb_server_create: models (multinomial, same F, <= 8), the storage dtype of
+ * nb_server_create: models (multinomial, same F, <= 128), the storage dtype of
  *   submitted groups (dense rows, ld = F, no side arrays), the device memory
  *   budget in bytes for staged inputs and outputs (0 = 1 GiB), the most
  *   groups per step (max_slots, the batch size bound), score options.
@@ -368,6 +370,101 @@ NB_API nb_status nb_pack_bf16(const void* X, nb_dtype src, int64_t n, int32_t F,
 NB_API nb_status nb_pack_fp8(const void* X, nb_dtype src, int64_t n, int32_t F,
                       int64_t ld, uint8_t* out, int64_t ld_out,
                       int8_t* row_exp, void* cuda_stream);
+
+/* ---- the group-wise method ------------------------------------------------
+ * Sec. 3: files below 500 KB fall into 100 size groups of 5 KB; per group the
+ * opcodes whose normalised occurrence differs most between malware and benign
+ * files are kept (top k, k = 20..200 in Sec. 4).  Sec. 4: one model per
+ * group on its k opcodes, except for groups with fewer than six training
+ * files of either class, whose files take the next group's model.
+ * Readings: size group g = min(floor(size / bin_bytes), n_bins - 1) (5120
+ * and 100 in the paper; a larger file joins the last group); a group is
+ * trained when every class has >= min_files files; an untrained group takes
+ * the first trained group above it, else the nearest one below. */
+
+/* HOST function.  class_counts: n_bins x C training files per (group,
+ * class), host memory.  Writes model_of[g] (host, n_bins) = the group whose
+ * model classifies group g's files.  NB_EINVAL when no group is trained. */
+NB_API nb_status nb_group_fallback(const int64_t* class_counts, int32_t n_bins, int32_t C,
+                                   int64_t min_files, int32_t* model_of);
+
+/* Route n files by size and sort them by group, stably.
+ *   sizes     int64[n] file sizes in bytes (device);
+ *   model_of  int32[n_bins] (device) maps size groups to output groups
+ *             [0, n_groups), or NULL: output group = size group (n_groups
+ *             must equal n_bins);  n_groups <= 512;
+ *   group     int32[n] (device): output group of each file;
+ *   order     int64[n] (device, or NULL): files listed by group, in file
+ *             order inside a group;  offsets int64[n_groups + 1] (device):
+ *             group g is order[offsets[g] .. offsets[g+1]);
+ *   y, C, class_counts: with labels y (device int32[n], classes < C) and
+ *             class_counts (device int64[n_bins x C], n_bins * C <= 4096),
+ *             the training files per (size group, class); else NULL;
+ *   workspace device scratch of >= nb_route_workspace(n, n_groups) bytes;
+ *   status    device int: the value 32 is or-ed in for a negative size
+ *             (counted as 0), a model_of entry or a label out of range.
+ * Three kernels, asynchronous on the stream. */
+NB_API size_t nb_route_workspace(int64_t n, int32_t n_groups);
+NB_API nb_status nb_route(const int64_t* sizes, int64_t n, int64_t bin_bytes, int32_t n_bins,
+                          const int32_t* model_of, int32_t n_groups, const int32_t* y,
+                          int32_t C, int32_t* group, int64_t* order, int64_t* offsets,
+                          int64_t* class_counts, void* workspace, size_t workspace_bytes,
+                          int* status, void* cuda_stream);
+
+/* Top-k opcode selection of two-class multinomial models (fitted on a
+ * group's training files over all opcodes).  With f_cj = N_cj / D_c, D_c the
+ * class's total count (NB_SELECT_TOTAL) or number of files (NB_SELECT_FILES)
+ * and f_c = 0 when D_c = 0, opcode j scores |f_1j - f_0j|, compared exactly
+ * (128-bit integers over the common denominator); larger first, ties to the
+ * lower index.  cols (device int32, n_models x k): model i's first k opcodes
+ * in rank order.  n_models <= 128, 1 <= k <= F.  The models' fits must be
+ * complete or ordered before the stream. */
+typedef enum { NB_SELECT_TOTAL = 0, NB_SELECT_FILES = 1 } nb_select_norm;
+NB_API nb_status nb_select_features(const nb_model* const* models, int32_t n_models,
+                                    int32_t k, int32_t norm, int32_t* cols, void* cuda_stream);
+
+/* Gather: out[r][t] = X[s][cols[g * k + t]] for t < k and 0 for k <= t <
+ * ld_out, where s = order[r] (or r when order is NULL) and g = group[s] (or 0
+ * when group is NULL; cols NULL: column t).  X: n_src source rows of F
+ * elements (U8 or F32, row pitch ld); n output rows of pitch ld_out (U8: a
+ * multiple of 4).  A source row outside [0, n_src) or a group outside [0,
+ * n_groups) gives a zero row, a column outside [0, F) a zero; each raises the
+ * value 32 in *status (device int).  All pointers device. */
+NB_API nb_status nb_gather(const void* X, nb_dtype dtype, int64_t ld, int32_t F, int64_t n_src,
+                           int64_t n,
+                           const int64_t* order, const int32_t* group, int32_t n_groups,
+                           const int32_t* cols, int32_t k, void* out, int64_t ld_out,
+                           int* status, void* cuda_stream);
+
+/* Group-wise classification of files given as full opcode histograms.
+ * nb_groupwise_create: models[0..n_models) two-class multinomial, each on k
+ *   opcodes (F = k), n_models <= 128; cols (host or device, n_models x k) the
+ *   opcodes of each model in its feature order; model_of (host, n_bins) the
+ *   model slot of each size group (for example nb_group_fallback's result
+ *   renumbered to slots); bin_bytes; F_full the histogram width; dtype U8 or
+ *   F32; max_files per call; score options.  Allocates all scratch.
+ * nb_groupwise_classify: X (device, n x ld, ld >= F_full) full histograms,
+ *   sizes (device int64[n]); label / margin / logpost (n x 2 or NULL) device,
+ *   in the files' order.  Routes the files (nb_route), gathers each file's
+ *   model's opcodes into a dense matrix ordered by group (nb_gather), scores
+ *   every group in one batched launch whose work list a kernel builds on the
+ *   device (no host synchronisation), rechecks in FP64 as nb_score_group
+ *   does, and scatters the results back: every file's results equal
+ *   nb_score_group of its model on its gathered row.  Asynchronous.
+ * nb_groupwise_status: reads (synchronously) the object's status word (32:
+ *   a bad size or column was met).  nb_groupwise_destroy frees everything. */
+typedef struct nb_groupwise nb_groupwise;
+NB_API nb_status nb_groupwise_create(const nb_model* const* models, int32_t n_models,
+                                     const int32_t* cols, int32_t k, const int32_t* model_of,
+                                     int32_t n_bins, int64_t bin_bytes, int32_t F_full,
+                                     nb_dtype dtype, int64_t max_files,
+                                     const nb_score_opts* opts, nb_groupwise** out);
+NB_API nb_status nb_groupwise_classify(nb_groupwise* gw, const void* X, int64_t ld,
+                                       const int64_t* sizes, int64_t n, uint8_t* label,
+                                       float* margin, float* logpost, void* cuda_stream,
+                                       int64_t* n_rechecked);
+NB_API nb_status nb_groupwise_status(nb_groupwise* gw, int* host_status);
+NB_API void nb_groupwise_destroy(nb_groupwise* gw);
 
 /* ---- errors / misc -------------------------------------------------------*/
 NB_API const char* nb_last_error(void);

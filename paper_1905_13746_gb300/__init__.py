@@ -51,6 +51,8 @@ class NbTileConfig(ctypes.Structure):
 
 
 NB_VARIANT_AUTO, NB_VARIANT_PIPELINED, NB_VARIANT_REGISTER = 0, 1, 2
+NB_SELECT_TOTAL, NB_SELECT_FILES = 0, 1
+ST_BAD_ROUTE = 32          # status bit of nb_route / nb_gather / nb_groupwise_status
 
 
 class NbGroup(ctypes.Structure):
@@ -111,6 +113,19 @@ _SIGS = [
     ("nb_pack_u8_fill", ctypes.c_int, [_P, _i64, _i32, _i64, _P, _i64, _P, _P, _P, _P]),
     ("nb_pack_bf16", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _P, _i64, _P]),
     ("nb_pack_fp8", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _P, _i64, _P, _P]),
+    ("nb_group_fallback", ctypes.c_int, [_P, _i32, _i32, _i64, _P]),
+    ("nb_route_workspace", ctypes.c_size_t, [_i64, _i32]),
+    ("nb_route", ctypes.c_int, [_P, _i64, _i64, _i32, _P, _i32, _P, _i32, _P, _P, _P, _P, _P,
+                                ctypes.c_size_t, _P, _P]),
+    ("nb_select_features", ctypes.c_int, [ctypes.POINTER(_P), _i32, _i32, _i32, _P, _P]),
+    ("nb_gather", ctypes.c_int, [_P, ctypes.c_int, _i64, _i32, _i64, _i64, _P, _P, _i32, _P,
+                                 _i32, _P, _i64, _P, _P]),
+    ("nb_groupwise_create", ctypes.c_int, [ctypes.POINTER(_P), _i32, _P, _i32, _P, _i32, _i64,
+                                           _i32, ctypes.c_int, _i64,
+                                           ctypes.POINTER(NbScoreOpts), ctypes.POINTER(_P)]),
+    ("nb_groupwise_classify", ctypes.c_int, [_P, _P, _i64, _P, _i64, _P, _P, _P, _P, _P]),
+    ("nb_groupwise_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    ("nb_groupwise_destroy", None, [_P]),
     ("nb_last_error", ctypes.c_char_p, []),
     ("nb_kernel_launches", ctypes.c_uint64, []),
     ("nb_version", ctypes.c_char_p, []),
@@ -556,3 +571,181 @@ def pack_fp8(X, stream=None):
     _check(lib().nb_pack_fp8(X.data_ptr(), src, n, F, X.stride(0), out.data_ptr(), ld_out,
                              row_exp.data_ptr(), _stream_ptr(stream)))
     return Features(out, NB_FP8E4M3, row_exp=row_exp)
+
+
+# ---- the group-wise method (Sec. 3 size groups and top-k opcodes, Sec. 4
+# per-group models and the small-group rule) ------------------------------------
+BIN_BYTES, N_BINS, MIN_FILES = 5 * 1024, 100, 6
+
+
+def group_fallback(class_counts, min_files=MIN_FILES):
+    """Host: model group of every size group from (n_bins x C) training-file
+    counts (nb_group_fallback)."""
+    import numpy as np
+    cc = np.ascontiguousarray(class_counts, dtype=np.int64)
+    n_bins, C = cc.shape
+    out = np.zeros(n_bins, np.int32)
+    _check(lib().nb_group_fallback(cc.ctypes.data, n_bins, C, int(min_files), out.ctypes.data))
+    return out
+
+
+def route(sizes, bin_bytes=BIN_BYTES, n_bins=N_BINS, model_of=None, n_groups=None, y=None,
+          C=2, want_order=True, stream=None):
+    """Route files by size (nb_route).  sizes: device int64 tensor.  Returns
+    dict(group, order, offsets, class_counts (with y), status) of device tensors."""
+    import torch
+    dev = sizes.device
+    n = sizes.shape[0]
+    G = int(n_groups) if n_groups is not None else n_bins
+    ws = int(lib().nb_route_workspace(n, G))
+    work = torch.empty(max(ws, 8), dtype=torch.uint8, device=dev)
+    group = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    order = torch.empty(max(n, 1), dtype=torch.int64, device=dev) if want_order else None
+    offsets = torch.empty(G + 1, dtype=torch.int64, device=dev)
+    cc = torch.empty((n_bins, C), dtype=torch.int64, device=dev) if y is not None else None
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    mo = None
+    if model_of is not None:
+        mo = torch.as_tensor(model_of, dtype=torch.int32).to(dev)
+    _check(lib().nb_route(sizes.data_ptr(), n, int(bin_bytes), int(n_bins),
+                          mo.data_ptr() if mo is not None else None, G,
+                          y.data_ptr() if y is not None else None, int(C), group.data_ptr(),
+                          order.data_ptr() if order is not None else None, offsets.data_ptr(),
+                          cc.data_ptr() if cc is not None else None, work.data_ptr(), ws,
+                          status.data_ptr(), _stream_ptr(stream)))
+    return {"group": group[:n], "order": order[:n] if order is not None else None,
+            "offsets": offsets, "class_counts": cc, "status": status, "_keep": (work, mo)}
+
+
+def select_features(models, k, norm=NB_SELECT_TOTAL, stream=None):
+    """Top-k opcodes of two-class models (nb_select_features): int32 (n x k)."""
+    import torch
+    arr = (_P * len(models))(*[m.handle for m in models])
+    cols = torch.empty((len(models), k), dtype=torch.int32, device="cuda")
+    _check(lib().nb_select_features(arr, len(models), int(k), int(norm), cols.data_ptr(),
+                                    _stream_ptr(stream)))
+    return cols
+
+
+def padded_ld(k, dtype_code):
+    """Row pitch (elements) of gathered rows: 16-byte aligned."""
+    es = 1 if dtype_code == NB_U8 else 4
+    return (k * es + 15) // 16 * 16 // es
+
+
+def gather(X, cols=None, k=None, order=None, group=None, n_groups=None, n=None, ld_out=None,
+           stream=None, status=None):
+    """nb_gather: rows of X (U8 or F32 tensor) by ``order``, columns by each
+    row's group's row of ``cols`` (int32 device tensor n_groups x k)."""
+    import torch
+    dt = _torch_dtype_code(X)
+    F = X.shape[1]
+    if k is None:
+        k = cols.shape[-1] if cols is not None else F
+    if n is None:
+        n = order.shape[0] if order is not None else X.shape[0]
+    if ld_out is None:
+        ld_out = padded_ld(k, dt)
+    out = torch.empty((n, ld_out), dtype=X.dtype, device=X.device)
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=X.device)
+    G = int(n_groups) if n_groups is not None else (cols.shape[0] if cols is not None and
+                                                     cols.dim() == 2 else 1)
+    _check(lib().nb_gather(X.data_ptr(), dt, X.stride(0), F, X.shape[0], n,
+                           order.data_ptr() if order is not None else None,
+                           group.data_ptr() if group is not None else None, G,
+                           cols.data_ptr() if cols is not None else None, int(k),
+                           out.data_ptr(), ld_out, st.data_ptr(), _stream_ptr(stream)))
+    return out[:, :k], st
+
+
+class Groupwise:
+    """Group-wise classifier over full opcode histograms (nb_groupwise_*)."""
+
+    def __init__(self, models, cols, model_of, F_full, dtype_code=NB_U8, max_files=1 << 20,
+                 bin_bytes=BIN_BYTES, want_logpost=True, recheck=NB_RECHECK_LP):
+        import numpy as np
+        self.models = list(models)
+        self.k = self.models[0].F
+        arr = (_P * len(self.models))(*[m.handle for m in self.models])
+        mo = np.ascontiguousarray(model_of, dtype=np.int32)
+        self.cols = cols.contiguous()
+        opts = NbScoreOpts(int(want_logpost), int(recheck), None)
+        h = _P()
+        _check(lib().nb_groupwise_create(arr, len(self.models), self.cols.data_ptr(), self.k,
+                                          mo.ctypes.data, mo.shape[0], int(bin_bytes),
+                                          int(F_full), dtype_code, int(max_files),
+                                          ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h.value
+        self.want_logpost = want_logpost
+
+    def close(self):
+        if self.handle:
+            lib().nb_groupwise_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def classify(self, X, sizes, stream=None, out=None):
+        """X: (n x F_full) device histograms, sizes: device int64 (n).  Returns
+        dict(label, margin, logpost, n_rechecked) in the files' order."""
+        import torch
+        n, dev = X.shape[0], X.device
+        if out is None:
+            out = {"label": torch.empty(n, dtype=torch.uint8, device=dev),
+                   "margin": torch.empty(n, dtype=torch.float32, device=dev),
+                   "logpost": torch.empty((n, 2), dtype=torch.float32, device=dev)
+                   if self.want_logpost else None,
+                   "n_rechecked": torch.zeros(1, dtype=torch.int64, device=dev)}
+        lp = out["logpost"].data_ptr() if out.get("logpost") is not None else None
+        _check(lib().nb_groupwise_classify(self.handle, X.data_ptr(), X.stride(0),
+                                           sizes.data_ptr(), n, out["label"].data_ptr(),
+                                           out["margin"].data_ptr(), lp, _stream_ptr(stream),
+                                           out["n_rechecked"].data_ptr()))
+        return out
+
+    def status(self):
+        v = ctypes.c_int(0)
+        _check(lib().nb_groupwise_status(self.handle, ctypes.byref(v)))
+        return v.value
+
+
+def fit_groupwise(X, y, sizes, k, norm=NB_SELECT_TOTAL, alpha=1.0, bin_bytes=BIN_BYTES,
+                  n_bins=N_BINS, min_files=MIN_FILES, stream=None):
+    """Train the per-group models of the method on the device.
+
+    X: (n x F) U8 or F32 full histograms, y: int32 labels, sizes: int64 file
+    sizes (all device tensors).  Routes the files (labels counted per size
+    group), applies the small-group rule, fits each trained group on all
+    opcodes, ranks its opcodes, and fits it again on its top k.  Returns
+    dict(models, cols, model_of (slot per size group), groups (size group of
+    each slot), full_models)."""
+    import torch
+    n, F = X.shape
+    r = route(sizes, bin_bytes, n_bins, y=y, C=2, stream=stream)
+    cc = r["class_counts"].cpu().numpy()
+    mo_bins = group_fallback(cc, min_files)
+    trained = sorted(set(mo_bins.tolist()))
+    slot = {g: i for i, g in enumerate(trained)}
+    offs = r["offsets"].cpu().tolist()
+    order = r["order"]
+    Xs, _ = gather(X, order=order, stream=stream)          # rows sorted by size group
+    # labels follow their rows (a 4-byte gather of one column)
+    ys = gather(y.view(torch.float32).reshape(n, 1), order=order, ld_out=1,
+                stream=stream)[0].reshape(n).view(torch.int32)
+    full = []
+    for g in trained:
+        a, b = offs[g], offs[g + 1]
+        full.append(fit(Xs[a:b], ys[a:b], 2, alpha=alpha, stream=stream))
+    cols = select_features(full, k, norm, stream=stream)
+    models = []
+    for i, g in enumerate(trained):
+        a, b = offs[g], offs[g + 1]
+        Xg, _ = gather(Xs[a:b], cols[i:i + 1], stream=stream)
+        models.append(fit(Xg, ys[a:b], 2, alpha=alpha, stream=stream))
+    model_of = [slot[int(m)] for m in mo_bins]
+    return {"models": models, "cols": cols, "model_of": model_of, "groups": trained,
+            "full_models": full, "class_counts": cc}

@@ -102,6 +102,34 @@ static nb_status batch_launch(nb_batch* b, cudaStream_t st) {
   return NB_OK;
 }
 
+namespace nbg {
+
+// The family-0 (two-class) work list on the device, for callers that build it
+// with a kernel (the group-wise scorer), and its rows per tile.
+nb_status batch_device_list(nb_batch* b, SegHeader** hdr, SegGroup** list0, int64_t* rs) {
+  if (!b || !b->fam[1].empty() || !b->fam[2].empty()) {
+    set_error("device-built work lists hold two-class groups only");
+    return NB_EINVAL;
+  }
+  *hdr = hdr_of(b->dev);
+  *list0 = list_of(b->dev, 0, b->max_groups);
+  *rs = b->fam[0].empty() ? 1 : b->plan.RS;
+  return NB_OK;
+}
+
+// The batch's launches on a work list already written on the device.
+nb_status batch_launch_device(nb_batch* b, cudaStream_t st, int64_t* n_rechecked) {
+  nb_status s = batch_launch(b, st);
+  if (s != NB_OK) return s;
+  if (n_rechecked)
+    NB_TRY_CUDA(cudaMemcpyAsync(n_rechecked, b->counter, sizeof(int64_t),
+                                cudaMemcpyDeviceToDevice, st),
+                "memcpy(n_rechecked)");
+  return NB_OK;
+}
+
+}  // namespace nbg
+
 extern "C" nb_status nb_batch_create(const nb_model* const* models, int n_models, nb_dtype dtype,
                                      int64_t max_ld, int max_groups, const nb_score_opts* opts,
                                      nb_batch** out) {

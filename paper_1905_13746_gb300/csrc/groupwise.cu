@@ -1,0 +1,744 @@
+// The group-wise method around the scorer (Sec. 3 size groups and top-k
+// opcode selection, Sec. 4 per-group models and the small-group rule):
+//
+//   nb_group_fallback   host: model group of every size group;
+//   nb_route            size -> group (-> model) per file, and a stable
+//                       counting sort of the files by group (three kernels:
+//                       per-tile warp-ranked counts, one scan, scatter);
+//   nb_select_features  exact top-k opcode ranking of two-class models;
+//   nb_gather           rows by a permutation, columns by each row's group's
+//                       selection, into a dense padded matrix;
+//   nb_groupwise_*      all of it for scoring: route, gather, one batched
+//                       two-class launch over every group with a work list
+//                       built on the device, FP64 recheck, and the results
+//                       put back in the files' order.
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "pipe.cuh"
+#include "seg.cuh"
+
+namespace nbg {
+
+constexpr int kRouteWarps = 8;
+constexpr int kRouteSub = 512;                          // files per warp and tile
+constexpr int kRouteTile = kRouteWarps * kRouteSub;     // files per block
+constexpr int kRouteMaxGroups = 512;
+constexpr int kRouteMaxClassCells = 4096;               // n_bins * C with labels
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Group of file i and its size group in *bin.  A negative size or a model_of
+// entry outside [0, n_out) raises ST_BAD_ROUTE and counts as 0, so that every
+// file still gets a group and the order stays a permutation.
+__device__ __forceinline__ int route_of(const int64_t* sizes, int64_t i, int64_t bin_bytes,
+                                        int n_bins, const int32_t* model_of, int n_out,
+                                        int* bin, int* status) {
+  long long s = sizes[i];
+  if (s < 0) {
+    atomicOr(status, ST_BAD_ROUTE);
+    s = 0;
+  }
+  long long g = s / bin_bytes;
+  if (g > n_bins - 1) g = n_bins - 1;
+  *bin = (int)g;
+  int m = model_of ? model_of[g] : (int)g;
+  if (m < 0 || m >= n_out) {
+    atomicOr(status, ST_BAD_ROUTE);
+    m = 0;
+  }
+  return m;
+}
+
+// Pass 1: group of every file, per-block counts per group (hist[g * nblk + b])
+// and, with labels, files per (size group, class).
+__global__ void __launch_bounds__(kRouteWarps * 32)
+    k_route_count(const int64_t* sizes, int64_t n, int64_t bin_bytes, int n_bins,
+                  const int32_t* model_of, int n_out, const int32_t* y, int C,
+                  int32_t* group, int64_t* hist, int64_t* class_counts, int* status) {
+  __shared__ int cnt[kRouteWarps][kRouteMaxGroups];
+  __shared__ int ccnt[kRouteMaxClassCells];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < kRouteWarps * kRouteMaxGroups; t += blockDim.x)
+    (&cnt[0][0])[t] = 0;
+  if (y)
+    for (int t = threadIdx.x; t < n_bins * C; t += blockDim.x) ccnt[t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRouteTile + (int64_t)warp * kRouteSub;
+  for (int step = 0; step < kRouteSub / 32; ++step) {
+    const int64_t i = base + step * 32 + lane;
+    int bin = -1, g = -1;
+    if (i < n) {
+      g = route_of(sizes, i, bin_bytes, n_bins, model_of, n_out, &bin, status);
+      group[i] = g;
+      if (y) {
+        const int c = y[i];
+        if (c >= 0 && c < C) atomicAdd(&ccnt[bin * C + c], 1);
+        else atomicOr(status, ST_BAD_ROUTE);
+      }
+    }
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, g);
+    if (g >= 0 && lane == __ffs(peers) - 1) cnt[warp][g] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < n_out; g += blockDim.x) {
+    int s = 0;
+#pragma unroll
+    for (int w = 0; w < kRouteWarps; ++w) s += cnt[w][g];
+    hist[(int64_t)g * gridDim.x + blockIdx.x] = s;
+  }
+  if (y)
+    for (int t = threadIdx.x; t < n_bins * C; t += blockDim.x)
+      if (ccnt[t]) atomicAdd(reinterpret_cast<unsigned long long*>(&class_counts[t]),
+                             (unsigned long long)ccnt[t]);
+}
+
+// Pass 2 (one block): exclusive scan of hist in place (group-major, so the
+// result is each block's first position per group) and offsets[g].
+__global__ void __launch_bounds__(1024)
+    k_route_scan(int64_t* hist, int64_t L, int nblk, int n_out, int64_t* offsets) {
+  __shared__ int64_t wsum[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t per = (L + blockDim.x - 1) / blockDim.x;
+  const int64_t a = t * per, b = a + per < L ? a + per : L;
+  int64_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += hist[i];
+  // block-wide exclusive scan of the per-thread sums
+  int64_t v = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t u = __shfl_up_sync(0xFFFFFFFFu, v, off);
+    if (lane >= off) v += u;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int64_t u = __shfl_up_sync(0xFFFFFFFFu, w, off);
+      if (lane >= off) w += u;
+    }
+    wsum[lane] = w;   // inclusive over warps
+  }
+  __syncthreads();
+  int64_t run = v - s + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int64_t i = a; i < b; ++i) {
+    const int64_t h = hist[i];
+    hist[i] = run;
+    run += h;
+  }
+  __syncthreads();
+  for (int g = t; g <= n_out; g += blockDim.x)
+    offsets[g] = g < n_out ? hist[(int64_t)g * nblk] : wsum[31];
+}
+
+// Pass 3: each file's position; ranks inside a warp step from the peers of
+// the same group, so the order within a group is the files' order (stable).
+__global__ void __launch_bounds__(kRouteWarps * 32)
+    k_route_scatter(const int32_t* group, int64_t n, int n_out, const int64_t* first,
+                    int64_t* order) {
+  __shared__ int cnt[kRouteWarps][kRouteMaxGroups];
+  __shared__ int64_t run[kRouteWarps][kRouteMaxGroups / 2];   // two passes of 256 groups
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < kRouteWarps * kRouteMaxGroups; t += blockDim.x)
+    (&cnt[0][0])[t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRouteTile + (int64_t)warp * kRouteSub;
+  for (int step = 0; step < kRouteSub / 32; ++step) {
+    const int64_t i = base + step * 32 + lane;
+    const int g = i < n ? group[i] : -1;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, g);
+    if (g >= 0 && lane == __ffs(peers) - 1) cnt[warp][g] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // groups [h * 256, h * 256 + 256) per pass keep their running positions in `run`
+  for (int h = 0; h * (kRouteMaxGroups / 2) < n_out; ++h) {
+    const int g0 = h * (kRouteMaxGroups / 2);
+    for (int t = threadIdx.x; t < kRouteMaxGroups / 2; t += blockDim.x) {
+      const int g = g0 + t;
+      if (g >= n_out) continue;
+      int64_t p = first[(int64_t)g * gridDim.x + blockIdx.x];
+      for (int w = 0; w < kRouteWarps; ++w) {
+        run[w][t] = p;
+        p += cnt[w][g];
+      }
+    }
+    __syncthreads();
+    for (int step = 0; step < kRouteSub / 32; ++step) {
+      const int64_t i = base + step * 32 + lane;
+      const int g = i < n ? group[i] : -1;
+      const bool mine = g >= g0 && g < g0 + kRouteMaxGroups / 2;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, mine ? g : -1);
+      if (mine) order[run[warp][g - g0] + __popc(peers & lanemask_lt())] = i;
+      __syncwarp();
+      if (mine && lane == __ffs(peers) - 1) run[warp][g - g0] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+size_t route_workspace(int64_t n, int n_out) {
+  const int64_t nblk = n > 0 ? (n + kRouteTile - 1) / kRouteTile : 1;
+  return (size_t)(nblk * n_out) * sizeof(int64_t);
+}
+
+nb_status launch_route(const int64_t* sizes, int64_t n, int64_t bin_bytes, int n_bins,
+                       const int32_t* model_of, int n_out, const int32_t* y, int C,
+                       int32_t* group, int64_t* order, int64_t* offsets,
+                       int64_t* class_counts, int64_t* hist, int* status, cudaStream_t st) {
+  const int64_t nblk = n > 0 ? (n + kRouteTile - 1) / kRouteTile : 0;
+  if (class_counts)
+    NB_TRY_CUDA(cudaMemsetAsync(class_counts, 0, sizeof(int64_t) * n_bins * C, st),
+                "memset(class_counts)");
+  if (nblk == 0) {
+    NB_TRY_CUDA(cudaMemsetAsync(offsets, 0, sizeof(int64_t) * (n_out + 1), st),
+                "memset(offsets)");
+    return NB_OK;
+  }
+  count_launch();
+  k_route_count<<<(unsigned)nblk, kRouteWarps * 32, 0, st>>>(
+      sizes, n, bin_bytes, n_bins, model_of, n_out, class_counts ? y : nullptr, C, group, hist,
+      class_counts, status);
+  NB_TRY_CUDA(cudaGetLastError(), "k_route_count launch");
+  count_launch();
+  k_route_scan<<<1, 1024, 0, st>>>(hist, nblk * n_out, (int)nblk, n_out, offsets);
+  NB_TRY_CUDA(cudaGetLastError(), "k_route_scan launch");
+  if (order) {
+    count_launch();
+    k_route_scatter<<<(unsigned)nblk, kRouteWarps * 32, 0, st>>>(group, n, n_out, hist, order);
+    NB_TRY_CUDA(cudaGetLastError(), "k_route_scatter launch");
+  }
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// top-k opcode selection (two-class models): key_j = |N_1j D_0 - N_0j D_1|
+// over the common denominator D_0 D_1 (a class with D_c = 0 counts as D_c = 1,
+// its N_cj being 0), compared exactly in 128-bit integers; rank_j = number
+// of opcodes with a larger key or an equal key and a lower index.
+// ---------------------------------------------------------------------------
+constexpr int kSelMaxModels = 128;
+constexpr int kSelThreads = 256;
+constexpr int kSelPer = 4;                        // candidates per thread
+constexpr int kSelBlock = kSelThreads * kSelPer;  // candidates per block
+constexpr int kSelTile = 1024;                    // keys staged per round
+
+struct SelModel {
+  const uint64_t* counts;   // 2 x F
+  const uint64_t* nc;       // 2
+  int F;
+};
+
+struct SelArgs {
+  SelModel m[kSelMaxModels];
+  int k, norm;
+  int32_t* cols;
+};
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 sel_key(const uint64_t* N, int F, int j, uint64_t D0,
+                                        uint64_t D1) {
+  const u128 a = (u128)N[F + j] * D0, b = (u128)N[j] * D1;
+  return a > b ? a - b : b - a;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select_topk(const SelArgs a) {
+  __shared__ uint64_t khi[kSelTile], klo[kSelTile];
+  __shared__ unsigned long long red[2][kSelThreads / 32];
+  const SelModel M = a.m[blockIdx.y];
+  const int F = M.F, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if ((int64_t)blockIdx.x * kSelBlock >= F) return;   // uniform per block
+  uint64_t D0, D1;
+  if (a.norm == NB_SELECT_FILES) {
+    D0 = M.nc[0];
+    D1 = M.nc[1];
+  } else {
+    unsigned long long s0 = 0, s1 = 0;
+    for (int j = t; j < F; j += blockDim.x) {
+      s0 += M.counts[j];
+      s1 += M.counts[F + j];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, off);
+      s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, off);
+    }
+    if (lane == 0) {
+      red[0][warp] = s0;
+      red[1][warp] = s1;
+    }
+    __syncthreads();
+    s0 = s1 = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    D0 = s0;
+    D1 = s1;
+  }
+  if (D0 == 0) D0 = 1;
+  if (D1 == 0) D1 = 1;
+  u128 key[kSelPer];
+  int jj[kSelPer], rank[kSelPer];
+#pragma unroll
+  for (int q = 0; q < kSelPer; ++q) {
+    jj[q] = blockIdx.x * kSelBlock + q * kSelThreads + t;
+    key[q] = jj[q] < F ? sel_key(M.counts, F, jj[q], D0, D1) : (u128)0;
+    rank[q] = 0;
+  }
+  for (int i0 = 0; i0 < F; i0 += kSelTile) {
+    __syncthreads();
+    for (int u = t; u < kSelTile; u += blockDim.x) {
+      const int i = i0 + u;
+      const u128 v = i < F ? sel_key(M.counts, F, i, D0, D1) : (u128)0;
+      khi[u] = (uint64_t)(v >> 64);
+      klo[u] = (uint64_t)v;
+    }
+    __syncthreads();
+    const int m = F - i0 < kSelTile ? F - i0 : kSelTile;
+    for (int u = 0; u < m; ++u) {
+      const u128 v = ((u128)khi[u] << 64) | klo[u];
+      const int i = i0 + u;
+#pragma unroll
+      for (int q = 0; q < kSelPer; ++q) rank[q] += (v > key[q] || (v == key[q] && i < jj[q]));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kSelPer; ++q)
+    if (jj[q] < F && rank[q] < a.k) a.cols[(int64_t)blockIdx.y * a.k + rank[q]] = jj[q];
+}
+
+// ---------------------------------------------------------------------------
+// gather: out[r][t] = X[src(r)][cols[grp * k + t]], t < k, zero up to ld_out
+// (src(r) = order[r] or r; grp = group[src(r)] or 0; cols == nullptr: t).
+// One warp per output row; the u8 kernel packs four bytes per lane.
+// ---------------------------------------------------------------------------
+template <int ES>
+__global__ void __launch_bounds__(256)
+    k_gather(const char* X, int64_t ld, int F, int64_t n_src, int64_t n, const int64_t* order,
+             const int32_t* group, int n_groups, const int32_t* cols, int k, char* out,
+             int64_t ld_out, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
+       r += warps) {
+    int64_t i = order ? order[r] : r;
+    int g = 0;
+    if (i < 0 || i >= n_src) {       // no source row: zero row
+      if (lane == 0) atomicOr(status, ST_BAD_ROUTE);
+      i = 0;
+      g = -1;
+    } else if (group) {
+      g = group[i];
+    }
+    if (g >= n_groups) g = -1;
+    if (g < 0) {                     // no selection to take: zero row
+      if (lane == 0) atomicOr(status, ST_BAD_ROUTE);
+      g = -1;
+    }
+    const int32_t* cg = cols && g >= 0 ? cols + (int64_t)g * k : nullptr;
+    const int kk = g >= 0 ? k : 0;
+    if (ES == 1) {
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(X) + i * ld;
+      uint32_t* dst = reinterpret_cast<uint32_t*>(out + r * ld_out);
+      for (int64_t t0 = 4 * lane; t0 < ld_out; t0 += 128) {
+        uint32_t w = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int t = (int)t0 + b;
+          if (t < kk) {
+            const int c = cg ? cg[t] : t;
+            if ((unsigned)c < (unsigned)F) w |= (uint32_t)src[c] << (8 * b);
+            else atomicOr(status, ST_BAD_ROUTE);
+          }
+        }
+        dst[t0 >> 2] = w;
+      }
+    } else {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(X + i * ld * 4);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(out + r * ld_out * 4);
+      for (int64_t t = lane; t < ld_out; t += 32) {
+        uint32_t v = 0;
+        if (t < kk) {
+          const int c = cg ? cg[t] : (int)t;
+          if ((unsigned)c < (unsigned)F) v = src[c];
+          else atomicOr(status, ST_BAD_ROUTE);
+        }
+        dst[t] = v;
+      }
+    }
+  }
+}
+
+nb_status launch_gather(const void* X, nb_dtype dt, int64_t ld, int F, int64_t n_src,
+                        int64_t n, const int64_t* order, const int32_t* group, int n_groups,
+                        const int32_t* cols, int k, void* out, int64_t ld_out, int* status,
+                        cudaStream_t st) {
+  if (n == 0) return NB_OK;
+  int64_t blocks = (n + 7) / 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  count_launch();
+  if (elem_size(dt) == 1)
+    k_gather<1><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const char*>(X), ld, F, n_src, n,
+                                                   order, group, n_groups, cols, k,
+                                                   static_cast<char*>(out), ld_out, status);
+  else
+    k_gather<4><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const char*>(X), ld, F, n_src, n,
+                                                   order, group, n_groups, cols, k,
+                                                   static_cast<char*>(out), ld_out, status);
+  NB_TRY_CUDA(cudaGetLastError(), "k_gather launch");
+  return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device-built work list of the batched two-class launch: group m = the rows
+// offsets[m] .. offsets[m+1]-1 of the gathered matrix, scored by model slot m
+// ---------------------------------------------------------------------------
+__global__ void k_gw_worklist(SegHeader* hdr, SegGroup* list, int n_models,
+                              const int64_t* offsets, const char* xs, int64_t ld_bytes,
+                              uint8_t* label, float* margin, float* logpost, int64_t rs) {
+  if (threadIdx.x != 0) return;
+  long long tiles = 0, chunks = 0;
+  for (int m = 0; m < n_models; ++m) {
+    const int64_t o = offsets[m], nm = offsets[m + 1] - o;
+    SegGroup& d = list[m];
+    d.X = xs + o * ld_bytes;
+    d.ld_bytes = ld_bytes;
+    d.n = nm;
+    d.ovf_ptr = nullptr;
+    d.ovf_col = nullptr;
+    d.ovf_add = nullptr;
+    d.row_exp = nullptr;
+    d.label = label + o;
+    d.margin = margin + o;
+    d.logpost = logpost ? logpost + 2 * o : nullptr;
+    d.tile0 = tiles;
+    d.chunk0 = chunks;
+    d.model = m;
+    d.family = 0;
+    tiles += (nm + rs - 1) / rs;
+    chunks += (nm + 31) / 32;
+  }
+  for (int f = 0; f < 3; ++f) {
+    hdr[f].n_groups = f == 0 ? n_models : 0;
+    hdr[f].pad = 0;
+    hdr[f].tiles = f == 0 ? tiles : 0;
+    hdr[f].chunks = f == 0 ? chunks : 0;
+    hdr[f].pad2 = 0;
+  }
+}
+
+// results back in the files' order
+__global__ void k_gw_unpermute(const int64_t* order, int64_t n, const uint8_t* label_s,
+                               const float* margin_s, const float* lp_s, uint8_t* label,
+                               float* margin, float* logpost) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = order[r];
+    label[i] = label_s[r];
+    margin[i] = margin_s[r];
+    if (logpost) {
+      const float2 v = reinterpret_cast<const float2*>(lp_s)[r];
+      logpost[2 * i] = v.x;
+      logpost[2 * i + 1] = v.y;
+    }
+  }
+}
+
+}  // namespace nbg
+
+using namespace nbg;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" nb_status nb_group_fallback(const int64_t* class_counts, int32_t n_bins, int32_t C,
+                                       int64_t min_files, int32_t* model_of) {
+  if (!class_counts || !model_of || n_bins < 1 || C < 1) {
+    set_error("nb_group_fallback: bad arguments");
+    return NB_EINVAL;
+  }
+  std::vector<char> trained((size_t)n_bins, 0);
+  bool any = false;
+  for (int g = 0; g < n_bins; ++g) {
+    int64_t lo = class_counts[(size_t)g * C];
+    for (int c = 1; c < C; ++c) {
+      const int64_t v = class_counts[(size_t)g * C + c];
+      lo = v < lo ? v : lo;
+    }
+    trained[g] = lo >= min_files;
+    any = any || trained[g];
+  }
+  if (!any) {
+    set_error("nb_group_fallback: no group has %lld files of every class", (long long)min_files);
+    return NB_EINVAL;
+  }
+  for (int g = 0; g < n_bins; ++g) {
+    int m = -1;
+    for (int h = g; h < n_bins && m < 0; ++h)
+      if (trained[h]) m = h;
+    for (int h = g - 1; h >= 0 && m < 0; --h)
+      if (trained[h]) m = h;
+    model_of[g] = m;
+  }
+  return NB_OK;
+}
+
+extern "C" size_t nb_route_workspace(int64_t n, int32_t n_groups) {
+  return route_workspace(n < 0 ? 0 : n, n_groups < 1 ? 1 : n_groups);
+}
+
+extern "C" nb_status nb_route(const int64_t* sizes, int64_t n, int64_t bin_bytes, int32_t n_bins,
+                              const int32_t* model_of, int32_t n_groups, const int32_t* y,
+                              int32_t C, int32_t* group, int64_t* order, int64_t* offsets,
+                              int64_t* class_counts, void* workspace, size_t workspace_bytes,
+                              int* status, void* cuda_stream) {
+  if (n < 0 || bin_bytes < 1 || n_bins < 1 || n_groups < 1 || n_groups > kRouteMaxGroups ||
+      (!model_of && n_groups != n_bins) || (n > 0 && (!sizes || !group)) || !offsets ||
+      (class_counts && (!y || C < 1 || (int64_t)n_bins * C > kRouteMaxClassCells)) ||
+      !status || workspace_bytes < route_workspace(n, n_groups) || !workspace) {
+    set_error("nb_route: bad arguments (n_groups <= %d, n_bins * C <= %d with labels, "
+              "workspace >= nb_route_workspace)", kRouteMaxGroups, kRouteMaxClassCells);
+    return NB_EINVAL;
+  }
+  return launch_route(sizes, n, bin_bytes, n_bins, model_of, n_groups, y, C, group, order,
+                      offsets, class_counts, static_cast<int64_t*>(workspace), status,
+                      static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" nb_status nb_select_features(const nb_model* const* models, int32_t n_models,
+                                        int32_t k, int32_t norm, int32_t* cols,
+                                        void* cuda_stream) {
+  if (!models || n_models < 1 || n_models > kSelMaxModels || !cols ||
+      (norm != NB_SELECT_TOTAL && norm != NB_SELECT_FILES)) {
+    set_error("nb_select_features: need 1 <= n_models <= %d, a norm, cols", kSelMaxModels);
+    return NB_EINVAL;
+  }
+  SelArgs a{};
+  int maxF = 0;
+  for (int i = 0; i < n_models; ++i) {
+    const nb_model* m = models[i];
+    if (!m || m->kind != NB_MULTINOMIAL || m->C != 2 || k < 1 || k > m->F) {
+      set_error("nb_select_features: model %d: needs a two-class multinomial model with "
+                "F >= k >= 1", i);
+      return NB_EINVAL;
+    }
+    a.m[i] = SelModel{m->d.counts, m->d.nc, m->F};
+    if (m->F > maxF) maxF = m->F;
+  }
+  a.k = k;
+  a.norm = norm;
+  a.cols = cols;
+  dim3 grid((unsigned)((maxF + kSelBlock - 1) / kSelBlock), (unsigned)n_models);
+  count_launch();
+  k_select_topk<<<grid, kSelThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(a);
+  NB_TRY_CUDA(cudaGetLastError(), "k_select_topk launch");
+  return NB_OK;
+}
+
+extern "C" nb_status nb_gather(const void* X, nb_dtype dtype, int64_t ld, int32_t F,
+                               int64_t n_src, int64_t n, const int64_t* order, const int32_t* group, int32_t n_groups,
+                               const int32_t* cols, int32_t k, void* out, int64_t ld_out,
+                               int* status, void* cuda_stream) {
+  const int es = elem_size(dtype);
+  if ((es != 1 && es != 4) || n < 0 || F < 1 || ld < F || k < 1 || ld_out < k ||
+      (!order && n_src < n) || (n > 0 && n_src < 1) ||
+      (!cols && k > F) || (n > 0 && (!X || !out)) || !status || (group && n_groups < 1) ||
+      (es == 1 && (ld_out % 4) != 0) || (es == 1 && (reinterpret_cast<uintptr_t>(out) & 3)) ||
+      (es == 4 && ((reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(X)) & 3))) {
+    set_error("nb_gather: bad arguments (1- or 4-byte elements, ld >= F, ld_out >= k, "
+              "u8 ld_out a multiple of 4, aligned buffers)");
+    return NB_EINVAL;
+  }
+  return launch_gather(X, dtype, ld, F, n_src, n, order, group, group ? n_groups : 1, cols, k, out,
+                       ld_out, status, static_cast<cudaStream_t>(cuda_stream));
+}
+
+// ---------------------------------------------------------------------------
+// the group-wise scorer object
+// ---------------------------------------------------------------------------
+struct nb_groupwise {
+  nb_batch* batch = nullptr;
+  int n_models = 0, k = 0, F_full = 0, n_bins = 0, want_lp = 0;
+  int64_t bin_bytes = 0, max_files = 0, ld_out = 0;
+  nb_dtype dtype = NB_U8;
+  void* mem = nullptr;        // one device allocation for everything below
+  int32_t* model_of = nullptr;
+  int32_t* cols = nullptr;
+  int32_t* group = nullptr;
+  int64_t* order = nullptr;
+  int64_t* offsets = nullptr;
+  int64_t* hist = nullptr;
+  char* xs = nullptr;
+  uint8_t* label_s = nullptr;
+  float* margin_s = nullptr;
+  float* lp_s = nullptr;
+  int* status = nullptr;
+};
+
+namespace nbg {
+// batch.cu
+nb_status batch_device_list(nb_batch* b, SegHeader** hdr, SegGroup** list0, int64_t* rs);
+nb_status batch_launch_device(nb_batch* b, cudaStream_t st, int64_t* n_rechecked);
+}  // namespace nbg
+
+extern "C" void nb_groupwise_destroy(nb_groupwise* g) {
+  if (!g) return;
+  if (g->batch) nb_batch_destroy(g->batch);
+  if (g->mem) {
+    cudaDeviceSynchronize();
+    cudaFree(g->mem);
+  }
+  delete g;
+}
+
+extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t n_models,
+                                         const int32_t* cols, int32_t k,
+                                         const int32_t* model_of, int32_t n_bins,
+                                         int64_t bin_bytes, int32_t F_full, nb_dtype dtype,
+                                         int64_t max_files, const nb_score_opts* opts,
+                                         nb_groupwise** out) {
+  if (!out || !models || n_models < 1 || n_models > kSegMaxModels || !cols || !model_of ||
+      n_bins < 1 || bin_bytes < 1 || F_full < 1 || k < 1 || k > F_full || max_files < 0 ||
+      (dtype != NB_U8 && dtype != NB_F32)) {
+    set_error("nb_groupwise_create: bad arguments (1 <= n_models <= %d, U8 or F32)",
+              kSegMaxModels);
+    return NB_EINVAL;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n_models; ++i)
+    if (!models[i] || models[i]->kind != NB_MULTINOMIAL || models[i]->C != 2 ||
+        models[i]->F != k) {
+      set_error("nb_groupwise_create: model %d must be two-class multinomial with F = k", i);
+      return NB_EINVAL;
+    }
+  for (int b = 0; b < n_bins; ++b)
+    if (model_of[b] < 0 || model_of[b] >= n_models) {
+      set_error("nb_groupwise_create: model_of[%d] = %d is not a model slot", b, model_of[b]);
+      return NB_EINVAL;
+    }
+  nb_groupwise* g = new (std::nothrow) nb_groupwise();
+  if (!g) {
+    set_error("nb_groupwise_create: out of host memory");
+    return NB_ENOMEM;
+  }
+  g->n_models = n_models;
+  g->k = k;
+  g->F_full = F_full;
+  g->n_bins = n_bins;
+  g->bin_bytes = bin_bytes;
+  g->max_files = max_files;
+  g->dtype = dtype;
+  g->want_lp = opts ? opts->want_logpost : 0;
+  const int es = elem_size(dtype);
+  g->ld_out = ((int64_t)k * es + 15) / 16 * 16 / es;   // rows 16-byte aligned
+  auto fail = [&](nb_status s) {
+    nb_groupwise_destroy(g);
+    return s;
+  };
+  nb_status s = nb_batch_create(models, n_models, dtype, g->ld_out, n_models, opts, &g->batch);
+  if (s != NB_OK) return fail(s);
+  // one allocation, 256-byte aligned pieces
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const int64_t nf = max_files > 0 ? max_files : 1;
+  const size_t o_model = take(sizeof(int32_t) * n_bins);
+  const size_t o_cols = take(sizeof(int32_t) * (size_t)n_models * k);
+  const size_t o_group = take(sizeof(int32_t) * nf);
+  const size_t o_order = take(sizeof(int64_t) * nf);
+  const size_t o_offs = take(sizeof(int64_t) * (n_models + 1));
+  const size_t o_hist = take(route_workspace(nf, n_models));
+  const size_t o_xs = take((size_t)nf * g->ld_out * es);
+  const size_t o_lab = take(nf);
+  const size_t o_mar = take(sizeof(float) * nf);
+  const size_t o_lp = take(g->want_lp ? sizeof(float) * 2 * nf : 0);
+  const size_t o_st = take(sizeof(int));
+  cudaError_t e = cudaMalloc(&g->mem, off);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(groupwise)"));
+  char* base = static_cast<char*>(g->mem);
+  g->model_of = reinterpret_cast<int32_t*>(base + o_model);
+  g->cols = reinterpret_cast<int32_t*>(base + o_cols);
+  g->group = reinterpret_cast<int32_t*>(base + o_group);
+  g->order = reinterpret_cast<int64_t*>(base + o_order);
+  g->offsets = reinterpret_cast<int64_t*>(base + o_offs);
+  g->hist = reinterpret_cast<int64_t*>(base + o_hist);
+  g->xs = base + o_xs;
+  g->label_s = reinterpret_cast<uint8_t*>(base + o_lab);
+  g->margin_s = reinterpret_cast<float*>(base + o_mar);
+  g->lp_s = g->want_lp ? reinterpret_cast<float*>(base + o_lp) : nullptr;
+  g->status = reinterpret_cast<int*>(base + o_st);
+  NB_TRY_CUDA(cudaMemset(g->mem, 0, off), "memset(groupwise)");
+  e = cudaMemcpy(g->model_of, model_of, sizeof(int32_t) * n_bins, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->cols, cols, sizeof(int32_t) * (size_t)n_models * k, cudaMemcpyDefault);
+  if (e != cudaSuccess) return fail(cuda_status(e, "memcpy(groupwise tables)"));
+  *out = g;
+  return NB_OK;
+}
+
+extern "C" nb_status nb_groupwise_classify(nb_groupwise* g, const void* X, int64_t ld,
+                                           const int64_t* sizes, int64_t n, uint8_t* label,
+                                           float* margin, float* logpost, void* cuda_stream,
+                                           int64_t* n_rechecked) {
+  if (!g || n < 0 || n > g->max_files || ld < g->F_full ||
+      (n > 0 && (!X || !sizes || !label || !margin || (g->want_lp && !logpost)))) {
+    set_error("nb_groupwise_classify: bad arguments (n <= max_files, ld >= F)");
+    return NB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  nb_status s = launch_route(sizes, n, g->bin_bytes, g->n_bins, g->model_of, g->n_models,
+                             nullptr, 0, g->group, g->order, g->offsets, nullptr, g->hist,
+                             g->status, st);
+  if (s != NB_OK) return s;
+  s = launch_gather(X, g->dtype, ld, g->F_full, n, n, g->order, g->group, g->n_models, g->cols,
+                    g->k, g->xs, g->ld_out, g->status, st);
+  if (s != NB_OK) return s;
+  SegHeader* hdr = nullptr;
+  SegGroup* list0 = nullptr;
+  int64_t rs = 1;
+  s = batch_device_list(g->batch, &hdr, &list0, &rs);
+  if (s != NB_OK) return s;
+  count_launch();
+  k_gw_worklist<<<1, 32, 0, st>>>(hdr, list0, g->n_models, g->offsets, g->xs,
+                                  g->ld_out * elem_size(g->dtype), g->label_s, g->margin_s,
+                                  g->want_lp ? g->lp_s : nullptr, rs);
+  NB_TRY_CUDA(cudaGetLastError(), "k_gw_worklist launch");
+  s = batch_launch_device(g->batch, st, n_rechecked);
+  if (s != NB_OK) return s;
+  if (n > 0) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+    count_launch();
+    k_gw_unpermute<<<(unsigned)blocks, 256, 0, st>>>(g->order, n, g->label_s, g->margin_s,
+                                                    g->want_lp ? g->lp_s : nullptr, label,
+                                                    margin, g->want_lp ? logpost : nullptr);
+    NB_TRY_CUDA(cudaGetLastError(), "k_gw_unpermute launch");
+  }
+  return NB_OK;
+}
+
+extern "C" nb_status nb_groupwise_status(nb_groupwise* g, int* host_status) {
+  if (!g || !host_status) {
+    set_error("nb_groupwise_status: bad arguments");
+    return NB_EINVAL;
+  }
+  NB_TRY_CUDA(cudaMemcpy(host_status, g->status, sizeof(int), cudaMemcpyDeviceToHost),
+              "memcpy(status)");
+  return NB_OK;
+}

@@ -26,7 +26,8 @@ enum : int {
   ST_BAD_VALUE = 2,       // negative, fractional or non-finite count
   ST_TIMEOUT = 4,         // a bounded wait gave up
   ST_BAD_TABLE = 8,       // non-finite parameter table
-  ST_OVF_RANGE = 16       // overflow column outside [0, F)
+  ST_OVF_RANGE = 16,      // overflow column outside [0, F)
+  ST_BAD_ROUTE = 32       // routing / gather input: negative size, group, label or column out of range
 };
 
 constexpr uint8_t kLabelRecheck = 255;   // internal marker in label[]

@@ -9,7 +9,7 @@
 
 namespace nbg {
 
-constexpr int kSegMaxModels = 8;
+constexpr int kSegMaxModels = 128;   // kernel arguments hold one entry per model
 
 struct SegGroup {
   const char* X;

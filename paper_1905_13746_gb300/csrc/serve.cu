@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "seg.cuh"
 
 namespace nbg {
 
@@ -303,7 +304,7 @@ static void worker_loop(nb_server* s) {
 extern "C" nb_status nb_server_create(const nb_model* const* models, int n_models, nb_dtype dtype,
                                       size_t mem_budget, int max_slots, const nb_score_opts* opts,
                                       nb_server** out) {
-  if (!out || !models || n_models < 1 || n_models > 8 || max_slots < 1 ||
+  if (!out || !models || n_models < 1 || n_models > kSegMaxModels || max_slots < 1 ||
       elem_size(dtype) == 0) {
     set_error("nb_server_create: need 1..8 models, max_slots >= 1, a valid dtype");
     return NB_EINVAL;
