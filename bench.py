@@ -373,7 +373,8 @@ def run_groupwise(args, device, reps=20, warm=3):
     s_te = torch.from_numpy(s[n_tr:]).to(device)
     stream = torch.cuda.Stream(device)
     rows = []
-    for k in GW_KS:
+    ks = [int(v) for v in args.gw_k.split(",")] if args.gw_k else list(GW_KS)
+    for k in ks:
         with torch.cuda.stream(stream):
             t0 = time.perf_counter()
             fg = nb.fit_groupwise(Xtr, ytr, s_tr, k, stream=stream)
@@ -791,6 +792,7 @@ def main():
                     help="print only the group-wise pipeline (size groups, top-k opcodes)")
     ap.add_argument("--gw-n", type=int, default=1_000_000)
     ap.add_argument("--gw-train", type=int, default=500_000)
+    ap.add_argument("--gw-k", default="", help="comma-separated k values (default 20..200)")
     ap.add_argument("--serving-only", action="store_true",
                     help="print only the serving sweep (loads 0.25/0.5/0.75/0.9)")
     args = ap.parse_args()

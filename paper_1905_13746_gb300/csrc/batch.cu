@@ -37,6 +37,7 @@ struct nb_batch {
   int F, F_pad;
   int max_groups;
   int want_lp, recheck;
+  bool plain = false;   // groups carry no side arrays (longer stages)
   // family 0 (two-class pipelined), 1 (general) and 2 (tensor-core) models;
   // a many-class slot sits in family 1 and, with tensor tables, in family 2
   std::vector<const nb_model*> fam[kFamilies];
@@ -44,7 +45,7 @@ struct nb_batch {
   size_t maps_off = 0;
   // two-class launch plan
   PipeArgs plan{};
-  int kv = 0, ncw = 0, smem = 0;
+  int kv = 0, rpw = 1, ncw = 0, smem = 0;
   SegArgs seg{};
   // work lists
   size_t bytes = 0;
@@ -74,7 +75,8 @@ static nb_status batch_launch(nb_batch* b, cudaStream_t st) {
     a.groups = list_of(b->dev, 0, b->max_groups);
     a.hdr = dh;
     int grid = 0;
-    nb_status s = launch_score2_seg(a, b->plan, b->dtype, b->kv, b->ncw, b->smem, &grid, st);
+    nb_status s =
+        launch_score2_seg(a, b->plan, b->dtype, b->kv, b->rpw, b->ncw, b->smem, &grid, st);
     if (s != NB_OK) return s;
   }
   if (!b->fam[1].empty()) {
@@ -130,9 +132,23 @@ nb_status batch_launch_device(nb_batch* b, cudaStream_t st, int64_t* n_rechecked
 
 }  // namespace nbg
 
+namespace nbg {
+nb_status batch_create(const nb_model* const* models, int n_models, nb_dtype dtype,
+                       int64_t max_ld, int max_groups, const nb_score_opts* opts, bool plain,
+                       nb_batch** out);
+}
+
 extern "C" nb_status nb_batch_create(const nb_model* const* models, int n_models, nb_dtype dtype,
                                      int64_t max_ld, int max_groups, const nb_score_opts* opts,
                                      nb_batch** out) {
+  return batch_create(models, n_models, dtype, max_ld, max_groups, opts, false, out);
+}
+
+// plain: every group is dense rows without side arrays (nb_batch_score rejects
+// others), which allows longer pipeline stages.
+nb_status nbg::batch_create(const nb_model* const* models, int n_models, nb_dtype dtype,
+                            int64_t max_ld, int max_groups, const nb_score_opts* opts, bool plain,
+                            nb_batch** out) {
   if (!out || !models || n_models < 1 || n_models > kSegMaxModels || max_groups < 1 ||
       elem_size(dtype) == 0) {
     set_error("nb_batch_create: need 1 <= n_models <= %d, max_groups >= 1, a valid dtype",
@@ -161,6 +177,7 @@ extern "C" nb_status nb_batch_create(const nb_model* const* models, int n_models
   b->F_pad = models[0]->F_pad;
   b->max_groups = max_groups;
   b->want_lp = opts ? opts->want_logpost : 0;
+  b->plain = plain;
   b->recheck = opts ? (int)opts->recheck : (int)NB_RECHECK_LP;
   for (int i = 0; i < n_models; ++i) {
     const int f = models[i]->C == 2 ? 0 : 1;
@@ -180,8 +197,8 @@ extern "C" nb_status nb_batch_create(const nb_model* const* models, int n_models
   };
   const int es = elem_size(dtype);
   if (!b->fam[0].empty()) {
-    nb_status s = seg2_plan(dtype, F, b->F_pad, max_ld * es, (int)b->fam[0].size(), &b->plan,
-                            &b->kv, &b->ncw, &b->smem);
+    nb_status s = seg2_plan(dtype, F, b->F_pad, max_ld * es, (int)b->fam[0].size(), plain,
+                            &b->plan, &b->kv, &b->rpw, &b->ncw, &b->smem);
     if (s != NB_OK) return fail(s);
   }
   b->maps_off = (kFamilies * sizeof(SegHeader) + kFamilies * (size_t)max_groups * sizeof(SegGroup) +
@@ -259,6 +276,10 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
       set_error("nb_batch_score: group %d: X must be 16-byte aligned, ld * element size a "
                 "multiple of 16 and ld <= the batch's max_ld",
                 i);
+      return NB_EINVAL;
+    }
+    if (b->plain && (g.aux.ovf_ptr || g.aux.row_exp)) {
+      set_error("nb_batch_score: group %d: this batch takes dense rows only", i);
       return NB_EINVAL;
     }
     if (g.aux.ovf_ptr && (!g.aux.ovf_col || !g.aux.ovf_add)) {

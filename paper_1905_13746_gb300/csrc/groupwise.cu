@@ -56,7 +56,7 @@ __device__ __forceinline__ int route_of(const int64_t* sizes, int64_t i, int64_t
   return m;
 }
 
-// Pass 1: group of every file, per-block counts per group (hist[g * nblk + b])
+// Pass 1: group of every file, per-block counts per group (hist[b * n_out + g])
 // and, with labels, files per (size group, class).
 __global__ void __launch_bounds__(kRouteWarps * 32)
     k_route_count(const int64_t* sizes, int64_t n, int64_t bin_bytes, int n_bins,
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kRouteWarps * 32)
     int s = 0;
 #pragma unroll
     for (int w = 0; w < kRouteWarps; ++w) s += cnt[w][g];
-    hist[(int64_t)g * gridDim.x + blockIdx.x] = s;
+    hist[(int64_t)blockIdx.x * n_out + g] = s;
   }
   if (y)
     for (int t = threadIdx.x; t < n_bins * C; t += blockDim.x)
@@ -100,51 +100,72 @@ __global__ void __launch_bounds__(kRouteWarps * 32)
                              (unsigned long long)ccnt[t]);
 }
 
-// Pass 2 (one block): exclusive scan of hist in place (group-major, so the
-// result is each block's first position per group) and offsets[g].
+// Pass 2 (one block of 1024 threads): thread (p, g), g < n_out, p < P =
+// 1024 / n_out, owns a slice of the blocks of column g of hist; it sums the
+// slice (coalesced across g), the slices' sums are scanned per group and the
+// group totals across groups (offsets[g], offsets[n_out] = n), then each
+// thread rewrites its slice as exclusive prefixes within the group: block b's
+// first position of group g is offsets[g] + hist[b * n_out + g].
 __global__ void __launch_bounds__(1024)
-    k_route_scan(int64_t* hist, int64_t L, int nblk, int n_out, int64_t* offsets) {
-  __shared__ int64_t wsum[32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t per = (L + blockDim.x - 1) / blockDim.x;
-  const int64_t a = t * per, b = a + per < L ? a + per : L;
+    k_route_scan(int64_t* hist, int nblk, int n_out, int64_t* offsets) {
+  __shared__ int64_t part[1024];
+  __shared__ int64_t tot[kRouteMaxGroups];
+  const int t = threadIdx.x;
+  const int P = 1024 / n_out;
+  const int g = t % n_out, p = t / n_out;
+  const bool on = p < P;
+  const int b0 = on ? (int)((int64_t)nblk * p / P) : 0;
+  const int b1 = on ? (int)((int64_t)nblk * (p + 1) / P) : 0;
   int64_t s = 0;
-  for (int64_t i = a; i < b; ++i) s += hist[i];
-  // block-wide exclusive scan of the per-thread sums
-  int64_t v = s;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int64_t u = __shfl_up_sync(0xFFFFFFFFu, v, off);
-    if (lane >= off) v += u;
-  }
-  if (lane == 31) wsum[warp] = v;
+#pragma unroll 4
+  for (int b = b0; b < b1; ++b) s += hist[(int64_t)b * n_out + g];
+  part[t] = on ? s : 0;
   __syncthreads();
-  if (warp == 0) {
-    int64_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+  int64_t start = 0, total = 0;
+  if (on) {
+    for (int q = 0; q < P; ++q) {
+      const int64_t v = part[q * n_out + g];
+      if (q < p) start += v;
+      total += v;
+    }
+    if (p == 0) tot[g] = total;
+  }
+  __syncthreads();
+  if (t < 32) {   // exclusive scan of the group totals by one warp
+    const int per = (n_out + 31) / 32;
+    const int a = t * per, e = min(n_out, a + per);
+    int64_t sum = 0;
+    for (int i = a; i < e; ++i) sum += tot[i];
+    int64_t v = sum;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const int64_t u = __shfl_up_sync(0xFFFFFFFFu, w, off);
-      if (lane >= off) w += u;
+      const int64_t u = __shfl_up_sync(0xFFFFFFFFu, v, off);
+      if (t >= off) v += u;
     }
-    wsum[lane] = w;   // inclusive over warps
+    int64_t run = v - sum;
+    for (int i = a; i < e; ++i) {
+      const int64_t x = tot[i];
+      tot[i] = run;
+      offsets[i] = run;
+      run += x;
+    }
+    if (t == 31) offsets[n_out] = v;
   }
-  __syncthreads();
-  int64_t run = v - s + (warp > 0 ? wsum[warp - 1] : 0);
-  for (int64_t i = a; i < b; ++i) {
-    const int64_t h = hist[i];
-    hist[i] = run;
-    run += h;
+  if (on) {
+    int64_t run = start;
+    for (int b = b0; b < b1; ++b) {
+      const int64_t h = hist[(int64_t)b * n_out + g];
+      hist[(int64_t)b * n_out + g] = run;
+      run += h;
+    }
   }
-  __syncthreads();
-  for (int g = t; g <= n_out; g += blockDim.x)
-    offsets[g] = g < n_out ? hist[(int64_t)g * nblk] : wsum[31];
 }
 
 // Pass 3: each file's position; ranks inside a warp step from the peers of
 // the same group, so the order within a group is the files' order (stable).
 __global__ void __launch_bounds__(kRouteWarps * 32)
     k_route_scatter(const int32_t* group, int64_t n, int n_out, const int64_t* first,
-                    int64_t* order) {
+                    const int64_t* offsets, int64_t* order) {
   __shared__ int cnt[kRouteWarps][kRouteMaxGroups];
   __shared__ int64_t run[kRouteWarps][kRouteMaxGroups / 2];   // two passes of 256 groups
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -166,7 +187,7 @@ __global__ void __launch_bounds__(kRouteWarps * 32)
     for (int t = threadIdx.x; t < kRouteMaxGroups / 2; t += blockDim.x) {
       const int g = g0 + t;
       if (g >= n_out) continue;
-      int64_t p = first[(int64_t)g * gridDim.x + blockIdx.x];
+      int64_t p = offsets[g] + first[(int64_t)blockIdx.x * n_out + g];
       for (int w = 0; w < kRouteWarps; ++w) {
         run[w][t] = p;
         p += cnt[w][g];
@@ -211,11 +232,12 @@ nb_status launch_route(const int64_t* sizes, int64_t n, int64_t bin_bytes, int n
       class_counts, status);
   NB_TRY_CUDA(cudaGetLastError(), "k_route_count launch");
   count_launch();
-  k_route_scan<<<1, 1024, 0, st>>>(hist, nblk * n_out, (int)nblk, n_out, offsets);
+  k_route_scan<<<1, 1024, 0, st>>>(hist, (int)nblk, n_out, offsets);
   NB_TRY_CUDA(cudaGetLastError(), "k_route_scan launch");
   if (order) {
     count_launch();
-    k_route_scatter<<<(unsigned)nblk, kRouteWarps * 32, 0, st>>>(group, n, n_out, hist, order);
+    k_route_scatter<<<(unsigned)nblk, kRouteWarps * 32, 0, st>>>(group, n, n_out, hist,
+                                                                  offsets, order);
     NB_TRY_CUDA(cudaGetLastError(), "k_route_scatter launch");
   }
   return NB_OK;
@@ -381,6 +403,125 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// u8 rows through shared memory.  A warp takes chunks of 32 consecutive
+// output rows; lane j loads row j's source index and group once per chunk (the
+// next chunk's while the current one is gathered), so no row waits on a
+// dependent index load.  Each row is copied with 16-byte cp.async copies
+// (coalesced, one HBM pass) while the previous one is gathered (two buffers
+// per warp); the group's selection stays in shared memory while consecutive
+// rows share the group (rows come sorted by group); bytes are gathered from
+// shared memory, four per lane per output word.
+constexpr int kGatherWarps = 8;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// source row (-1: none) and group (-1: none) of output row r
+__device__ __forceinline__ void gather_index(int64_t r, int64_t n, const int64_t* order,
+                                             const int32_t* group, int n_groups, int64_t n_src,
+                                             int64_t* i, int* g) {
+  *i = -1;
+  *g = -1;
+  if (r >= n) return;
+  int64_t s = order ? order[r] : r;
+  if (s < 0 || s >= n_src) return;
+  *i = s;
+  int gg = group ? group[s] : 0;
+  *g = gg < 0 || gg >= n_groups ? -1 : gg;
+}
+
+__global__ void __launch_bounds__(kGatherWarps * 32)
+    k_gather_u8s(const unsigned char* X, int64_t ld, int F, int64_t n_src, int64_t n,
+                 const int64_t* order, const int32_t* group, int n_groups, const int32_t* cols,
+                 int k, unsigned char* out, int64_t ld_out, int row_bytes, int* status) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* buf = gsm + (size_t)warp * 2 * row_bytes;
+  const int kq = (k + 3) & ~3;   // selection stride: 16-byte aligned rows of sel
+  int32_t* sel = reinterpret_cast<int32_t*>(gsm + (size_t)kGatherWarps * 2 * row_bytes) +
+                 (size_t)warp * kq;
+  const int nv = (F + 15) >> 4;
+  const int64_t nchunks = (n + 31) / 32;
+  const int64_t wstride = (int64_t)gridDim.x * kGatherWarps;
+  int64_t c = (int64_t)blockIdx.x * kGatherWarps + warp;
+  if (c >= nchunks) return;
+  // lane j: source row and group of row j of the current and the next chunk
+  int64_t ci, ni;
+  int cg, ng;
+  gather_index(c * 32 + lane, n, order, group, n_groups, n_src, &ci, &cg);
+  gather_index((c + wstride) * 32 + lane, n, order, group, n_groups, n_src, &ni, &ng);
+  auto fetch = [&](int64_t i, unsigned char* dst) {
+    if (i >= 0) {
+      const unsigned char* src = X + i * ld;
+      for (int v = lane; v < nv; v += 32) cp_async16(dst + 16 * v, src + 16 * v);
+    }
+    cp_async_commit();
+  };
+  fetch(__shfl_sync(0xFFFFFFFFu, ci, 0), buf);
+  int held = -2;   // group whose selection sel holds (-1: identity)
+  int b = 0;
+  for (; c < nchunks; c += wstride) {
+    const int rows = (int)min((int64_t)32, n - c * 32);
+    for (int j = 0; j < rows; ++j, b ^= 1) {
+      const int64_t i = __shfl_sync(0xFFFFFFFFu, ci, j);
+      const int g = __shfl_sync(0xFFFFFFFFu, cg, j);
+      // the next row (this chunk's j + 1, else the next chunk's first) lands meanwhile
+      const int64_t inext = j + 1 < rows ? __shfl_sync(0xFFFFFFFFu, ci, (j + 1) & 31)
+                                         : __shfl_sync(0xFFFFFFFFu, ni, 0);
+      fetch(inext, buf + (size_t)(b ^ 1) * row_bytes);
+      cp_async_wait1();   // this thread's copies of the current row
+      const bool bad = i < 0 || g < 0;
+      if (bad && lane == 0) atomicOr(status, ST_BAD_ROUTE);
+      const int want = cols ? g : -1;
+      if (!bad && want != held) {
+        for (int t = lane; t < k; t += 32) sel[t] = cols ? cols[(int64_t)g * k + t] : t;
+        held = want;
+      }
+      __syncwarp();       // every lane's copies and sel visible
+      const unsigned char* row = buf + (size_t)b * row_bytes;
+      uint32_t* dst = reinterpret_cast<uint32_t*>(out + (c * 32 + j) * ld_out);
+      for (int64_t t0 = 4 * lane; t0 < ld_out; t0 += 128) {
+        uint32_t w = 0;
+        if (!bad && t0 + 3 < k) {
+          const int4 c4 = *reinterpret_cast<const int4*>(sel + t0);
+          const unsigned cmax = max(max((unsigned)c4.x, (unsigned)c4.y),
+                                    max((unsigned)c4.z, (unsigned)c4.w));
+          if (cmax < (unsigned)F) {
+            w = (uint32_t)row[c4.x] | ((uint32_t)row[c4.y] << 8) | ((uint32_t)row[c4.z] << 16) |
+                ((uint32_t)row[c4.w] << 24);
+          } else {
+            atomicOr(status, ST_BAD_ROUTE);
+          }
+        } else if (!bad) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int t = (int)t0 + q;
+            if (t < k) {
+              const int cc = sel[t];
+              if ((unsigned)cc < (unsigned)F) w |= (uint32_t)row[cc] << (8 * q);
+              else atomicOr(status, ST_BAD_ROUTE);
+            }
+          }
+        }
+        dst[t0 >> 2] = w;
+      }
+      __syncwarp();       // buffer b is free for the row after next
+    }
+    ci = ni;
+    cg = ng;
+    gather_index((c + 2 * wstride) * 32 + lane, n, order, group, n_groups, n_src, &ni, &ng);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 nb_status launch_gather(const void* X, nb_dtype dt, int64_t ld, int F, int64_t n_src,
                         int64_t n, const int64_t* order, const int32_t* group, int n_groups,
                         const int32_t* cols, int k, void* out, int64_t ld_out, int* status,
@@ -389,6 +530,28 @@ nb_status launch_gather(const void* X, nb_dtype dt, int64_t ld, int F, int64_t n
   int64_t blocks = (n + 7) / 8;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
+  int64_t cblocks = ((n + 31) / 32 + kGatherWarps - 1) / kGatherWarps;   // 32-row chunks
+  if (cblocks > cap) cblocks = cap;
+  // staged u8 path: 16-byte aligned rows whose copies and selections fit
+  const int row_bytes = (F + 15) / 16 * 16;
+  const size_t smem =
+      (size_t)kGatherWarps * 2 * row_bytes + (size_t)kGatherWarps * ((k + 3) & ~3) * 4;
+  if (elem_size(dt) == 1 && (ld % 16) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+      smem <= 96 * 1024) {
+    static int configured = 0;
+    if ((int)smem > kSmemOptIn && configured < (int)smem) {
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_gather_u8s, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem),
+                  "cudaFuncSetAttribute(gather)");
+      configured = (int)smem;
+    }
+    count_launch();
+    k_gather_u8s<<<(unsigned)cblocks, kGatherWarps * 32, smem, st>>>(
+        static_cast<const unsigned char*>(X), ld, F, n_src, n, order, group, n_groups, cols, k,
+        static_cast<unsigned char*>(out), ld_out, row_bytes, status);
+    NB_TRY_CUDA(cudaGetLastError(), "k_gather_u8s launch");
+    return NB_OK;
+  }
   count_launch();
   if (elem_size(dt) == 1)
     k_gather<1><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const char*>(X), ld, F, n_src, n,
@@ -406,13 +569,45 @@ nb_status launch_gather(const void* X, nb_dtype dt, int64_t ld, int F, int64_t n
 // device-built work list of the batched two-class launch: group m = the rows
 // offsets[m] .. offsets[m+1]-1 of the gathered matrix, scored by model slot m
 // ---------------------------------------------------------------------------
-__global__ void k_gw_worklist(SegHeader* hdr, SegGroup* list, int n_models,
-                              const int64_t* offsets, const char* xs, int64_t ld_bytes,
-                              uint8_t* label, float* margin, float* logpost, int64_t rs) {
-  if (threadIdx.x != 0) return;
-  long long tiles = 0, chunks = 0;
-  for (int m = 0; m < n_models; ++m) {
-    const int64_t o = offsets[m], nm = offsets[m + 1] - o;
+__global__ void __launch_bounds__(128)
+    k_gw_worklist(SegHeader* hdr, SegGroup* list, int n_models, const int64_t* offsets,
+                  const char* xs, int64_t ld_bytes, uint8_t* label, float* margin,
+                  float* logpost, int64_t rs) {
+  // one thread per model slot (n_models <= 128); first tiles and chunks by a
+  // block-wide exclusive scan
+  __shared__ long long wt[4], wc[4];
+  const int m = threadIdx.x, lane = m & 31, warp = m >> 5;
+  int64_t o = 0, nm = 0;
+  if (m < n_models) {
+    o = offsets[m];
+    nm = offsets[m + 1] - o;
+  }
+  const long long t = (nm + rs - 1) / rs, c = (nm + 31) / 32;
+  long long it = t, ic = c;   // inclusive scans within the warp
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const long long ut = __shfl_up_sync(0xFFFFFFFFu, it, off);
+    const long long uc = __shfl_up_sync(0xFFFFFFFFu, ic, off);
+    if (lane >= off) {
+      it += ut;
+      ic += uc;
+    }
+  }
+  if (lane == 31) {
+    wt[warp] = it;
+    wc[warp] = ic;
+  }
+  __syncthreads();
+  long long bt = 0, bc = 0, tt = 0, tc = 0;
+  for (int w = 0; w < 4; ++w) {
+    if (w < warp) {
+      bt += wt[w];
+      bc += wc[w];
+    }
+    tt += wt[w];
+    tc += wc[w];
+  }
+  if (m < n_models) {
     SegGroup& d = list[m];
     d.X = xs + o * ld_bytes;
     d.ld_bytes = ld_bytes;
@@ -424,19 +619,17 @@ __global__ void k_gw_worklist(SegHeader* hdr, SegGroup* list, int n_models,
     d.label = label + o;
     d.margin = margin + o;
     d.logpost = logpost ? logpost + 2 * o : nullptr;
-    d.tile0 = tiles;
-    d.chunk0 = chunks;
+    d.tile0 = bt + it - t;
+    d.chunk0 = bc + ic - c;
     d.model = m;
     d.family = 0;
-    tiles += (nm + rs - 1) / rs;
-    chunks += (nm + 31) / 32;
   }
-  for (int f = 0; f < 3; ++f) {
-    hdr[f].n_groups = f == 0 ? n_models : 0;
-    hdr[f].pad = 0;
-    hdr[f].tiles = f == 0 ? tiles : 0;
-    hdr[f].chunks = f == 0 ? chunks : 0;
-    hdr[f].pad2 = 0;
+  if (m < 3) {
+    hdr[m].n_groups = m == 0 ? n_models : 0;
+    hdr[m].pad = 0;
+    hdr[m].tiles = m == 0 ? tt : 0;
+    hdr[m].chunks = m == 0 ? tc : 0;
+    hdr[m].pad2 = 0;
   }
 }
 
@@ -591,6 +784,9 @@ struct nb_groupwise {
 namespace nbg {
 // batch.cu
 nb_status batch_device_list(nb_batch* b, SegHeader** hdr, SegGroup** list0, int64_t* rs);
+nb_status batch_create(const nb_model* const* models, int n_models, nb_dtype dtype,
+                       int64_t max_ld, int max_groups, const nb_score_opts* opts, bool plain,
+                       nb_batch** out);
 nb_status batch_launch_device(nb_batch* b, cudaStream_t st, int64_t* n_rechecked);
 }  // namespace nbg
 
@@ -648,7 +844,7 @@ extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t 
     nb_groupwise_destroy(g);
     return s;
   };
-  nb_status s = nb_batch_create(models, n_models, dtype, g->ld_out, n_models, opts, &g->batch);
+  nb_status s = batch_create(models, n_models, dtype, g->ld_out, n_models, opts, true, &g->batch);
   if (s != NB_OK) return fail(s);
   // one allocation, 256-byte aligned pieces
   size_t off = 0;
@@ -715,7 +911,7 @@ extern "C" nb_status nb_groupwise_classify(nb_groupwise* g, const void* X, int64
   s = batch_device_list(g->batch, &hdr, &list0, &rs);
   if (s != NB_OK) return s;
   count_launch();
-  k_gw_worklist<<<1, 32, 0, st>>>(hdr, list0, g->n_models, g->offsets, g->xs,
+  k_gw_worklist<<<1, 128, 0, st>>>(hdr, list0, g->n_models, g->offsets, g->xs,
                                   g->ld_out * elem_size(g->dtype), g->label_s, g->margin_s,
                                   g->want_lp ? g->lp_s : nullptr, rs);
   NB_TRY_CUDA(cudaGetLastError(), "k_gw_worklist launch");

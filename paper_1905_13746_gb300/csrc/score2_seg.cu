@@ -58,12 +58,14 @@ struct SegSrc {
   }
 };
 
-template <int DT, int KV, int NCW>
+template <int DT, int KV, int RPW, int NCW>
 __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
     k_score2_seg(const SegArgs a, PipeArgs p) {
+  constexpr int LPR = 32 / RPW;   // lanes per row: RPW rows per warp pass
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t full[kMaxStages], empty[kMaxStages], tabbar;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / LPR, li = lane % LPR;
   const int n_groups = a.hdr->n_groups;
   const long long tiles = a.hdr->tiles;
   const long long t0 = tiles * blockIdx.x / gridDim.x;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
         limb = reinterpret_cast<const signed char*>(tb);
 #pragma unroll
         for (int kv = 0; kv < KV; ++kv) {
-          const int v = lane + 32 * kv;
+          const int v = li + LPR * kv;
           if (DT == NB_U8) {
             const uint4* tab = reinterpret_cast<const uint4*>(tb);
             const uint4 z = make_uint4(0, 0, 0, 0);
@@ -187,15 +189,17 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
     const long long* sp = reinterpret_cast<const long long*>(st + p.ptr_off);
     const uint16_t* scol = reinterpret_cast<const uint16_t*>(st + p.col_off);
     const uint16_t* sadd = reinterpret_cast<const uint16_t*>(st + p.add_off);
-    for (int r = warp; r < nr; r += NCW) {
-      if (nres == 32) finish();
-      const unsigned char* rp = st + (size_t)r * ld_bytes;
+    for (int r0 = warp * RPW; r0 < nr; r0 += NCW * RPW) {
+      if (nres + RPW > 32) finish();
+      const int r = r0 + grp;             // this lane group's row
+      const bool valid = r < nr;
+      const unsigned char* rp = st + (size_t)(valid ? r : 0) * ld_bytes;
       int c0[2] = {0, 0}, c1[2] = {0, 0}, c2[2] = {0, 0};   // even / odd vector chains
       uint32_t ct[2] = {0u, 0u};
       float acc[4] = {0.f, 0.f, 0.f, 0.f}, tf = 0.f;
 #pragma unroll
       for (int kv = 0; kv < KV; ++kv) {
-        const int v = lane + 32 * kv, e = kv & 1;
+        const int v = li + LPR * kv, e = kv & 1;
         if (v < nv) {
           uint4 x = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
           if (DT == NB_U8) {
@@ -240,9 +244,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
       }
       int a0 = c0[0] + c0[1], a1 = c1[0] + c1[1], a2 = c2[0] + c2[1];
       uint32_t tt = ct[0] + ct[1];
-      if (DT == NB_U8 && G.ovf_ptr) {
+      if (DT == NB_U8 && G.ovf_ptr && valid) {
         const long long k0 = sp[r], k1 = sp[r + 1];
-        for (long long e = k0 + lane; e < k1; e += 32) {
+        for (long long e = k0 + li; e < k1; e += LPR) {
           const uint32_t col = in_smem ? scol[e - ebase] : G.ovf_col[e];
           const int add = in_smem ? sadd[e - ebase] : G.ovf_add[e];
           if (col < (uint32_t)a.F) {
@@ -256,43 +260,51 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
           }
         }
       }
-      int s0 = 0, s1 = 0, s2 = 0;
-      uint32_t st_ = 0;
-      float ss = 0.f, stf = 0.f;
+      // lane nres + j takes row r0 + j of this pass from its group's first lane
+      const int src = (lane - nres) * LPR;
+      const bool take = lane >= nres && lane < nres + RPW && r0 + (lane - nres) < nr;
+      const int sl = take ? src : 0;
       if (DT == NB_U8) {
-        const int k = sum4_transposed<32>(a0, a1, a2, (int)tt, lane);
-        s0 = __shfl_sync(0xFFFFFFFFu, k, 0);
-        s1 = __shfl_sync(0xFFFFFFFFu, k, 8);
-        s2 = __shfl_sync(0xFFFFFFFFu, k, 16);
-        st_ = (uint32_t)__shfl_sync(0xFFFFFFFFu, k, 24);
+        // the group's four sums end up in its four lane quarters
+        const int k4 = sum4_transposed<LPR>(a0, a1, a2, (int)tt, li);
+        const int s0 = __shfl_sync(0xFFFFFFFFu, k4, sl);
+        const int s1 = __shfl_sync(0xFFFFFFFFu, k4, sl + LPR / 4);
+        const int s2 = __shfl_sync(0xFFFFFFFFu, k4, sl + LPR / 2);
+        const uint32_t st_ = (uint32_t)__shfl_sync(0xFFFFFFFFu, k4, sl + 3 * LPR / 4);
+        if (take) {
+          ra0 = s0, ra1 = s1, ra2 = s2, rt = st_;
+        }
       } else {
         float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
+        for (int off = LPR / 2; off > 0; off >>= 1) {
           sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
           tf += __shfl_xor_sync(0xFFFFFFFFu, tf, off);
         }
-        ss = sum, stf = tf;
+        const float ss = __shfl_sync(0xFFFFFFFFu, sum, sl);
+        const float stf = __shfl_sync(0xFFFFFFFFu, tf, sl);
+        if (take) {
+          rs = ss, rtf = stf;
+        }
       }
-      if (lane == nres) {
-        ra0 = s0, ra1 = s1, ra2 = s2, rt = st_, rs = ss, rtf = stf;
-        rrow = row0 + r;
+      if (take) {
+        rrow = row0 + r0 + (lane - nres);
         rgrp = g;
       }
-      ++nres;
+      nres += (nr - r0) < RPW ? (nr - r0) : RPW;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
-    if (nres >= 24) finish();
+    if (nres + RPW > 32) finish();
   }
   finish();
 }
 
 // ---------------------------------------------------------------------------
-template <int DT, int KV, int NCW>
+template <int DT, int KV, int RPW, int NCW>
 static nb_status run_seg(const SegArgs& a, const PipeArgs& p, int smem, int* grid,
                          cudaStream_t st) {
-  auto kern = k_score2_seg<DT, KV, NCW>;
+  auto kern = k_score2_seg<DT, KV, RPW, NCW>;
   if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(seg)");
@@ -311,30 +323,47 @@ static nb_status run_seg(const SegArgs& a, const PipeArgs& p, int smem, int* gri
 }
 
 // Plan of a segmented two-class launch for rows of at most max_ld_bytes.
+// u8 rows of up to 16 (32) vectors take 8 (16) lanes per row, four (two) rows
+// per warp pass, so that short rows (a few hundred selected opcodes) keep all
+// lanes busy; exact integer sums make the result independent of the shape.
+// FP32 rows keep 32 lanes per row (their reduction order is that of the
+// single-group scorer).
+//
+// Rows per stage: at most 48 when groups may carry side arrays (the producer's
+// lanes hold the overflow pointers of a tile), up to 240 for plain rows, so
+// that stages of short rows still move tens of KB.
 nb_status seg2_plan(nb_dtype dt, int F, int F_pad, long long max_ld_bytes, int n_models,
-                    PipeArgs* p, int* kv_out, int* ncw_out, int* smem_out) {
+                    bool plain_rows, PipeArgs* p, int* kv_out, int* rpw_out, int* ncw_out,
+                    int* smem_out) {
   const int es = elem_size(dt);
   const int nvec_row = (F * es + 15) / 16;
-  const int kv = (nvec_row + 31) / 32;
+  const int rpw = dt == NB_U8 ? (nvec_row <= 16 ? 4 : (nvec_row <= 32 ? 2 : 1)) : 1;
+  const int lpr = 32 / rpw;
+  const int kv = (nvec_row + lpr - 1) / lpr;
   const int kv_max = dt == NB_F32 ? 8 : 4;
   if (kv < 1 || kv > kv_max || max_ld_bytes > 8192) {
     set_error("batched two-class scoring supports rows of at most %d vectors and 8 KB",
               32 * kv_max);
     return NB_EUNSUPPORTED;
   }
-  const int ncw = (dt == NB_F32 ? kv <= 8 : kv <= 2) ? 8 : 12;
+  const int ncw = rpw > 1 ? 12 : ((dt == NB_F32 ? kv <= 8 : kv <= 2) ? 8 : 12);
   const uint32_t tab = dt == NB_U8 ? (uint32_t)(3 * F_pad) : (uint32_t)(4 * F_pad);
   const uint32_t stride = (tab + 127) / 128 * 128;
-  long long per = 32768 / ((long long)ncw * max_ld_bytes);
-  int rs = ncw * (int)(per > 0 ? per : 1);
-  if (rs > kMaxStageRows) rs = kMaxStageRows;
+  long long per = 32768 / ((long long)ncw * rpw * max_ld_bytes);
+  int rs = ncw * rpw * (int)(per > 0 ? per : 1);
+  const int max_rows = plain_rows ? 240 : kMaxStageRows;
+  if (rs > max_rows) {
+    rs = max_rows - max_rows % (ncw * rpw);   // whole warp passes
+    if (rs < 1) rs = max_rows;
+  }
   const unsigned budget = ncw == 8 ? 100u * 1024u : 180u * 1024u;
   PipeArgs q{};
-  pipe_layout(q, rs, 1, max_ld_bytes, true, false, stride * (uint32_t)n_models, 0);
+  pipe_layout(q, rs, 1, max_ld_bytes, !plain_rows, false, stride * (uint32_t)n_models, 0);
   int S = q.stages_off + q.stage_bytes > budget ? 2 : (int)((budget - q.stages_off) / q.stage_bytes);
   S = S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
-  pipe_layout(*p, rs, S, max_ld_bytes, true, false, stride * (uint32_t)n_models, 0);
+  pipe_layout(*p, rs, S, max_ld_bytes, !plain_rows, false, stride * (uint32_t)n_models, 0);
   *kv_out = kv;
+  *rpw_out = rpw;
   *ncw_out = ncw;
   *smem_out = (int)(p->stages_off + (uint32_t)p->S * p->stage_bytes);
   if (*smem_out > 220 * 1024) {
@@ -344,15 +373,17 @@ nb_status seg2_plan(nb_dtype dt, int F, int F_pad, long long max_ld_bytes, int n
   return NB_OK;
 }
 
-nb_status launch_score2_seg(const SegArgs& a, const PipeArgs& p, nb_dtype dt, int kv, int ncw,
-                            int smem, int* grid, cudaStream_t st) {
-#define NB_SEG_CASE(D, K, N) \
-  if (dt == D && kv == K && ncw == N) return run_seg<D, K, N>(a, p, smem, grid, st);
-  NB_SEG_CASE(NB_U8, 1, 8) NB_SEG_CASE(NB_U8, 2, 8) NB_SEG_CASE(NB_U8, 3, 12)
-  NB_SEG_CASE(NB_U8, 4, 12)
-  NB_SEG_CASE(NB_F32, 1, 8) NB_SEG_CASE(NB_F32, 2, 8) NB_SEG_CASE(NB_F32, 3, 8)
-  NB_SEG_CASE(NB_F32, 4, 8) NB_SEG_CASE(NB_F32, 5, 8) NB_SEG_CASE(NB_F32, 6, 8)
-  NB_SEG_CASE(NB_F32, 7, 8) NB_SEG_CASE(NB_F32, 8, 8)
+nb_status launch_score2_seg(const SegArgs& a, const PipeArgs& p, nb_dtype dt, int kv, int rpw,
+                            int ncw, int smem, int* grid, cudaStream_t st) {
+#define NB_SEG_CASE(D, K, R, N) \
+  if (dt == D && kv == K && rpw == R && ncw == N) return run_seg<D, K, R, N>(a, p, smem, grid, st);
+  NB_SEG_CASE(NB_U8, 1, 1, 8) NB_SEG_CASE(NB_U8, 2, 1, 8) NB_SEG_CASE(NB_U8, 3, 1, 12)
+  NB_SEG_CASE(NB_U8, 4, 1, 12)
+  NB_SEG_CASE(NB_U8, 1, 4, 12) NB_SEG_CASE(NB_U8, 2, 4, 12)
+  NB_SEG_CASE(NB_U8, 1, 2, 12) NB_SEG_CASE(NB_U8, 2, 2, 12)
+  NB_SEG_CASE(NB_F32, 1, 1, 8) NB_SEG_CASE(NB_F32, 2, 1, 8) NB_SEG_CASE(NB_F32, 3, 1, 8)
+  NB_SEG_CASE(NB_F32, 4, 1, 8) NB_SEG_CASE(NB_F32, 5, 1, 8) NB_SEG_CASE(NB_F32, 6, 1, 8)
+  NB_SEG_CASE(NB_F32, 7, 1, 8) NB_SEG_CASE(NB_F32, 8, 1, 8)
 #undef NB_SEG_CASE
   set_error("batched two-class scoring supports u8 and f32 storage");
   return NB_EUNSUPPORTED;

@@ -63,9 +63,10 @@ struct PipeArgs;
 
 // launchers (score2_seg.cu, score_general.cu, recheck.cu)
 nb_status seg2_plan(nb_dtype dt, int F, int F_pad, long long max_ld_bytes, int n_models,
-                    PipeArgs* p, int* kv_out, int* ncw_out, int* smem_out);
-nb_status launch_score2_seg(const SegArgs& a, const PipeArgs& p, nb_dtype dt, int kv, int ncw,
-                            int smem, int* grid, cudaStream_t st);
+                    bool plain_rows, PipeArgs* p, int* kv_out, int* rpw_out, int* ncw_out,
+                    int* smem_out);
+nb_status launch_score2_seg(const SegArgs& a, const PipeArgs& p, nb_dtype dt, int kv, int rpw,
+                            int ncw, int smem, int* grid, cudaStream_t st);
 nb_status launch_score_gen_seg(const SegGroup* groups, const SegHeader* hdr,
                                const nb_model* const* models, int n_models, nb_dtype dt, int F,
                                int want_lp, int recheck, int* status, cudaStream_t st);
