@@ -445,12 +445,19 @@ NB_API nb_status nb_gather(const void* X, nb_dtype dtype, int64_t ld, int32_t F,
  *   F32; max_files per call; score options.  Allocates all scratch.
  * nb_groupwise_classify: X (device, n x ld, ld >= F_full) full histograms,
  *   sizes (device int64[n]); label / margin / logpost (n x 2 or NULL) device,
- *   in the files' order.  Routes the files (nb_route), gathers each file's
- *   model's opcodes into a dense matrix ordered by group (nb_gather), scores
- *   every group in one batched launch whose work list a kernel builds on the
- *   device (no host synchronisation), rechecks in FP64 as nb_score_group
- *   does, and scatters the results back: every file's results equal
- *   nb_score_group of its model on its gathered row.  Asynchronous.
+ *   in the files' order.  U8 histograms with 16-byte aligned rows take one
+ *   fused launch: every model's weights and opcode selection sit in shared
+ *   memory, each row finds its model from its size and is scored on its
+ *   selected counts straight from the streamed histogram, then the FP64
+ *   recheck (two launches in all).  Otherwise -- F32 histograms, unaligned
+ *   rows, or models whose tables exceed shared memory -- the files are routed
+ *   (nb_route), each file's model's opcodes gathered into a dense matrix
+ *   ordered by group (nb_gather), every group scored in one batched launch
+ *   whose work list a kernel builds on the device, rechecked in FP64, and the
+ *   results scattered back (eight launches).  No host synchronisation either
+ *   way; every file's results equal nb_score_group of its model on its
+ *   gathered row.  Asynchronous.  The models must not be re-fitted while the
+ *   object exists (the fused path keeps a copy of their u8 tables).
  * nb_groupwise_status: reads (synchronously) the object's status word (32:
  *   a bad size or column was met).  nb_groupwise_destroy frees everything. */
 typedef struct nb_groupwise nb_groupwise;

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "pipe.cuh"
+#include "score2.cuh"
 #include "seg.cuh"
 
 namespace nbg {
@@ -650,6 +651,159 @@ __global__ void k_gw_unpermute(const int64_t* order, int64_t n, const uint8_t* l
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused group-wise scorer (u8 histograms, two-class models on k opcodes): one
+// streaming pass over the full histograms in the files' order.  A pack staged
+// once per block in shared memory holds every model's int8 weight limbs (three
+// planes of kp bytes, feature t at byte t), its selection (kp uint16 opcode
+// indices), its two-class header, and the model slot of each size group.  The
+// producer warp streams RS-row tiles of the histograms (pipe.cuh); a row's 8
+// lanes find its model from its size, gather its k selected counts from the
+// staged row four at a time and accumulate them against the model's limbs
+// with dp4a -- the same integer sums as scoring the gathered row, so the
+// outputs are the same bits -- and the finished rows go straight to the
+// outputs in the files' order.
+// ---------------------------------------------------------------------------
+constexpr int kGwLPR = 8;                  // lanes per row
+constexpr int kGwRPW = 32 / kGwLPR;        // rows per warp pass
+constexpr int kGwNCW = 12;                 // consumer warps
+
+struct GwArgs {
+  const char* X;
+  int64_t ld_bytes;
+  int64_t n;
+  const int64_t* sizes;
+  int64_t bin_bytes;
+  int n_bins, k, kp, kw;   // kw = ceil(k / 4) words of four features
+  const void* pack;
+  uint32_t pack_bytes, sel_off, hdr_off, map_off;
+  uint8_t* label;
+  float* margin;
+  float* logpost;
+  int want_lp, recheck;
+  int* status;
+};
+
+__global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
+    k_score_gw(const GwArgs a, const PipeArgs p) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages], tabbar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / kGwLPR, li = lane % kGwLPR;
+  const long long t0 = p.tiles * blockIdx.x / gridDim.x;
+  const long long t1 = p.tiles * (blockIdx.x + 1) / gridDim.x;
+  const long long ntl = t1 - t0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kGwNCW);
+    }
+    mbar_init(&tabbar, 1);
+  }
+  __syncthreads();
+  if (warp == kGwNCW) {
+    const PipeSrc src{a.X, a.ld_bytes, a.n, nullptr, nullptr, nullptr, nullptr, a.pack,
+                      a.status};
+    pipe_produce(src, p, sm, full, empty, &tabbar, t0, ntl);
+    return;
+  }
+  if (!mbar_wait_bounded(&tabbar, 0)) {
+    if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+    return;
+  }
+  const unsigned char* limbs = sm;                                      // model m at m * 3 kp
+  const uint16_t* sels = reinterpret_cast<const uint16_t*>(sm + a.sel_off);   // m * kp
+  const C2Header* hdrs = reinterpret_cast<const C2Header*>(sm + a.hdr_off);
+  const unsigned char* map = sm + a.map_off;                            // size group -> slot
+  // valid bytes of the last four-feature word
+  const int kt = a.k - 4 * (a.kw - 1);
+  const uint32_t tail_mask = kt >= 4 ? 0xFFFFFFFFu : ((1u << (8 * kt)) - 1u);
+
+  int ra0 = 0, ra1 = 0, ra2 = 0, rmod = 0;
+  uint32_t rt = 0;
+  long long rrow = -1;
+  int nres = 0;
+  auto finish = [&]() {
+    if (lane < nres) {
+      const C2Header& H = hdrs[rmod];
+      const long long D = ((long long)ra2 << 16) + ((long long)ra1 << 8) + (long long)ra0;
+      const float Dsum = (float)D * H.inv_scale;
+      const float d = Dsum + H.b;
+      const float tau = c2_tau_u8((float)rt, Dsum, H.b, H.inv_scale, H.maxabs);
+      c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, rrow, d, tau);
+    }
+    nres = 0;
+  };
+
+  for (long long k = 0; k < ntl; ++k) {
+    const int s = (int)(k % p.S);
+    const uint32_t ph = (uint32_t)((k / p.S) & 1);
+    if (!mbar_wait_bounded(&full[s], ph)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      return;
+    }
+    const unsigned char* st = sm + p.stages_off + (size_t)s * p.stage_bytes;
+    const StageMeta* mp = reinterpret_cast<const StageMeta*>(st + p.meta_off);
+    const int nr = mp->nr;
+    const long long row0 = mp->row0;
+    for (int r0 = warp * kGwRPW; r0 < nr; r0 += kGwNCW * kGwRPW) {
+      if (nres + kGwRPW > 32) finish();
+      const int r = r0 + grp;
+      const bool valid = r < nr;
+      int m = 0;
+      if (valid) {
+        long long sz = a.sizes[row0 + r];
+        if (sz < 0) {
+          if (li == 0) atomicOr(a.status, ST_BAD_ROUTE);
+          sz = 0;
+        }
+        long long bin = sz / a.bin_bytes;
+        if (bin > a.n_bins - 1) bin = a.n_bins - 1;
+        m = map[bin];
+      }
+      int c0 = 0, c1 = 0, c2 = 0;
+      uint32_t ct = 0;
+      if (valid) {
+        const unsigned char* rp = st + (size_t)r * a.ld_bytes;
+        const uint16_t* sg = sels + (size_t)m * a.kp;
+        const unsigned char* lg = limbs + (size_t)m * 3 * a.kp;
+        for (int w = li; w < a.kw; w += kGwLPR) {
+          const uint2 cc = *reinterpret_cast<const uint2*>(sg + 4 * w);
+          uint32_t x = (uint32_t)rp[cc.x & 0xFFFFu] | ((uint32_t)rp[cc.x >> 16] << 8) |
+                       ((uint32_t)rp[cc.y & 0xFFFFu] << 16) | ((uint32_t)rp[cc.y >> 16] << 24);
+          if (w == a.kw - 1) x &= tail_mask;
+          const uint32_t l0 = *reinterpret_cast<const uint32_t*>(lg + 4 * w);
+          const uint32_t l1 = *reinterpret_cast<const uint32_t*>(lg + a.kp + 4 * w);
+          const uint32_t l2 = *reinterpret_cast<const uint32_t*>(lg + 2 * a.kp + 4 * w);
+          c0 = dp4a_us(x, l0, c0);
+          c1 = dp4a_us(x, l1, c1);
+          c2 = dp4a_us(x, l2, c2);
+          ct = dp4a_uu(x, 0x01010101u, ct);
+        }
+      }
+      const int k4 = sum4_transposed<kGwLPR>(c0, c1, c2, (int)ct, li);
+      // lane nres + j takes row r0 + j of this pass from its group's first lane
+      const int src = (lane - nres) * kGwLPR;
+      const bool take = lane >= nres && lane < nres + kGwRPW && r0 + (lane - nres) < nr;
+      const int sl = take ? src : 0;
+      const int s0 = __shfl_sync(0xFFFFFFFFu, k4, sl);
+      const int s1 = __shfl_sync(0xFFFFFFFFu, k4, sl + kGwLPR / 4);
+      const int s2 = __shfl_sync(0xFFFFFFFFu, k4, sl + kGwLPR / 2);
+      const uint32_t sT = (uint32_t)__shfl_sync(0xFFFFFFFFu, k4, sl + 3 * kGwLPR / 4);
+      const int sm_ = __shfl_sync(0xFFFFFFFFu, m, sl);
+      if (take) {
+        ra0 = s0, ra1 = s1, ra2 = s2, rt = sT, rmod = sm_;
+        rrow = row0 + r0 + (lane - nres);
+      }
+      nres += (nr - r0) < kGwRPW ? (nr - r0) : kGwRPW;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (nres + kGwRPW > 32) finish();
+  }
+  finish();
+}
+
 }  // namespace nbg
 
 using namespace nbg;
@@ -764,7 +918,7 @@ extern "C" nb_status nb_gather(const void* X, nb_dtype dtype, int64_t ld, int32_
 // ---------------------------------------------------------------------------
 struct nb_groupwise {
   nb_batch* batch = nullptr;
-  int n_models = 0, k = 0, F_full = 0, n_bins = 0, want_lp = 0;
+  int n_models = 0, k = 0, F_full = 0, n_bins = 0, want_lp = 0, recheck = NB_RECHECK_LP;
   int64_t bin_bytes = 0, max_files = 0, ld_out = 0;
   nb_dtype dtype = NB_U8;
   void* mem = nullptr;        // one device allocation for everything below
@@ -779,6 +933,11 @@ struct nb_groupwise {
   float* margin_s = nullptr;
   float* lp_s = nullptr;
   int* status = nullptr;
+  // fused scorer (u8): the shared-memory pack and its layout
+  std::vector<const nb_model*> models;
+  unsigned char* pack = nullptr;
+  uint32_t pack_bytes = 0, sel_off = 0, hdr_off = 0, map_off = 0;
+  int kp = 0;
 };
 
 namespace nbg {
@@ -788,6 +947,11 @@ nb_status batch_create(const nb_model* const* models, int n_models, nb_dtype dty
                        int64_t max_ld, int max_groups, const nb_score_opts* opts, bool plain,
                        nb_batch** out);
 nb_status batch_launch_device(nb_batch* b, cudaStream_t st, int64_t* n_rechecked);
+nb_status launch_recheck_gw(const unsigned char* X, int64_t ld, int64_t n, const int64_t* sizes,
+                            int64_t bin_bytes, int n_bins, int k, const int32_t* model_of,
+                            const int32_t* cols, const nb_model* const* models, int n_models,
+                            uint8_t* label, float* margin, float* logpost, int want_lp,
+                            int64_t* n_rechecked, cudaStream_t st);
 }  // namespace nbg
 
 extern "C" void nb_groupwise_destroy(nb_groupwise* g) {
@@ -838,6 +1002,7 @@ extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t 
   g->max_files = max_files;
   g->dtype = dtype;
   g->want_lp = opts ? opts->want_logpost : 0;
+  g->recheck = opts ? (int)opts->recheck : (int)NB_RECHECK_LP;
   const int es = elem_size(dtype);
   g->ld_out = ((int64_t)k * es + 15) / 16 * 16 / es;   // rows 16-byte aligned
   auto fail = [&](nb_status s) {
@@ -865,7 +1030,25 @@ extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t 
   const size_t o_mar = take(sizeof(float) * nf);
   const size_t o_lp = take(g->want_lp ? sizeof(float) * 2 * nf : 0);
   const size_t o_st = take(sizeof(int));
-  cudaError_t e = cudaMalloc(&g->mem, off);
+  // fused-scorer pack: limbs (3 kp per model), selections (kp uint16 per model),
+  // headers, size group -> slot bytes; 16-byte aligned sections
+  g->kp = models[0]->F_pad;
+  g->models.assign(models, models + n_models);
+  const uint32_t lb = (uint32_t)(3 * g->kp * n_models);
+  g->sel_off = (lb + 15) / 16 * 16;
+  g->hdr_off = g->sel_off + (uint32_t)(2 * g->kp * n_models + 15) / 16 * 16;
+  g->map_off = g->hdr_off + (uint32_t)(sizeof(C2Header) * n_models);
+  g->pack_bytes = g->map_off + (uint32_t)(n_bins + 15) / 16 * 16;
+  const size_t o_pack = dtype == NB_U8 ? take(g->pack_bytes) : 0;
+  std::vector<int32_t> hcols((size_t)n_models * k);
+  cudaError_t e = cudaMemcpy(hcols.data(), cols, sizeof(int32_t) * hcols.size(), cudaMemcpyDefault);
+  if (e != cudaSuccess) return fail(cuda_status(e, "memcpy(cols)"));
+  for (size_t i = 0; i < hcols.size(); ++i)
+    if (hcols[i] < 0 || hcols[i] >= F_full) {
+      set_error("nb_groupwise_create: cols[%zu] = %d is not an opcode column", i, hcols[i]);
+      return fail(NB_EINVAL);
+    }
+  e = cudaMalloc(&g->mem, off);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(groupwise)"));
   char* base = static_cast<char*>(g->mem);
   g->model_of = reinterpret_cast<int32_t*>(base + o_model);
@@ -882,10 +1065,100 @@ extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t 
   NB_TRY_CUDA(cudaMemset(g->mem, 0, off), "memset(groupwise)");
   e = cudaMemcpy(g->model_of, model_of, sizeof(int32_t) * n_bins, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(g->cols, cols, sizeof(int32_t) * (size_t)n_models * k, cudaMemcpyDefault);
+    e = cudaMemcpy(g->cols, hcols.data(), sizeof(int32_t) * hcols.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_status(e, "memcpy(groupwise tables)"));
+  if (dtype == NB_U8) {
+    g->pack = reinterpret_cast<unsigned char*>(base + o_pack);
+    std::vector<uint16_t> hsel((size_t)n_models * g->kp, 0);
+    for (int m = 0; m < n_models; ++m)
+      for (int t = 0; t < k; ++t) hsel[(size_t)m * g->kp + t] = (uint16_t)hcols[(size_t)m * k + t];
+    std::vector<unsigned char> hmap((size_t)n_bins);
+    for (int b = 0; b < n_bins; ++b) hmap[b] = (unsigned char)model_of[b];
+    for (int m = 0; m < n_models && e == cudaSuccess; ++m) {
+      e = cudaMemcpy(g->pack + (size_t)m * 3 * g->kp, models[m]->d.limbs, 3 * (size_t)g->kp,
+                     cudaMemcpyDeviceToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g->pack + g->hdr_off + sizeof(C2Header) * m, models[m]->d.c2,
+                       sizeof(C2Header), cudaMemcpyDeviceToDevice);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->pack + g->sel_off, hsel.data(), 2 * hsel.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->pack + g->map_off, hmap.data(), hmap.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_status(e, "memcpy(groupwise pack)"));
+  }
   *out = g;
   return NB_OK;
+}
+
+// The fused path (k_score_gw + k_recheck_gw): u8 histograms, 16-byte aligned
+// rows, and a pack plus two row stages that fit in shared memory; else
+// NB_EUNSUPPORTED and the caller routes, gathers and batches.
+static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, const int64_t* sizes,
+                                 int64_t n, uint8_t* label, float* margin, float* logpost,
+                                 cudaStream_t st, int64_t* n_rechecked) {
+  if (!g->pack || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || (ld % 16) != 0 || ld > 8192)
+    return NB_EUNSUPPORTED;
+  // the largest stage of 48, 32, 24 or 16 rows of which two fit beside the pack
+  PipeArgs p{};
+  const uint32_t budget = 220u * 1024u;
+  int rs = 0;
+  for (int cand : {48, 32, 24, 16}) {
+    pipe_layout(p, cand, 1, ld, false, false, g->pack_bytes, n);
+    if (p.stages_off + 2 * p.stage_bytes <= budget) {
+      rs = cand;
+      break;
+    }
+  }
+  if (rs == 0) return NB_EUNSUPPORTED;
+  int S = (int)((budget - p.stages_off) / p.stage_bytes);
+  S = S > kMaxStages ? kMaxStages : S;
+  pipe_layout(p, rs, S, ld, false, false, g->pack_bytes, n);
+  const int smem = (int)(p.stages_off + (uint32_t)S * p.stage_bytes);
+  if (n_rechecked) NB_TRY_CUDA(cudaMemsetAsync(n_rechecked, 0, sizeof(int64_t), st), "memset");
+  if (n == 0) return NB_OK;
+  GwArgs a{};
+  a.X = static_cast<const char*>(X);
+  a.ld_bytes = ld;
+  a.n = n;
+  a.sizes = sizes;
+  a.bin_bytes = g->bin_bytes;
+  a.n_bins = g->n_bins;
+  a.k = g->k;
+  a.kp = g->kp;
+  a.kw = (g->k + 3) / 4;
+  a.pack = g->pack;
+  a.pack_bytes = g->pack_bytes;
+  a.sel_off = g->sel_off;
+  a.hdr_off = g->hdr_off;
+  a.map_off = g->map_off;
+  a.label = label;
+  a.margin = margin;
+  a.logpost = g->want_lp ? logpost : nullptr;
+  a.want_lp = g->want_lp;
+  a.recheck = g->recheck;
+  a.status = g->status;
+  static int configured = 0;
+  if (smem > kSmemOptIn && configured < smem) {
+    NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gw, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                "cudaFuncSetAttribute(k_score_gw)");
+    configured = smem;
+  }
+  int occ = 0;
+  NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_gw, (kGwNCW + 1) * 32,
+                                                            smem),
+              "occupancy(k_score_gw)");
+  if (occ < 1) return NB_EUNSUPPORTED;
+  long long blocks = (long long)num_sms() * occ;
+  if (blocks > p.tiles) blocks = p.tiles;
+  count_launch();
+  k_score_gw<<<(unsigned)blocks, (kGwNCW + 1) * 32, smem, st>>>(a, p);
+  NB_TRY_CUDA(cudaGetLastError(), "k_score_gw launch");
+  if (g->recheck == NB_RECHECK_OFF) return NB_OK;
+  return launch_recheck_gw(static_cast<const unsigned char*>(X), ld, n, sizes, g->bin_bytes,
+                           g->n_bins, g->k, g->model_of, g->cols, g->models.data(), g->n_models,
+                           label, margin, g->want_lp ? logpost : nullptr, g->want_lp, n_rechecked,
+                           st);
 }
 
 extern "C" nb_status nb_groupwise_classify(nb_groupwise* g, const void* X, int64_t ld,
@@ -898,6 +1171,10 @@ extern "C" nb_status nb_groupwise_classify(nb_groupwise* g, const void* X, int64
     return NB_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  {
+    nb_status fs = groupwise_fused(g, X, ld, sizes, n, label, margin, logpost, st, n_rechecked);
+    if (fs != NB_EUNSUPPORTED) return fs;
+  }
   nb_status s = launch_route(sizes, n, g->bin_bytes, g->n_bins, g->model_of, g->n_models,
                              nullptr, 0, g->group, g->order, g->offsets, nullptr, g->hist,
                              g->status, st);

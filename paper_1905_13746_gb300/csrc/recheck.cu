@@ -39,6 +39,7 @@ struct RView {
   uint8_t* label;
   float* margin;
   float* logpost;
+  const int32_t* cols;   // feature j is stored column cols[j] (nullptr: column j)
 };
 
 __device__ __forceinline__ double load_x(int dtype, const char* rp, int j, double scale) {
@@ -69,7 +70,8 @@ __device__ __forceinline__ void recheck_row(const RView& v, const RModel& md, in
     double acc = 0.0;
     if (md.kind == NB_MULTINOMIAL) {
       const double* lt = md.p0 + (int64_t)c * v.F;
-      for (int j = lane; j < v.F; j += 32) acc = fma(load_x(v.dtype, rp, j, scale), lt[j], acc);
+      for (int j = lane; j < v.F; j += 32)
+        acc = fma(load_x(v.dtype, rp, v.cols ? v.cols[j] : j, scale), lt[j], acc);
       if (v.dtype == NB_U8 && v.ovf_ptr) {
         for (int64_t k = v.ovf_ptr[r] + lane; k < v.ovf_ptr[r + 1]; k += 32) {
           const int j = v.ovf_col[k];
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(256) k_recheck_seg(const RSegArgs a) {
     unsigned m = __ballot_sync(0xFFFFFFFFu, f);
     if (!m) continue;
     RView v;
+    v.cols = nullptr;
     v.X = G.X;
     v.dtype = a.dtype;
     v.F = a.F;
@@ -234,6 +237,103 @@ nb_status launch_recheck_seg(const SegGroup* groups, const SegHeader* hdr,
   count_launch();
   k_recheck_seg<<<num_sms() * 4, 256, 0, st>>>(a);
   NB_TRY_CUDA(cudaGetLastError(), "k_recheck_seg launch");
+  return NB_OK;
+}
+
+}  // namespace nbg
+
+namespace nbg {
+
+// ---------------------------------------------------------------------------
+// group-wise recheck: rows in the files' order, each with the model of its
+// size group and that model's opcode selection (feature t = column cols[t] of
+// the full histogram), the arithmetic of recheck_row unchanged
+// ---------------------------------------------------------------------------
+struct RGwArgs {
+  const unsigned char* X;
+  int64_t ld;
+  int64_t n;
+  const int64_t* sizes;
+  int64_t bin_bytes;
+  int n_bins, k;
+  const int32_t* model_of;   // size group -> model slot
+  const int32_t* cols;       // n_models x k
+  RModel md[kSegMaxModels];
+  uint8_t* label;
+  float* margin;
+  float* logpost;
+  int want_lp;
+  unsigned long long* n_rechecked;
+};
+
+__global__ void __launch_bounds__(256) k_recheck_gw(const RGwArgs a) {
+  __shared__ double s_sh[8][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  unsigned long long cnt = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < a.n; base += nwarps * 32) {
+    const int64_t row = base + lane;
+    const bool f = row < a.n && a.label[row] == kLabelRecheck;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, f);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t r = base + src;
+      long long sz = a.sizes[r];
+      sz = sz < 0 ? 0 : sz;
+      long long bin = sz / a.bin_bytes;
+      if (bin > a.n_bins - 1) bin = a.n_bins - 1;
+      const int g = a.model_of[bin];
+      RView v;
+      v.X = reinterpret_cast<const char*>(a.X);
+      v.ld = a.ld;
+      v.dtype = NB_U8;
+      v.F = a.k;
+      v.ovf_ptr = nullptr;
+      v.ovf_col = nullptr;
+      v.ovf_add = nullptr;
+      v.row_exp = nullptr;
+      v.label = a.label;
+      v.margin = a.margin;
+      v.logpost = a.logpost;
+      v.cols = a.cols + (int64_t)g * a.k;
+      recheck_row(v, a.md[g], r, a.want_lp, s_sh[warp]);
+      ++cnt;
+    }
+  }
+  if (lane == 0 && cnt && a.n_rechecked) atomicAdd(a.n_rechecked, cnt);
+}
+
+nb_status launch_recheck_gw(const unsigned char* X, int64_t ld, int64_t n, const int64_t* sizes,
+                            int64_t bin_bytes, int n_bins, int k, const int32_t* model_of,
+                            const int32_t* cols, const nb_model* const* models, int n_models,
+                            uint8_t* label, float* margin, float* logpost, int want_lp,
+                            int64_t* n_rechecked, cudaStream_t st) {
+  if (n == 0) return NB_OK;
+  RGwArgs a{};
+  a.X = X;
+  a.ld = ld;
+  a.n = n;
+  a.sizes = sizes;
+  a.bin_bytes = bin_bytes;
+  a.n_bins = n_bins;
+  a.k = k;
+  a.model_of = model_of;
+  a.cols = cols;
+  for (int i = 0; i < n_models && i < kSegMaxModels; ++i) {
+    const nb_model* m = models[i];
+    a.md[i] = RModel{m->kind, m->C, m->d.p0, m->d.p1, m->d.log_pi, m->d.gconst};
+  }
+  a.label = label;
+  a.margin = margin;
+  a.logpost = logpost;
+  a.want_lp = want_lp;
+  a.n_rechecked = reinterpret_cast<unsigned long long*>(n_rechecked);
+  const int64_t chunks = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  count_launch();
+  k_recheck_gw<<<(unsigned)(chunks < cap ? chunks : cap), 256, 0, st>>>(a);
+  NB_TRY_CUDA(cudaGetLastError(), "k_recheck_gw launch");
   return NB_OK;
 }
 

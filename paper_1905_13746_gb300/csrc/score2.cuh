@@ -141,9 +141,9 @@ struct Decode<NB_FP8E4M3> {
   }
 };
 
-// Sums four int32 values over the LPR lanes of a lane group (LPR = 16 or 32)
-// with 6 (5) shuffles instead of 4 x 5 (4): the first two steps halve the set
-// of values each lane carries.  Returns the lane's share: lanes [0, LPR/4) of
+// Sums four int32 values over the LPR lanes of a lane group (LPR = 4 .. 32,
+// a power of two) with log2(LPR) + 1 shuffles instead of 4 log2(LPR): the
+// first two steps halve the set of values each lane carries.  Returns the lane's share: lanes [0, LPR/4) of
 // the group hold the sum of a0, then a1, a2 and a3 by quarter.  Integer sums
 // are exact, so the order does not matter.
 template <int LPR>

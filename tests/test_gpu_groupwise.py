@@ -209,7 +209,7 @@ def test_groupwise_one_hundred_models_in_one_launch():
     res = gw.classify(torch.from_numpy(Xt_np).cuda(), torch.from_numpy(st).cuda())
     torch.cuda.synchronize()
     launches = nb.nb_kernel_launches() - launches0
-    assert launches <= 9, launches                 # route x3, gather, list, score, recheck, back
+    assert launches <= 2, launches                 # fused scorer + recheck
     compare(to_np(res), ogw.score_groups(Xt_np, st, fo))
 
 
@@ -231,6 +231,33 @@ def test_groupwise_rows_equal_single_group_scoring():
         assert (alone["label"] == res["label"][rows]).all()
         assert (alone["margin"] == res["margin"][rows]).all()
         assert (alone["lp"] == res["lp"][rows]).all()
+
+
+def test_groupwise_routed_path_f32_and_unaligned():
+    # F32 histograms, and u8 rows whose pitch is not a multiple of 16, take
+    # the route + gather + batched-launch path; same results as the oracle
+    n_bins, F, k = 12, 200, 24
+    X, y, s = _workload(91, 5000, F, n_bins)
+    tr, te = synth.split_per_class(92, y)
+    fo = ogw.fit_groups(X[tr], y[tr], s[tr], k, n_bins=n_bins)
+    ref = ogw.score_groups(X[te], s[te], fo)
+    X32 = torch.from_numpy(X.astype(np.float32)).cuda()
+    fg = nb.fit_groupwise(X32[tr], torch.from_numpy(y[tr]).cuda(), torch.from_numpy(s[tr]).cuda(),
+                          k, n_bins=n_bins)
+    gw = nb.Groupwise(fg["models"], fg["cols"], fg["model_of"], F, dtype_code=nb.NB_F32,
+                      max_files=len(te))
+    res = gw.classify(X32[te], torch.from_numpy(s[te]).cuda())
+    torch.cuda.synchronize()
+    compare(to_np(res), ref)
+    # u8 with a row pitch of F + 4 bytes (rows not 16-byte aligned)
+    fg8 = nb.fit_groupwise(torch.from_numpy(X[tr]).cuda(), torch.from_numpy(y[tr]).cuda(),
+                           torch.from_numpy(s[tr]).cuda(), k, n_bins=n_bins)
+    Xp = torch.zeros((len(te), F + 4), dtype=torch.uint8, device="cuda")
+    Xp[:, :F] = torch.from_numpy(X[te]).cuda()
+    gw8 = nb.Groupwise(fg8["models"], fg8["cols"], fg8["model_of"], F, max_files=len(te))
+    res8 = gw8.classify(Xp[:, :F], torch.from_numpy(s[te]).cuda())
+    torch.cuda.synchronize()
+    compare(to_np(res8), ref)
 
 
 def test_groupwise_empty_call():
