@@ -703,8 +703,9 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
   __syncthreads();
   if (warp == kGwNCW) {
     const PipeSrc src{a.X, a.ld_bytes, a.n, nullptr, nullptr, nullptr, nullptr, a.pack,
-                      a.status};
-    pipe_produce(src, p, sm, full, empty, &tabbar, t0, ntl);
+                      a.status, a.sizes};
+    const SizeMap zm{a.bin_bytes, a.n_bins, a.map_off};
+    pipe_produce(src, p, sm, full, empty, &tabbar, t0, ntl, &zm);
     return;
   }
   if (!mbar_wait_bounded(&tabbar, 0)) {
@@ -714,7 +715,6 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
   const unsigned char* limbs = sm;                                      // model m at m * 3 kp
   const uint16_t* sels = reinterpret_cast<const uint16_t*>(sm + a.sel_off);   // m * kp
   const C2Header* hdrs = reinterpret_cast<const C2Header*>(sm + a.hdr_off);
-  const unsigned char* map = sm + a.map_off;                            // size group -> slot
   // valid bytes of the last four-feature word
   const int kt = a.k - 4 * (a.kw - 1);
   const uint32_t tail_mask = kt >= 4 ? 0xFFFFFFFFu : ((1u << (8 * kt)) - 1u);
@@ -746,21 +746,12 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
     const StageMeta* mp = reinterpret_cast<const StageMeta*>(st + p.meta_off);
     const int nr = mp->nr;
     const long long row0 = mp->row0;
+    const int32_t* slot = reinterpret_cast<const int32_t*>(st + p.y_off);   // model per row
     for (int r0 = warp * kGwRPW; r0 < nr; r0 += kGwNCW * kGwRPW) {
       if (nres + kGwRPW > 32) finish();
       const int r = r0 + grp;
       const bool valid = r < nr;
-      int m = 0;
-      if (valid) {
-        long long sz = a.sizes[row0 + r];
-        if (sz < 0) {
-          if (li == 0) atomicOr(a.status, ST_BAD_ROUTE);
-          sz = 0;
-        }
-        long long bin = sz / a.bin_bytes;
-        if (bin > a.n_bins - 1) bin = a.n_bins - 1;
-        m = map[bin];
-      }
+      const int m = valid ? slot[r] : 0;
       int c0 = 0, c1 = 0, c2 = 0;
       uint32_t ct = 0;
       if (valid) {
@@ -1104,7 +1095,7 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   const uint32_t budget = 220u * 1024u;
   int rs = 0;
   for (int cand : {48, 32, 24, 16}) {
-    pipe_layout(p, cand, 1, ld, false, false, g->pack_bytes, n);
+    pipe_layout(p, cand, 1, ld, false, true, g->pack_bytes, n);
     if (p.stages_off + 2 * p.stage_bytes <= budget) {
       rs = cand;
       break;
@@ -1113,7 +1104,7 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   if (rs == 0) return NB_EUNSUPPORTED;
   int S = (int)((budget - p.stages_off) / p.stage_bytes);
   S = S > kMaxStages ? kMaxStages : S;
-  pipe_layout(p, rs, S, ld, false, false, g->pack_bytes, n);
+  pipe_layout(p, rs, S, ld, false, true, g->pack_bytes, n);
   const int smem = (int)(p.stages_off + (uint32_t)S * p.stage_bytes);
   if (n_rechecked) NB_TRY_CUDA(cudaMemsetAsync(n_rechecked, 0, sizeof(int64_t), st), "memset");
   if (n == 0) return NB_OK;

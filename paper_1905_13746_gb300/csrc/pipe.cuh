@@ -46,6 +46,7 @@ struct TileInfo {
   const uint16_t* ovf_add;
   long long E;               // entries in the group's list (ovf_ptr[n])
   const int32_t* y;          // the group's labels (fit), or nullptr
+  const int64_t* sizes;      // file sizes (group-wise scorer), or nullptr
 };
 
 // what the producer streams
@@ -59,6 +60,15 @@ struct PipeSrc {
   const int32_t* y;        // labels (fit), or nullptr
   const void* table;       // parameter table for offset 0, or nullptr
   int* status;
+  const int64_t* sizes;    // file sizes whose model slots go to the y area, or nullptr
+};
+
+// Size group -> model slot map of the group-wise scorer (in the staged table):
+// a row's slot is map[min(max(size, 0) / bin_bytes, n_bins - 1)].
+struct SizeMap {
+  int64_t bin_bytes;
+  int n_bins;
+  uint32_t map_off;         // offset of the map (one byte per size group) in shared memory
 };
 
 // Layout of the per-stage side areas after RS rows of ld_bytes each.
@@ -103,6 +113,7 @@ struct SingleSrc {
     t.ovf_add = src->ovf_add;
     t.E = E;
     t.y = src->y;
+    t.sizes = src->sizes;
     return t;
   }
 };
@@ -127,10 +138,11 @@ __device__ __forceinline__ void pipe_stage_tables(unsigned char* sm, const void*
 struct TilePre {
   long long pa, pb;   // ptr[row0 + lane], ptr[row0 + 32 + lane]
   int32_t ya, yb;     // y[row0 + lane], y[row0 + 32 + lane]
+  long long za, zb;   // sizes[row0 + lane], sizes[row0 + 32 + lane]
 };
 
 __device__ __forceinline__ TilePre pipe_preload(const TileInfo& t, int lane) {
-  TilePre r{0, 0, 0, 0};
+  TilePre r{0, 0, 0, 0, 0, 0};
   if (t.ovf_ptr) {
     r.pa = lane <= t.nr ? t.ovf_ptr[t.row0 + lane] : 0;
     r.pb = lane + 32 <= t.nr ? t.ovf_ptr[t.row0 + 32 + lane] : 0;
@@ -139,7 +151,22 @@ __device__ __forceinline__ TilePre pipe_preload(const TileInfo& t, int lane) {
     r.ya = lane < t.nr ? t.y[t.row0 + lane] : 0;
     r.yb = lane + 32 < t.nr ? t.y[t.row0 + 32 + lane] : 0;
   }
+  if (t.sizes) {
+    r.za = lane < t.nr ? t.sizes[t.row0 + lane] : 0;
+    r.zb = lane + 32 < t.nr ? t.sizes[t.row0 + 32 + lane] : 0;
+  }
   return r;
+}
+
+__device__ __forceinline__ int32_t size_slot(long long z, const SizeMap& sm,
+                                             const unsigned char* smem, int* status) {
+  if (z < 0) {   // flagged, counted as size 0
+    atomicOr(status, ST_BAD_ROUTE);
+    z = 0;
+  }
+  long long b = z / sm.bin_bytes;
+  if (b > sm.n_bins - 1) b = sm.n_bins - 1;
+  return (int32_t)smem[sm.map_off + b];
 }
 
 // Producer warp: the whole warp calls it; lane 0 issues the copies.  `src`
@@ -147,10 +174,21 @@ __device__ __forceinline__ TilePre pipe_preload(const TileInfo& t, int lane) {
 template <class Src>
 __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
                                                    unsigned char* sm, uint64_t* full,
-                                                   uint64_t* empty, long long ntl, int* status) {
+                                                   uint64_t* empty, long long ntl, int* status,
+                                                   const SizeMap* zmap = nullptr,
+                                                   uint64_t* tabbar = nullptr) {
   const int lane = threadIdx.x & 31;
   TileInfo cur, nxt;
-  TilePre pc{0, 0, 0, 0}, pn{0, 0, 0, 0};
+  TilePre pc{0, 0, 0, 0, 0, 0}, pn{0, 0, 0, 0, 0, 0};
+  if (zmap && ntl > 0) {   // the size map arrives with the table
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait_bounded(tabbar, 0);
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (!ok) {
+      if (lane == 0) atomicOr(status, ST_TIMEOUT);
+      return;
+    }
+  }
   if (ntl > 0) {
     cur = src.tile(0);
     pc = pipe_preload(cur, lane);
@@ -162,7 +200,7 @@ __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
   for (long long k = 0; k < ntl; ++k) {
     // tile k + 2: its global values are in flight while tile k is staged
     TileInfo nn = nxt;
-    TilePre p2{0, 0, 0, 0};
+    TilePre p2{0, 0, 0, 0, 0, 0};
     if (k + 2 < ntl) {
       nn = src.tile(k + 2);
       p2 = pipe_preload(nn, lane);
@@ -196,6 +234,11 @@ __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
       int32_t* sy = reinterpret_cast<int32_t*>(st + p.y_off);
       if (lane < nr) sy[lane] = pc.ya;
       if (lane + 32 < nr) sy[lane + 32] = pc.yb;
+    } else if (cur.sizes && zmap) {
+      // the rows' model slots from their sizes
+      int32_t* sy = reinterpret_cast<int32_t*>(st + p.y_off);
+      if (lane < nr) sy[lane] = size_slot(pc.za, *zmap, sm, status);
+      if (lane + 32 < nr) sy[lane + 32] = size_slot(pc.zb, *zmap, sm, status);
     }
     // the lanes' shared-memory writes are ordered before lane 0's arrive
     // (a release) by the warp barrier
@@ -235,11 +278,12 @@ __device__ __forceinline__ void pipe_produce_tiles(Src& src, const PipeArgs& p,
 // Single-matrix producer (the table, if any, is staged at offset 0).
 __device__ __forceinline__ void pipe_produce(const PipeSrc& src, const PipeArgs& p,
                                              unsigned char* sm, uint64_t* full, uint64_t* empty,
-                                             uint64_t* tabbar, long long t0, long long ntl) {
+                                             uint64_t* tabbar, long long t0, long long ntl,
+                                             const SizeMap* zmap = nullptr) {
   if (src.table) pipe_stage_tables(sm, &src.table, 1, p.tab_bytes, 0, tabbar);
   SingleSrc ss{&src, &p, t0, 0};
   ss.init();
-  pipe_produce_tiles(ss, p, sm, full, empty, ntl, src.status);
+  pipe_produce_tiles(ss, p, sm, full, empty, ntl, src.status, zmap, tabbar);
 }
 
 }  // namespace nbg

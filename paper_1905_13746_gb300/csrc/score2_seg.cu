@@ -41,6 +41,7 @@ struct SegSrc {
     gi.ovf_add = G.ovf_add;
     gi.E = G.ovf_ptr ? G.ovf_ptr[G.n] : 0;
     gi.y = nullptr;
+    gi.sizes = nullptr;
     gi.row0 = G.n;   // holds n until a tile is cut
   }
   __device__ __forceinline__ void init() {
