@@ -35,10 +35,11 @@ METRIC = ("files/sec & HBM-roofline % at F=1024, plain FP32 vs low-prec; "
           "serving p99 latency")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# u8 two-class scorer on the default workload, from an ncu capture of this
-# kernel at full size (summarised under profiles/); reported only for that
+# u8 two-class scorer on the default workload: an ncu capture of the same
+# kernel and tile configuration on 500,000 files of the same recipe, scaled by
+# the files processed (summarised under profiles/); reported only for that
 # workload and tile configuration.
-SCORE_TRAFFIC = {(1_000_000, 1024, (1, 4, 48, 2)): 1_047_915_264 + 14_503_168}
+SCORE_TRAFFIC = {(1_000_000, 1024, (1, 4, 48, 2)): 2 * (523_985_920 + 7_966_208)}
 
 
 def _dist():
