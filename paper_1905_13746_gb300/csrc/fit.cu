@@ -782,9 +782,12 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
         NB_TRY_CUDA(cudaFuncSetAttribute(k_counts_ovf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem),
                     "cudaFuncSetAttribute");
+      // shared 32-bit bins: at most 32,768 rows per block (adds are < 2^16)
       const long long ob = (n + 255) / 256;
+      long long grid = ob < sms * 2 ? ob : sms * 2;
+      if (use_smem && grid < (n + 32767) / 32768) grid = (n + 32767) / 32768;
       count_launch();
-      k_counts_ovf<<<(unsigned)(ob < sms * 2 ? ob : sms * 2), 256, smem, st>>>(
+      k_counts_ovf<<<(unsigned)grid, 256, smem, st>>>(
           aux->ovf_ptr, aux->ovf_col, aux->ovf_add, y, n, F, C, use_smem,
           reinterpret_cast<unsigned long long*>(d.counts), d.status);
       NB_TRY_CUDA(cudaGetLastError(), "k_counts_ovf");

@@ -8,8 +8,14 @@
 // which of two per-lane accumulator sets receives the row.  u8 rows are
 // summed as packed 16-bit lanes (even and odd bytes of each word), which
 // cannot overflow before 257 rows; every 256 rows of a warp the sums move into
-// a per-block 32-bit histogram in shared memory, which is added to the global
-// uint64 counts once per block.  Integer sums are exact in any order.
+// a per-block histogram in shared memory, which is added to the global uint64
+// counts once per block.  Overflow bounds: u8 (at most 255 + 65,535 per
+// element) and u16 rows keep 32-bit block sums, with at most 32,768 rows per
+// block; FP32 / BF16 / FP8 counts (below 2^24) flush their 32-bit lane sums
+// every 255 rows into a 64-bit block histogram.  Integer sums are exact in
+// any order.
+#include <type_traits>
+
 #include "pipe.cuh"
 #include "score2.cuh"
 
@@ -43,10 +49,21 @@ __device__ __forceinline__ uint32_t count_of(float v, int* status) {
   return (uint32_t)v;
 }
 
+// block histogram word: 32 bits where the bounds above allow it, else 64
+template <int DT>
+using Fit2Hist = typename std::conditional<DT == NB_U8 || DT == NB_U16, unsigned int,
+                                           unsigned long long>::type;
+// rows between flushes of a warp's 32-bit lane sums
+template <int DT>
+constexpr int fit2_flush_rows() {
+  return DT == NB_U8 ? 256 : (DT == NB_U16 ? 32768 : 255);
+}
+constexpr long long kFit2BlockRows = 32768;   // most rows of one block (32-bit sums)
+
 // move a warp's per-lane sums into the block histogram and clear them
 template <int DT, int KV, int NA, int EPV>
-__device__ __forceinline__ void fit2_flush(uint32_t (&acc)[2][KV][NA], unsigned int* hist, int F,
-                                           int F_pad, int lane, int nv) {
+__device__ __forceinline__ void fit2_flush(uint32_t (&acc)[2][KV][NA], Fit2Hist<DT>* hist,
+                                           int F, int F_pad, int lane, int nv) {
 #pragma unroll
   for (int kv = 0; kv < KV; ++kv) {
     const int v = lane + 32 * kv;
@@ -63,7 +80,7 @@ __device__ __forceinline__ void fit2_flush(uint32_t (&acc)[2][KV][NA], unsigned 
           val = acc[c][kv][e];
         }
         const int j = v * EPV + e;
-        if (v < nv && val && j < F) atomicAdd(&hist[c * F_pad + j], val);
+        if (v < nv && val && j < F) atomicAdd(&hist[c * F_pad + j], (Fit2Hist<DT>)val);
       }
 #pragma unroll
       for (int e = 0; e < NA; ++e) acc[c][kv][e] = 0u;
@@ -80,9 +97,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
   const long long t0 = p.tiles * blockIdx.x / gridDim.x;
   const long long t1 = p.tiles * (blockIdx.x + 1) / gridDim.x;
   const long long ntl = t1 - t0;
-  unsigned int* hist = reinterpret_cast<unsigned int*>(sm);   // [2][F_pad]
+  Fit2Hist<DT>* hist = reinterpret_cast<Fit2Hist<DT>*>(sm);   // [2][F_pad]
 
-  for (int k = threadIdx.x; k < 2 * f.F_pad; k += blockDim.x) hist[k] = 0u;
+  for (int k = threadIdx.x; k < 2 * f.F_pad; k += blockDim.x) hist[k] = 0;
   if (threadIdx.x == 0) {
     ncount[0] = ncount[1] = 0u;
     for (int s = 0; s < p.S; ++s) {
@@ -205,7 +222,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
           const uint32_t col = m.in_smem ? scol[e - m.ebase] : f.ovf_col[e];
           const uint32_t add = m.in_smem ? sadd[e - m.ebase] : f.ovf_add[e];
           if (col < (uint32_t)f.F)
-            atomicAdd(&hist[c * f.F_pad + col], add);
+            atomicAdd(&hist[c * f.F_pad + col], (Fit2Hist<DT>)add);
           else
             atomicOr(f.status, ST_OVF_RANGE);
         }
@@ -215,7 +232,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
     if (lane == 0) mbar_arrive(&empty[s]);
     // a warp takes at most ceil(RS / NCW) rows per stage, so flushing here
     // keeps the packed 16-bit lanes below 257 rows
-    if (since_flush + (p.RS + NCW - 1) / NCW > (DT == NB_U8 ? 256 : 32768)) {
+    if (since_flush + (p.RS + NCW - 1) / NCW > fit2_flush_rows<DT>()) {
       fit2_flush<DT, KV, NA, EPV>(acc, hist, f.F, f.F_pad, lane, nv);
       since_flush = 0;
     }
@@ -229,7 +246,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
   asm volatile("bar.sync 1, %0;" ::"r"(NCW * 32) : "memory");
   for (int j = threadIdx.x; j < 2 * f.F_pad; j += NCW * 32) {
     const int c = j / f.F_pad, jj = j % f.F_pad;
-    const unsigned int v = hist[j];
+    const Fit2Hist<DT> v = hist[j];
     if (v && jj < f.F) atomicAdd(&f.counts[(long long)c * f.F + jj], (unsigned long long)v);
   }
   if (threadIdx.x < 2 && ncount[threadIdx.x])
@@ -250,6 +267,8 @@ static nb_status run_fit2(const Fit2Args& f, const PipeArgs& p, int smem, cudaSt
               "occupancy(fit2)");
   if (occ < 1) return NB_EUNSUPPORTED;
   long long blocks = (long long)num_sms() * occ;
+  const long long need = (f.n + kFit2BlockRows - 1) / kFit2BlockRows;   // 32-bit block sums
+  if (blocks < need) blocks = need;
   if (blocks > p.tiles) blocks = p.tiles;
   count_launch();
   kern<<<(unsigned)blocks, (kFitNCW + 1) * 32, smem, st>>>(f, p);
@@ -284,15 +303,21 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
   if (!aligned || kv > kv_max || f.ld_bytes > 8192) return NB_EUNSUPPORTED;
   const bool side_ok = !f.ovf_ptr || ((reinterpret_cast<uintptr_t>(f.ovf_col) & 15) == 0 &&
                                       (reinterpret_cast<uintptr_t>(f.ovf_add) & 15) == 0);
-  int rs = (int)(24576 / f.ld_bytes);
-  rs = rs > 32 ? 32 : (rs < 1 ? 1 : rs);
-  PipeArgs p{};
-  const uint32_t hist_bytes = (uint32_t)(8 * m->F_pad);
-  pipe_layout(p, rs, 4, f.ld_bytes, side_ok, true, hist_bytes, n);
-  const int smem = (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
-  if (smem > 220 * 1024) return NB_EUNSUPPORTED;
   // eight consumer warps and two blocks per SM for u8 rows of <= 64 vectors
   const int ncw = (dt == NB_U8 && kv <= 2) ? 8 : 12;
+  // stages of ~24 KB; rows of 2 KB or more get one row per consumer warp per
+  // stage (as many stages as fit, at least two), so that no warp idles
+  int rs = (int)(24576 / f.ld_bytes);
+  rs = rs > 32 ? 32 : (rs < 1 ? 1 : rs);
+  if (f.ld_bytes >= 2048 && rs < ncw) rs = ncw;
+  PipeArgs p{};
+  const uint32_t hist_bytes = (uint32_t)((dt == NB_U8 || dt == NB_U16 ? 8 : 16) * m->F_pad);
+  pipe_layout(p, rs, 4, f.ld_bytes, side_ok, true, hist_bytes, n);
+  int S = 4;
+  while (S > 2 && p.stages_off + (uint32_t)S * p.stage_bytes > 220u * 1024u) --S;
+  pipe_layout(p, rs, S, f.ld_bytes, side_ok, true, hist_bytes, n);
+  const int smem = (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
+  if (smem > 220 * 1024) return NB_EUNSUPPORTED;
 #define NB_FIT2_CASE(D, K)                                                \
   if (dt == D && kv == K)                                                 \
     return ncw == 8 ? run_fit2<D, K, 8>(f, p, smem, st) : run_fit2<D, K, 12>(f, p, smem, st);

@@ -57,6 +57,23 @@ def test_fit_counts_exact(fmt, F):
     assert np.allclose(lpi, ref["log_pi"], rtol=1e-14, atol=1e-14)
 
 
+@pytest.mark.parametrize("C", [2, 3])
+def test_fit_counts_exact_past_32_bits(C):
+    # FP32 counts just below 2^24 over 700 rows: per-class sums reach ~6e9,
+    # beyond any 32-bit accumulator; the counts must still be exact
+    rng = np.random.default_rng(77)
+    n, F = 700, 40
+    X = rng.integers(16_000_000, 16_777_216, size=(n, F)).astype(np.float32)
+    X[:, ::7] = 0
+    y = (np.arange(n) % C).astype(np.int32)
+    model = nb.fit(nb.Features(torch.from_numpy(X).cuda(), nb.NB_F32),
+                   torch.from_numpy(y).cuda(), C)
+    counts, _ = model.counts()
+    ref = np.stack([X[y == c].astype(np.uint64).sum(axis=0) for c in range(C)])
+    assert ref.max() > 2**32
+    assert (counts == ref).all()
+
+
 @pytest.mark.parametrize("C", [3, 17, 64])
 def test_fit_counts_many_classes(C):
     X, y, _ = count_matrix(7 * C, 4099, 300, C=C, conc=0.1, clip=255)
