@@ -297,8 +297,9 @@ static nb_status run_pipe(const S2Args& a, const PipeArgs& p, int smem, cudaStre
 
 // Shapes: rows per warp pass (RPW = 1 or 2, lanes per row 32 / RPW), vectors
 // per lane (KV) and consumer warps (NCW).  Eight consumer warps and two blocks
-// per SM when the Delta slice fits the 96-register budget, else twelve
-// consumers and one block.
+// per SM when the Delta slice fits the 96-register budget, or for u8 rows of
+// 64 vectors at two rows per pass when the stages leave room for two blocks;
+// else twelve consumers and one block.
 nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_per_stage,
                              int rows_per_warp, int stage_entries, cudaStream_t st) {
   const int rpw = rows_per_warp == 2 ? 2 : 1;
@@ -306,24 +307,36 @@ nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_
   const int kv = (a.nvec_row + lpr - 1) / lpr;
   const int kv_max = dt == NB_F32 ? 8 : 4;
   if (kv < 1 || kv > kv_max || a.ld_bytes > 8192) return NB_EUNSUPPORTED;
-  const int ncw = (rpw == 1 && (dt == NB_F32 ? kv <= 8 : kv <= 2)) ? 8 : 12;
-  // rows per stage: whole passes of ncw * rpw rows, 16-48 KB
-  const int pass_rows = ncw * rpw;
-  long long per = 32768 / ((long long)pass_rows * a.ld_bytes);
-  int rs = rows_per_stage > 0 ? rows_per_stage : pass_rows * (int)(per > 0 ? per : 1);
-  if (rs > kMaxStageRows) rs = kMaxStageRows;
-  if (rs < 1) rs = 1;
-  const unsigned budget = ncw == 8 ? 100u * 1024u : 180u * 1024u;   // per block
-  int S = stages;
-  if (S <= 0) {
-    PipeArgs q{};
-    pipe_layout(q, rs, 1, a.ld_bytes, stage_entries != 0, false, a.table_bytes, a.n);
-    S = q.stages_off + q.stage_bytes > budget ? 2 : (int)((budget - q.stages_off) / q.stage_bytes);
-  }
-  S = S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
+  // Stage plan for `ncw` consumer warps: rows per stage in whole passes of
+  // ncw * rpw rows, 16-48 KB; stages filling ~100 KB (eight consumers, two
+  // blocks per SM) or ~180 KB (twelve, one block) unless given.
+  auto plan = [&](int ncw, PipeArgs& p) {
+    const int pass_rows = ncw * rpw;
+    long long per = 32768 / ((long long)pass_rows * a.ld_bytes);
+    int rs = rows_per_stage > 0 ? rows_per_stage : pass_rows * (int)(per > 0 ? per : 1);
+    if (rs > kMaxStageRows) rs = kMaxStageRows;
+    if (rs < 1) rs = 1;
+    const unsigned budget = ncw == 8 ? 100u * 1024u : 180u * 1024u;   // per block
+    int S = stages;
+    if (S <= 0) {
+      PipeArgs q{};
+      pipe_layout(q, rs, 1, a.ld_bytes, stage_entries != 0, false, a.table_bytes, a.n);
+      S = q.stages_off + q.stage_bytes > budget ? 2 : (int)((budget - q.stages_off) / q.stage_bytes);
+    }
+    S = S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
+    pipe_layout(p, rs, S, a.ld_bytes, stage_entries != 0, false, a.table_bytes, a.n);
+    return (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
+  };
+  int ncw = (rpw == 1 && (dt == NB_F32 ? kv <= 8 : kv <= 2)) ? 8 : 12;
   PipeArgs p{};
-  pipe_layout(p, rs, S, a.ld_bytes, stage_entries != 0, false, a.table_bytes, a.n);
-  const int smem = (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
+  int smem = 0;
+  // two u8 rows per pass: eight consumer warps whenever the stages leave room
+  // for two blocks (18 warps) per SM
+  if (dt == NB_U8 && rpw == 2 && kv == 4) {
+    smem = plan(8, p);
+    if (smem <= 112 * 1024) ncw = 8;
+  }
+  if (ncw == 12 || smem == 0) smem = plan(ncw, p);
   if (smem > 220 * 1024) return NB_EUNSUPPORTED;
   // rounding depth of the FP32 paths: serial FMAs per accumulator, the four
   // accumulators, the lane-group butterfly, the weight and final roundings
@@ -336,6 +349,7 @@ nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_
   NB_PIPE_CASE(D, 4, 1, 12) NB_PIPE_CASE(D, 1, 2, 12) NB_PIPE_CASE(D, 2, 2, 12)               \
   NB_PIPE_CASE(D, 3, 2, 12) NB_PIPE_CASE(D, 4, 2, 12)
   NB_PIPE_DT(NB_U8)
+  NB_PIPE_CASE(NB_U8, 4, 2, 8)
   NB_PIPE_DT(NB_FP8E4M3)
   NB_PIPE_DT(NB_U16)
   NB_PIPE_DT(NB_BF16)

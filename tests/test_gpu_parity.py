@@ -59,10 +59,10 @@ def test_fit_counts_exact(fmt, F):
 
 @pytest.mark.parametrize("C", [2, 3])
 def test_fit_counts_exact_past_32_bits(C):
-    # FP32 counts just below 2^24 over 700 rows: per-class sums reach ~6e9,
+    # FP32 counts just below 2^24 over 1,200 rows: per-class sums reach ~6e9,
     # beyond any 32-bit accumulator; the counts must still be exact
     rng = np.random.default_rng(77)
-    n, F = 700, 40
+    n, F = 1200, 40
     X = rng.integers(16_000_000, 16_777_216, size=(n, F)).astype(np.float32)
     X[:, ::7] = 0
     y = (np.arange(n) % C).astype(np.int32)
