@@ -14,6 +14,7 @@
 //                       put back in the files' order.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -654,15 +655,17 @@ __global__ void k_gw_unpermute(const int64_t* order, int64_t n, const uint8_t* l
 // ---------------------------------------------------------------------------
 // Fused group-wise scorer (u8 histograms, two-class models on k opcodes): one
 // streaming pass over the full histograms in the files' order.  A pack staged
-// once per block in shared memory holds every model's int8 weight limbs (three
-// planes of kp bytes, feature t at byte t), its selection (kp uint16 opcode
-// indices), its two-class header, and the model slot of each size group.  The
-// producer warp streams RS-row tiles of the histograms (pipe.cuh); a row's 8
-// lanes find its model from its size, gather its k selected counts from the
-// staged row four at a time and accumulate them against the model's limbs
-// with dp4a -- the same integer sums as scoring the gathered row, so the
-// outputs are the same bits -- and the finished rows go straight to the
-// outputs in the files' order.
+// once per block in shared memory holds, per model, W four-feature records
+// {4 opcode columns (uint16), limb-0 bytes, limb-1 bytes} plus a plane of
+// limb-2 words, its two-class header, and the model slot of each size group.
+// The model's (opcode, weight) pairs are sorted by opcode and dealt so that
+// the 8 lanes of a row, at each of their four byte gathers, read 8 neighbouring
+// selected columns (few shared-memory bank conflicts); the k pairs are padded
+// to a multiple of 32 with column 0 and zero weights.  The producer warp
+// streams RS-row tiles of the histograms and each row's model slot
+// (pipe.cuh); a row's lanes gather four counts per record and accumulate them
+// against the limbs with dp4a.  Integer sums do not depend on the order, so
+// the results are the bits of scoring the gathered row.
 // ---------------------------------------------------------------------------
 constexpr int kGwLPR = 8;                  // lanes per row
 constexpr int kGwRPW = 32 / kGwLPR;        // rows per warp pass
@@ -674,9 +677,9 @@ struct GwArgs {
   int64_t n;
   const int64_t* sizes;
   int64_t bin_bytes;
-  int n_bins, k, kp, kw;   // kw = ceil(k / 4) words of four features
+  int n_bins, W, npad;     // records per model (a multiple of 8); padded pairs
   const void* pack;
-  uint32_t pack_bytes, sel_off, hdr_off, map_off;
+  uint32_t pack_bytes, l2_off, hdr_off, map_off;
   uint8_t* label;
   float* margin;
   float* logpost;
@@ -712,12 +715,9 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
     if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
     return;
   }
-  const unsigned char* limbs = sm;                                      // model m at m * 3 kp
-  const uint16_t* sels = reinterpret_cast<const uint16_t*>(sm + a.sel_off);   // m * kp
+  const uint4* recs = reinterpret_cast<const uint4*>(sm);                       // m * W
+  const uint32_t* l2s = reinterpret_cast<const uint32_t*>(sm + a.l2_off);       // m * W
   const C2Header* hdrs = reinterpret_cast<const C2Header*>(sm + a.hdr_off);
-  // valid bytes of the last four-feature word
-  const int kt = a.k - 4 * (a.kw - 1);
-  const uint32_t tail_mask = kt >= 4 ? 0xFFFFFFFFu : ((1u << (8 * kt)) - 1u);
 
   int ra0 = 0, ra1 = 0, ra2 = 0, rmod = 0;
   uint32_t rt = 0;
@@ -756,21 +756,20 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
       uint32_t ct = 0;
       if (valid) {
         const unsigned char* rp = st + (size_t)r * a.ld_bytes;
-        const uint16_t* sg = sels + (size_t)m * a.kp;
-        const unsigned char* lg = limbs + (size_t)m * 3 * a.kp;
-        for (int w = li; w < a.kw; w += kGwLPR) {
-          const uint2 cc = *reinterpret_cast<const uint2*>(sg + 4 * w);
-          uint32_t x = (uint32_t)rp[cc.x & 0xFFFFu] | ((uint32_t)rp[cc.x >> 16] << 8) |
-                       ((uint32_t)rp[cc.y & 0xFFFFu] << 16) | ((uint32_t)rp[cc.y >> 16] << 24);
-          if (w == a.kw - 1) x &= tail_mask;
-          const uint32_t l0 = *reinterpret_cast<const uint32_t*>(lg + 4 * w);
-          const uint32_t l1 = *reinterpret_cast<const uint32_t*>(lg + a.kp + 4 * w);
-          const uint32_t l2 = *reinterpret_cast<const uint32_t*>(lg + 2 * a.kp + 4 * w);
-          c0 = dp4a_us(x, l0, c0);
-          c1 = dp4a_us(x, l1, c1);
-          c2 = dp4a_us(x, l2, c2);
+        const uint4* rg = recs + (size_t)m * a.W;
+        const uint32_t* l2g = l2s + (size_t)m * a.W;
+        for (int w = li; w < a.W; w += kGwLPR) {
+          const uint4 rc = rg[w];
+          const uint32_t x = (uint32_t)rp[rc.x & 0xFFFFu] | ((uint32_t)rp[rc.x >> 16] << 8) |
+                             ((uint32_t)rp[rc.y & 0xFFFFu] << 16) |
+                             ((uint32_t)rp[rc.y >> 16] << 24);
+          c0 = dp4a_us(x, rc.z, c0);
+          c1 = dp4a_us(x, rc.w, c1);
+          c2 = dp4a_us(x, l2g[w], c2);
           ct = dp4a_uu(x, 0x01010101u, ct);
         }
+        // the padding pairs read column 0 with zero weights: take them out of T
+        if (li == 0) ct -= (uint32_t)a.npad * (uint32_t)rp[0];
       }
       const int k4 = sum4_transposed<kGwLPR>(c0, c1, c2, (int)ct, li);
       // lane nres + j takes row r0 + j of this pass from its group's first lane
@@ -927,8 +926,8 @@ struct nb_groupwise {
   // fused scorer (u8): the shared-memory pack and its layout
   std::vector<const nb_model*> models;
   unsigned char* pack = nullptr;
-  uint32_t pack_bytes = 0, sel_off = 0, hdr_off = 0, map_off = 0;
-  int kp = 0;
+  uint32_t pack_bytes = 0, l2_off = 0, hdr_off = 0, map_off = 0;
+  int kp = 0, W = 0, npad = 0;
 };
 
 namespace nbg {
@@ -1021,13 +1020,14 @@ extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t 
   const size_t o_mar = take(sizeof(float) * nf);
   const size_t o_lp = take(g->want_lp ? sizeof(float) * 2 * nf : 0);
   const size_t o_st = take(sizeof(int));
-  // fused-scorer pack: limbs (3 kp per model), selections (kp uint16 per model),
-  // headers, size group -> slot bytes; 16-byte aligned sections
+  // fused-scorer pack: records (16 B per four features), limb-2 words, headers,
+  // size group -> slot bytes; 16-byte aligned sections
   g->kp = models[0]->F_pad;
   g->models.assign(models, models + n_models);
-  const uint32_t lb = (uint32_t)(3 * g->kp * n_models);
-  g->sel_off = (lb + 15) / 16 * 16;
-  g->hdr_off = g->sel_off + (uint32_t)(2 * g->kp * n_models + 15) / 16 * 16;
+  g->W = (k + 31) / 32 * 8;
+  g->npad = 4 * g->W - k;
+  g->l2_off = (uint32_t)(16 * g->W * n_models);
+  g->hdr_off = g->l2_off + (uint32_t)(4 * g->W * n_models + 15) / 16 * 16;
   g->map_off = g->hdr_off + (uint32_t)(sizeof(C2Header) * n_models);
   g->pack_bytes = g->map_off + (uint32_t)(n_bins + 15) / 16 * 16;
   const size_t o_pack = dtype == NB_U8 ? take(g->pack_bytes) : 0;
@@ -1060,20 +1060,44 @@ extern "C" nb_status nb_groupwise_create(const nb_model* const* models, int32_t 
   if (e != cudaSuccess) return fail(cuda_status(e, "memcpy(groupwise tables)"));
   if (dtype == NB_U8) {
     g->pack = reinterpret_cast<unsigned char*>(base + o_pack);
-    std::vector<uint16_t> hsel((size_t)n_models * g->kp, 0);
-    for (int m = 0; m < n_models; ++m)
-      for (int t = 0; t < k; ++t) hsel[(size_t)m * g->kp + t] = (uint16_t)hcols[(size_t)m * k + t];
+    const int W = g->W, kp = g->kp;
+    std::vector<uint32_t> hrec((size_t)n_models * W * 4, 0u), hl2((size_t)n_models * W, 0u);
+    std::vector<unsigned char> hl(3 * (size_t)kp);
+    std::vector<int> ord(k);
+    for (int m = 0; m < n_models && e == cudaSuccess; ++m) {
+      // the model's three limb planes (feature t at byte t of each)
+      e = cudaMemcpy(hl.data(), models[m]->d.limbs, hl.size(), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
+      const int32_t* cm = hcols.data() + (size_t)m * k;
+      for (int t = 0; t < k; ++t) ord[t] = t;
+      std::stable_sort(ord.begin(), ord.end(), [cm](int u, int v) { return cm[u] < cm[v]; });
+      for (int pos = 0; pos < 4 * W; ++pos) {
+        // sorted pair pos goes to record j * 8 + lane, byte q, where
+        // pos = 32 j + 8 q + lane
+        const int j = pos / 32, q = (pos % 32) / 8, ln = pos % 8;
+        const size_t r = (size_t)m * W + (size_t)j * 8 + ln;
+        uint32_t col = 0, l0 = 0, l1 = 0, l2 = 0;
+        if (pos < k) {
+          const int t = ord[pos];
+          col = (uint32_t)cm[t];
+          l0 = hl[t];
+          l1 = hl[(size_t)kp + t];
+          l2 = hl[2 * (size_t)kp + t];
+        }
+        hrec[4 * r + (q >> 1)] |= col << (16 * (q & 1));
+        hrec[4 * r + 2] |= l0 << (8 * q);
+        hrec[4 * r + 3] |= l1 << (8 * q);
+        hl2[r] |= l2 << (8 * q);
+      }
+      e = cudaMemcpy(g->pack + g->hdr_off + sizeof(C2Header) * m, models[m]->d.c2,
+                     sizeof(C2Header), cudaMemcpyDeviceToDevice);
+    }
     std::vector<unsigned char> hmap((size_t)n_bins);
     for (int b = 0; b < n_bins; ++b) hmap[b] = (unsigned char)model_of[b];
-    for (int m = 0; m < n_models && e == cudaSuccess; ++m) {
-      e = cudaMemcpy(g->pack + (size_t)m * 3 * g->kp, models[m]->d.limbs, 3 * (size_t)g->kp,
-                     cudaMemcpyDeviceToDevice);
-      if (e == cudaSuccess)
-        e = cudaMemcpy(g->pack + g->hdr_off + sizeof(C2Header) * m, models[m]->d.c2,
-                       sizeof(C2Header), cudaMemcpyDeviceToDevice);
-    }
     if (e == cudaSuccess)
-      e = cudaMemcpy(g->pack + g->sel_off, hsel.data(), 2 * hsel.size(), cudaMemcpyHostToDevice);
+      e = cudaMemcpy(g->pack, hrec.data(), 4 * hrec.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->pack + g->l2_off, hl2.data(), 4 * hl2.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(g->pack + g->map_off, hmap.data(), hmap.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_status(e, "memcpy(groupwise pack)"));
@@ -1115,12 +1139,11 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   a.sizes = sizes;
   a.bin_bytes = g->bin_bytes;
   a.n_bins = g->n_bins;
-  a.k = g->k;
-  a.kp = g->kp;
-  a.kw = (g->k + 3) / 4;
+  a.W = g->W;
+  a.npad = g->npad;
   a.pack = g->pack;
   a.pack_bytes = g->pack_bytes;
-  a.sel_off = g->sel_off;
+  a.l2_off = g->l2_off;
   a.hdr_off = g->hdr_off;
   a.map_off = g->map_off;
   a.label = label;
