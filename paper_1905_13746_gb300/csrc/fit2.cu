@@ -305,15 +305,16 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
                                       (reinterpret_cast<uintptr_t>(f.ovf_add) & 15) == 0);
   // eight consumer warps and two blocks per SM for u8 rows of <= 64 vectors
   const int ncw = (dt == NB_U8 && kv <= 2) ? 8 : 12;
-  // stages of ~24 KB; rows of 2 KB or more get one row per consumer warp per
+  // eight consumers (two blocks per SM): two stages of up to 48 rows (~48 KB);
+  // twelve: stages of ~24 KB, rows of 2 KB or more one row per consumer warp per
   // stage (as many stages as fit, at least two), so that no warp idles
-  int rs = (int)(24576 / f.ld_bytes);
-  rs = rs > 32 ? 32 : (rs < 1 ? 1 : rs);
+  int rs = (int)((ncw == 8 ? 49152 : 24576) / f.ld_bytes);
+  rs = rs > (ncw == 8 ? 48 : 32) ? (ncw == 8 ? 48 : 32) : (rs < 1 ? 1 : rs);
   if (f.ld_bytes >= 2048 && rs < ncw) rs = ncw;
   PipeArgs p{};
   const uint32_t hist_bytes = (uint32_t)((dt == NB_U8 || dt == NB_U16 ? 8 : 16) * m->F_pad);
   pipe_layout(p, rs, 4, f.ld_bytes, side_ok, true, hist_bytes, n);
-  int S = 4;
+  int S = ncw == 8 ? 2 : 4;
   while (S > 2 && p.stages_off + (uint32_t)S * p.stage_bytes > 220u * 1024u) --S;
   pipe_layout(p, rs, S, f.ld_bytes, side_ok, true, hist_bytes, n);
   const int smem = (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);

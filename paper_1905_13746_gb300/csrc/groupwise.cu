@@ -758,7 +758,13 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
         const unsigned char* rp = st + (size_t)r * a.ld_bytes;
         const uint4* rg = recs + (size_t)m * a.W;
         const uint32_t* l2g = l2s + (size_t)m * a.W;
-        for (int w = li; w < a.W; w += kGwLPR) {
+        // the four rows of a pass sit 1,024-byte multiples apart (the same
+        // banks for the same column): each row group starts at another block
+        // of records, so their gathers fall in different parts of the rows
+        const int J = a.W / kGwLPR;
+        int jj = grp % J;
+        for (int it = 0; it < J; ++it, jj = jj + 1 == J ? 0 : jj + 1) {
+          const int w = jj * kGwLPR + li;
           const uint4 rc = rg[w];
           const uint32_t x = (uint32_t)rp[rc.x & 0xFFFFu] | ((uint32_t)rp[rc.x >> 16] << 8) |
                              ((uint32_t)rp[rc.y & 0xFFFFu] << 16) |
