@@ -256,12 +256,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
 template <int DT, int KV, int kFitNCW>
 static nb_status run_fit2(const Fit2Args& f, const PipeArgs& p, int smem, cudaStream_t st) {
   auto kern = k_fit2_pipe<DT, KV, kFitNCW>;
-  static int configured = 0;
-  if (smem > kSmemOptIn && configured < smem) {
+  if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(fit2)");
-    configured = smem;
-  }
   int occ = 0;
   NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (kFitNCW + 1) * 32, smem),
               "occupancy(fit2)");

@@ -540,13 +540,10 @@ nb_status launch_gather(const void* X, nb_dtype dt, int64_t ld, int F, int64_t n
       (size_t)kGatherWarps * 2 * row_bytes + (size_t)kGatherWarps * ((k + 3) & ~3) * 4;
   if (elem_size(dt) == 1 && (ld % 16) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
       smem <= 96 * 1024) {
-    static int configured = 0;
-    if ((int)smem > kSmemOptIn && configured < (int)smem) {
+    if ((int)smem > kSmemOptIn)   // per device and function: set at every launch
       NB_TRY_CUDA(cudaFuncSetAttribute(k_gather_u8s, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem),
                   "cudaFuncSetAttribute(gather)");
-      configured = (int)smem;
-    }
     count_launch();
     k_gather_u8s<<<(unsigned)cblocks, kGatherWarps * 32, smem, st>>>(
         static_cast<const unsigned char*>(X), ld, F, n_src, n, order, group, n_groups, cols, k,
@@ -1158,12 +1155,9 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   a.want_lp = g->want_lp;
   a.recheck = g->recheck;
   a.status = g->status;
-  static int configured = 0;
-  if (smem > kSmemOptIn && configured < smem) {
+  if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gw, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(k_score_gw)");
-    configured = smem;
-  }
   int occ = 0;
   NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_gw, (kGwNCW + 1) * 32,
                                                             smem),

@@ -274,12 +274,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 template <int DT, int KV, int RPW, int NCW>
 static nb_status run_pipe(const S2Args& a, const PipeArgs& p, int smem, cudaStream_t st) {
   auto kern = k_score2_pipe<DT, KV, RPW, NCW>;
-  static int configured = 0;
-  if (smem > kSmemOptIn && configured < smem) {
+  if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(pipe)");
-    configured = smem;
-  }
   int occ = 0;
   NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (NCW + 1) * 32, smem),
               "occupancy(pipe)");

@@ -505,13 +505,10 @@ nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt, in
   const int C_pad = ((m->C + 3) / 4) * 4;
   const int smem =
       (int)sizeof(float) * (GBK * (GBM + 4) + GBK * (GCB + 4) + GBM * C_pad + GBM + GBM * 8);
-  static int configured = 0;
-  if (smem > kSmemOptIn && configured < smem) {
+  if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem > 96 * 1024 ? smem : 96 * 1024),
                 "cudaFuncSetAttribute");
-    configured = smem > 96 * 1024 ? smem : 96 * 1024;
-  }
   int occ = 0;
   NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_score_gen, 256, smem),
               "occupancy");
