@@ -59,3 +59,41 @@ def test_oracle_is_not_imported_by_the_product():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "nb_oracle" not in text, fn
+
+
+def test_group_fallback_host_logic_matches_the_oracle():
+    # nb_group_fallback is host code (no GPU needed): the small-group rule of
+    # Sec. 4 against the oracle, on the paper's own list and random cases
+    import numpy as np
+
+    import paper_1905_13746_gb300 as nb
+    from oracle import groupwise as ogw
+    cc = np.full((100, 2), 30)
+    cc[[4, 7, 60, 64, 96, 97, 99]] = (5, 40)
+    assert nb.group_fallback(cc).tolist() == ogw.group_models(cc).tolist()
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        nb_ = int(rng.integers(1, 40))
+        C = int(rng.integers(2, 4))
+        cc = rng.integers(0, 12, size=(nb_, C))
+        mf = int(rng.integers(0, 8))
+        try:
+            ref = ogw.group_models(cc, mf).tolist()
+        except ValueError:
+            with pytest.raises(nb.NbError):
+                nb.group_fallback(cc, mf)
+            continue
+        assert nb.group_fallback(cc, mf).tolist() == ref
+
+
+def test_groupwise_arguments_rejected_before_any_device_work():
+    import paper_1905_13746_gb300 as nb
+    lib = nb.lib()
+    # invalid shapes fail with NB_EINVAL and a message, without touching a GPU
+    assert lib.nb_route(None, -1, 5120, 100, None, 100, None, 2, None, None, None, None, None,
+                        0, None, None) == nb.NB_EINVAL
+    assert b"nb_route" in lib.nb_last_error()
+    assert lib.nb_gather(None, nb.NB_U16, 16, 16, 1, 1, None, None, 1, None, 1, None, 16, None,
+                         None) == nb.NB_EINVAL
+    assert lib.nb_select_features(None, 0, 1, 0, None, None) == nb.NB_EINVAL
+    assert lib.nb_route_workspace(10000, 100) >= 100 * 8
