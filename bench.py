@@ -50,6 +50,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest of every rank's value x (a job's time is its slowest rank's);
+    x itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, max_ms, world):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (replicas: each rank scores its own units)."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -887,9 +905,7 @@ def main():
             model, W["low_tr"], W["y_tr"], W["low_all"], out, args.steps, args.warmup, stream)
     torch.cuda.synchronize()
     if ws > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, device)
         dist.barrier()
     ms_step = total_ms / args.steps
     n_rechecked = int(out["n_rechecked"].item())
@@ -942,7 +958,8 @@ def main():
         # the copy targets are the device buffers behind dev["ftr"] / dev["fall"]
         e2e_ms = time_e2e(model, host_pairs, dev_pairs | dev, out, host_out,
                           max(3, args.steps // 2), args.warmup, stream)
-        e2e = {"value": N / (e2e_ms * 1e-3), "unit": "files/s", "ms_per_step": e2e_ms,
+        e2e_ms = max_over_ranks(e2e_ms, device)
+        e2e = {"value": job_rate(N, e2e_ms, ws), "unit": "files/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
         del host, devb, dev
 
@@ -962,7 +979,7 @@ def main():
         cpu = cpu_oracle_sample(Xfit, W["y"][tr[:nfit]], Xsc, len(tr), N)
         cpu.pop("step_s_extrapolated", None)
 
-    files_per_s = ws * N / (ms_step * 1e-3)
+    files_per_s = job_rate(N, ms_step, ws)
     line = {
         "metric": METRIC, "value": files_per_s, "unit": "files/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
