@@ -281,3 +281,23 @@ def test_plain_method_with_all_opcodes_in_one_group():
     res = to_np(gw.classify(torch.from_numpy(X).cuda(), torch.from_numpy(s).cuda()))
     ref = oscore(X.astype(np.float64), mn_fit(X, y, 2))
     compare(res, ref)
+
+
+@pytest.mark.parametrize("want_lp,recheck", [(False, nb.NB_RECHECK_LABEL), (True, nb.NB_RECHECK_OFF),
+                                             (False, nb.NB_RECHECK_LP)])
+def test_groupwise_output_and_recheck_options(want_lp, recheck):
+    n_bins, F, k = 10, 128, 32
+    X, y, s = _workload(101, 5000, F, n_bins)
+    tr, te = synth.split_per_class(102, y)
+    fo, fg = _fit_both(X[tr], y[tr], s[tr], k, nb.NB_SELECT_TOTAL, n_bins)
+    gw = nb.Groupwise(fg["models"], fg["cols"], fg["model_of"], F, max_files=len(te),
+                      want_logpost=want_lp, recheck=recheck)
+    res = to_np(gw.classify(torch.from_numpy(X[te]).cuda(), torch.from_numpy(s[te]).cuda()))
+    ref = ogw.score_groups(X[te], s[te], fo, want_lp=want_lp)
+    if recheck == nb.NB_RECHECK_OFF:
+        # no recheck: labels may differ only on rows the FP32 bound could not settle
+        agree = (res["label"] == ref["label"]).mean()
+        assert agree > 0.999
+        assert res["n_rechecked"] == 0
+    else:
+        compare(res, ref, check_lp=want_lp)
