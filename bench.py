@@ -756,6 +756,15 @@ def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_tota
             "step_s_extrapolated": step_s}
 
 
+def workload_config(N, F, n_train, ws):
+    """The headline workload, as both arms name it."""
+    return {"workload": f"multinomial NB, C=2, N={N} files x F={F} opcode counts (u16, "
+                        f"lognormal(8.5, 1) totals, Dirichlet(0.1) class profiles), fit on the "
+                        f"2:1 per-class train split ({n_train} files) + score all N with log "
+                        f"posteriors (labels equal to the FP64 decision)",
+            "N": N, "F": F, "C": 2, "train_files": n_train, "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -790,8 +799,7 @@ def run_reference(args):
             "ms_per_step": statistics.median([x["step_s_extrapolated"] for x in vals]) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"multinomial NB, C=2, N={N} files x F={F} u16 counts",
-                       "N": N, "F": F, "C": 2},
+            "config": workload_config(N, F, len(tr), ws),
             "cpu_baseline": {"value": v, "unit": "files/s", "cores": 1, "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "files/s", "h2d_bytes_per_step": 0,
@@ -985,14 +993,13 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": f"multinomial NB, C=2, N={N} files x F={F} opcode counts "
-                               f"(u16 generated, stored u8 + overflow list), fit on the "
-                               f"2:1 per-class train split ({len(W['tr'])} files) + score "
-                               f"all N with log posteriors and FP64 recheck",
-                   "N": N, "F": F, "C": 2, "train_files": len(W["tr"]),
-                   "storage": "u8+overflow", "weights": "22-bit fixed-point Delta, int8 limbs",
-                   "l2": "inputs larger than L2 (score reads %.2f GB per step)" % (score_bytes / 1e9),
-                   "parallelism": f"replicas x{ws}"},
+        "config": workload_config(N, F, len(W["tr"]), ws),
+        "implementation": {"storage": "u8 + overflow list (packed from the u16 counts)",
+                           "weights": "22-bit fixed-point Delta, int8 limbs, dp4a",
+                           "recheck": "FP64 for rows whose rigorous bound does not settle "
+                                      "the label or the log posteriors to 1e-5",
+                           "l2": "inputs larger than L2 (score reads %.2f GB per step)"
+                                 % (score_bytes / 1e9)},
         "roofline": {"bound": "hbm", "kernel": "nb_score_group (k_score2_pipe u8 + k_recheck scan)",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
