@@ -23,14 +23,16 @@
 // epilogue bounds both and marks the row for the FP64 recheck when the bound
 // does not settle the label (or the log posteriors).
 //
-// Roles of one persistent CTA per SM (352 threads):
-//   warps 0-7  convert u8 rows to FP16 operand tiles, drain the accumulators,
-//              run the epilogue (arg-max, top-2 margin, log-sum-exp);
-//   warp 8     streams each tile's rows into shared memory (2-D tensor TMA,
-//              128 rows x 128 features per box, 128-byte swizzle, zero fill
-//              past the last row and feature);
-//   warp 9     allocates tensor memory and issues the MMAs (one thread);
-//   warp 10    streams the weight-limb stages (bulk copies).
+// Roles of one persistent CTA per SM (608 threads):
+//   warps 0-15  convert u8 rows to FP16 operand tiles (four warps per tensor-
+//               memory lane quadrant), drain the accumulators, run the
+//               epilogue (arg-max, top-2 margin, log-sum-exp), 16 classes each;
+//   warp 16     streams each tile's rows into shared memory (2-D tensor TMA,
+//               128 rows x 128 features per box, 128-byte swizzle, zero fill
+//               past the last row and feature);
+//   warp 17     allocates tensor memory and issues the MMAs (one thread);
+//   warp 18     streams the weight-limb stages (bulk copies, multicast to the
+//               CTAs of a cluster).
 // Every wait is bounded; a wait that runs out raises ST_TIMEOUT, all roles
 // stop, outstanding copies and MMAs are waited for, and tensor memory is freed.
 #include <cuda.h>
