@@ -51,6 +51,20 @@ def test_route_groups_and_stable_order(n):
         assert (cc == ogw.group_class_counts(g_ref, y)).all()
 
 
+@pytest.mark.parametrize("n_bins,bin_bytes", [(1, 5120), (512, 1000), (333, 7)])
+def test_route_group_count_extremes(n_bins, bin_bytes):
+    # one group, the most groups a route takes (512: two scan slices per
+    # group), and a count that does not divide the 1,024 scan threads
+    n = 20000
+    s = np.random.default_rng(n_bins).integers(0, bin_bytes * (n_bins + 3), n).astype(np.int64)
+    r = nb.route(torch.from_numpy(s).cuda(), bin_bytes=bin_bytes, n_bins=n_bins)
+    g = ogw.size_group(s, bin_bytes, n_bins)
+    assert (r["group"].cpu().numpy() == g).all()
+    assert (r["order"].cpu().numpy() == np.argsort(g, kind="stable")).all()
+    offs = r["offsets"].cpu().numpy()
+    assert (offs == np.concatenate([[0], np.cumsum(np.bincount(g, minlength=n_bins))])).all()
+
+
 def test_route_through_a_model_map():
     n = 30000
     s = _sizes(7, n)
