@@ -421,8 +421,12 @@ extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype d
   const int es = elem_size(dtype);
   const bool aligned =
       ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ld * es) % 16 == 0);
-  if (m->kind == NB_MULTINOMIAL && m->C == 2 && aligned)
+  if (m->kind == NB_MULTINOMIAL && m->C == 2 && aligned) {
+    // the two-class scorers count the rows they mark, so the recheck can skip
+    // its scan when there are none
+    o.counted = n_rechecked != nullptr && recheck != NB_RECHECK_OFF;
     s = launch_score2(m, X, dtype, n, ld, aux, o, st);
+  }
   else if (tc_eligible(m, dtype, X, ld))
     s = launch_score_tc(m, X, n, ld, aux, o, st);
   else

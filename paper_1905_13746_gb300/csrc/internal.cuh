@@ -143,6 +143,7 @@ struct ScoreOut {
   int64_t* n_rechecked;
   int want_lp;
   int recheck;
+  bool counted = false;   // the scorer counted its marked rows into n_rechecked
 };
 
 nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt,

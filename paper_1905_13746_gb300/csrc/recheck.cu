@@ -116,12 +116,14 @@ struct RArgs {
   RModel md;
   int64_t n;
   int want_lp;
+  int counted;   // *n_rechecked already holds the marked rows (skip when 0, do not add)
   unsigned long long* n_rechecked;
 };
 
 __global__ void __launch_bounds__(256) k_recheck(const RArgs a) {
   __shared__ double s_sh[8][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (a.counted && *a.n_rechecked == 0ull) return;   // the scorer marked no row
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   unsigned long long cnt = 0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < a.n; base += nwarps * 32) {
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_recheck(const RArgs a) {
       ++cnt;
     }
   }
-  if (lane == 0 && cnt && a.n_rechecked) atomicAdd(a.n_rechecked, cnt);
+  if (lane == 0 && cnt && a.n_rechecked && !a.counted) atomicAdd(a.n_rechecked, cnt);
 }
 
 nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t n, int64_t ld,
@@ -156,6 +158,7 @@ nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t 
   a.md = RModel{m->kind, m->C, m->d.p0, m->d.p1, m->d.log_pi, m->d.gconst};
   a.n = n;
   a.want_lp = o.want_lp;
+  a.counted = o.counted ? 1 : 0;
   a.n_rechecked = reinterpret_cast<unsigned long long*>(o.n_rechecked);
   const int64_t chunks = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;

@@ -344,6 +344,7 @@ nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt, int64_t n
   a.logpost = o.logpost;
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
+  a.marks = o.counted ? reinterpret_cast<unsigned long long*>(o.n_rechecked) : nullptr;
   a.status = m->d.status;
   int smem;
   if (dt == NB_U8) {

@@ -32,6 +32,7 @@ struct S2Args {
   float* logpost;
   int want_lp;
   int recheck;
+  unsigned long long* marks;   // counts the rows marked for the recheck, or nullptr
   int k_base;     // FP32 path: rounding depth of a row without overflow entries
   int* status;
 };
@@ -42,7 +43,7 @@ __device__ __forceinline__ float softplusf(float z) {
 
 // Outputs of one row from its log-odds d and the bound tau on |d - d_exact|:
 // label (or the recheck mark), margin |d|, log posteriors -softplus(-+d).
-__device__ __forceinline__ void c2_store(uint8_t* label, float* margin, float* logpost,
+__device__ __forceinline__ bool c2_store(uint8_t* label, float* margin, float* logpost,
                                          int want_lp, int recheck, int64_t row, float d,
                                          float tau) {
   bool flag = false;
@@ -57,10 +58,20 @@ __device__ __forceinline__ void c2_store(uint8_t* label, float* margin, float* l
     logpost[2 * row] = -softplusf(d);
     logpost[2 * row + 1] = -softplusf(-d);
   }
+  return flag;
 }
 
+// c2_store for the single-group scorers; the marked rows are also counted into
+// a.marks (the call's n_rechecked), one atomic per warp, so that the FP64
+// recheck can skip its scan when no row was marked.
 __device__ __forceinline__ void c2_epilogue(const S2Args& a, int64_t row, float d, float tau) {
-  c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, row, d, tau);
+  const bool flag = c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, row, d, tau);
+  if (a.marks) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, flag);
+    if (m && (int)(threadIdx.x & 31) == __ffs(act) - 1)
+      atomicAdd(a.marks, (unsigned long long)__popc(m));
+  }
 }
 
 // Rigorous bound on |d_gpu - d_exact| of the fixed-point u8 path: the Delta
