@@ -311,22 +311,35 @@ __global__ void __launch_bounds__(256) k_score_gauss(const GGArgs a) {
     for (int c = 0; c < a.C; ++c) {
       const float* mu = a.mu + (int64_t)c * a.F_pad;
       const float* iv = a.ivar + (int64_t)c * a.F_pad;
-      float q = 0.f, B = 0.f;
+      // q = sum v dx^2 (the score); a2 = sum v |dx| |m| and a4 = sum v m^2 feed
+      // the bound below
+      float q = 0.f, a2 = 0.f, a4 = 0.f;
       for (int j = lane; j < a.F; j += 32) {
         const float x = __ldg(xr + j), m = mu[j], v = iv[j];
         const float dx = x - m;
         q = fmaf(dx * dx, v, q);
-        const float ab = fabsf(x) + fabsf(m);
-        B = fmaf(ab * ab, v, B);
+        a2 = fmaf(fabsf(dx) * fabsf(m), v, a2);
+        a4 = fmaf(m * m, v, a4);
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
-        B += __shfl_xor_sync(0xFFFFFFFFu, B, off);
+        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, off);
+        a4 += __shfl_xor_sync(0xFFFFFFFFu, a4, off);
       }
       if (lane == 0) {
-        ssh[warp][c] = a.kc[c] - 0.5f * q;
-        tsh[warp][c] = 0.5f * gam * B * 1.01f + 3e-7f * fabsf(a.kc[c]) + 1e-12f * (B + fabsf(a.kc[c]));
+        // |s - s_FP64| with u = 2^-24: per term, m = fl(mu) and v = fl(1/var)
+        // are within u relative, dx = fl(x - m) is within u(|dx| + |m|) of
+        // x - mu, so v dx^2 is within u v (4 dx^2 + 2 |dx||m|) + 2u^2 v (dx^2 +
+        // m^2); the FP32 sum adds gamma * q; kc and the final subtraction add
+        // u (|kc| + |s|).  1% slack covers the FP32 evaluation of the bound.
+        const float u = 5.9604645e-8f;
+        const float sc = a.kc[c] - 0.5f * q;
+        ssh[warp][c] = sc;
+        tsh[warp][c] = (0.5f * (u * (4.f * q + 2.f * a2) * (1.f + 2.f * u) +
+                                2.f * u * u * (q + a4) + gam * q) +
+                        u * (fabsf(a.kc[c]) + fabsf(sc))) * 1.01f +
+                       1e-12f * (q + fabsf(a.kc[c])) + 1e-30f;
       }
     }
     __syncwarp();
