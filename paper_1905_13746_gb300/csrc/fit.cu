@@ -834,13 +834,14 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
 __global__ void __launch_bounds__(256) k_gauss_partial(const float* X, int64_t ld, int64_t n,
                                                        int F, int C, const int32_t* y, int pass,
                                                        const double* mu_c, const double* mu_all,
-                                                       double* partial, int* status) {
+                                                       double* partial, int64_t chunk_rows,
+                                                       int* status) {
   // partial layout: [chunk][slot 0..C][F]
   extern __shared__ double acc[];   // [8 warps][C+1][kGTile]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j0 = blockIdx.y * kGTile;
-  const int64_t r0 = (int64_t)blockIdx.x * kGChunkRows;
-  int64_t r1 = r0 + kGChunkRows;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
+  int64_t r1 = r0 + chunk_rows;
   if (r1 > n) r1 = n;
   const int S = C + 1;
   for (int k = threadIdx.x; k < 8 * S * kGTile; k += blockDim.x) acc[k] = 0.0;
@@ -896,21 +897,23 @@ __global__ void k_gauss_reduce(const double* partial, int nchunk, int F, int C,
   }
 }
 
-// var += eps, log prior, Gaussian constants and FP32 tables.  One block.
-__global__ void __launch_bounds__(1024) k_gauss_finalize(
+// var += eps, log prior, Gaussian constants and FP32 tables.  One block of
+// 256 threads; reductions by warp shuffles and one pass over the warp results.
+__global__ void __launch_bounds__(256) k_gauss_finalize(
     const double* m2_all, int F, int F_pad, int C, double var_smoothing,
     const unsigned long long* nc, int64_t n, int prior_given, const double* mu, double* var,
     double* log_pi, double* gconst, float* g_mu, float* g_ivar, float* g_const, int* status) {
-  __shared__ double red[1024];
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double mx = 0.0;
   for (int j = threadIdx.x; j < F; j += blockDim.x) mx = fmax(mx, m2_all[j]);
-  red[threadIdx.x] = mx;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+  if (lane == 0) red[warp] = mx;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
-  }
-  const double eps = var_smoothing * red[0];
+  double gm = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, red[w]);
+  const double eps = var_smoothing * gm;
   __syncthreads();
   for (int k = threadIdx.x; k < C * F_pad; k += blockDim.x) {
     const int c = k / F_pad, j = k % F_pad;
@@ -930,18 +933,18 @@ __global__ void __launch_bounds__(1024) k_gauss_finalize(
   for (int c = 0; c < C; ++c) {
     double s = 0.0;
     for (int j = threadIdx.x; j < F; j += blockDim.x) s += log(kTwoPi * var[(int64_t)c * F + j]);
-    red[threadIdx.x] = s;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+    if (lane == 0) red[warp] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
     if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
       if (!prior_given) {
         if (nc[c] == 0) atomicOr(status, ST_BAD_LABEL);
         log_pi[c] = nc[c] ? log((double)nc[c]) - log((double)n) : 0.0;
       }
-      gconst[c] = log_pi[c] - 0.5 * red[0];
+      gconst[c] = log_pi[c] - 0.5 * t;
       g_const[c] = (float)gconst[c];
     }
     __syncthreads();
@@ -963,7 +966,10 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
   k_label_hist<<<(unsigned)(g < sms * 4 ? g : sms * 4), 256, 0, st>>>(
       y, n, C, reinterpret_cast<unsigned long long*>(d.nc), d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_label_hist");
-  const int nchunk = (int)((n + kGChunkRows - 1) / kGChunkRows);
+  // row chunks: 32 rows for small fits (more blocks in flight), else 256; the
+  // partials are summed in chunk order, so the result depends only on n
+  const int64_t chunk_rows = n <= 65536 ? 32 : kGChunkRows;
+  const int nchunk = (int)((n + chunk_rows - 1) / chunk_rows);
   const size_t part_elems = (size_t)nchunk * S * F;
   const size_t extra = (size_t)F * 2;   // mu_all, m2_all
   void* scratch = nullptr;
@@ -982,7 +988,7 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
   for (int pass = 0; pass < 2; ++pass) {
     count_launch();
     k_gauss_partial<<<grid, 256, smem, st>>>(X, ld, n, F, C, y, pass, d.p0, mu_all, partial,
-                                             d.status);
+                                             chunk_rows, d.status);
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_partial");
     count_launch();
     k_gauss_reduce<<<rb < 1024 ? rb : 1024, 256, 0, st>>>(
@@ -991,7 +997,7 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_reduce");
   }
   count_launch();
-  k_gauss_finalize<<<1, 1024, 0, st>>>(m2_all, F, m->F_pad, C, m->var_smoothing,
+  k_gauss_finalize<<<1, 256, 0, st>>>(m2_all, F, m->F_pad, C, m->var_smoothing,
                                        reinterpret_cast<unsigned long long*>(d.nc), n,
                                        log_prior_dev != nullptr, d.p0, d.p1, d.log_pi, d.gconst,
                                        d.g_mu, d.g_ivar, d.g_const, d.status);

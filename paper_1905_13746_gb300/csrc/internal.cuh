@@ -187,7 +187,8 @@ __global__ void k_label_hist(const int32_t* y, int64_t n, int C, unsigned long l
                              int* status);
 __global__ void k_gauss_partial(const float* X, int64_t ld, int64_t n, int F, int C,
                                 const int32_t* y, int pass, const double* mu_c,
-                                const double* mu_all, double* partial, int* status);
+                                const double* mu_all, double* partial, int64_t chunk_rows,
+                                int* status);
 __global__ void k_gauss_reduce(const double* partial, int nchunk, int F, int C,
                                const unsigned long long* nc, int64_t n, int pass, double* mu_c,
                                double* mu_all, double* m2_c, double* m2_all);

@@ -115,7 +115,7 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
   for (int pass = 0; pass < 2; ++pass) {
     count_launch();
     k_gauss_partial<<<grid, 256, smem, st>>>(X, ld, n, F, C, y, pass, d.p0, mu_all, partial,
-                                             d.status);
+                                             (int64_t)kGChunkRows, d.status);
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_partial");
     count_launch();
     k_gauss_reduce<<<rb < 1024 ? rb : 1024, 256, 0, st>>>(
@@ -124,7 +124,7 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_reduce");
   }
   count_launch();
-  k_gauss_finalize<<<1, 1024, 0, st>>>(m2_all, F, m->F_pad, C, vs,
+  k_gauss_finalize<<<1, 256, 0, st>>>(m2_all, F, m->F_pad, C, vs,
                                        reinterpret_cast<unsigned long long*>(d.nc), n,
                                        prior != nullptr, d.p0, d.p1, d.log_pi, d.gconst, d.g_mu,
                                        d.g_ivar, d.g_const, d.status);
