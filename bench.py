@@ -767,8 +767,10 @@ def run_many_class(args, device):
 # ----------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample of the same workload)
 # ----------------------------------------------------------------------------
-def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_total):
-    """Time the FP64 oracle (single thread) on a sample; extrapolate one step."""
+def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_total,
+                      nthreads=1):
+    """Time the FP64 oracle on a sample; extrapolate one step.  Its fit is one
+    thread; its scoring uses nthreads threads (the oracle's own option)."""
     import oracle
     Xf = X16_host_fit.astype(np.float64)
     t = time.perf_counter()
@@ -780,12 +782,13 @@ def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_tota
     for r0 in range(0, X16_host_score.shape[0], chunk):
         Xs = X16_host_score[r0:r0 + chunk].astype(np.float64)
         t = time.perf_counter()
-        oracle.score(Xs, m, nthreads=1)
+        oracle.score(Xs, m, nthreads=nthreads)
         t_score += time.perf_counter() - t
     nf, ns = X16_host_fit.shape[0], X16_host_score.shape[0]
     step_s = t_fit * (n_train_total / nf) + t_score * (n_total / ns)
-    return {"value": n_total / step_s, "unit": "files/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, 1 thread: fit on {nf} training files "
+    threads = "1 thread" if nthreads == 1 else f"fit 1 thread, score {nthreads} threads"
+    return {"value": n_total / step_s, "unit": "files/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"FP64 C oracle, {threads}: fit on {nf} training files "
                       f"({t_fit:.2f} s) + score {ns} files ({t_score:.2f} s), "
                       f"extrapolated linearly to fit {n_train_total} + score {n_total}",
             "step_s_extrapolated": step_s}
@@ -1018,6 +1021,10 @@ def main():
         Xfit = W["X16"].view(torch.int16).index_select(0, fit_rows).cpu().numpy().view(np.uint16)
         Xsc = W["X16"][: args.cpu_score_rows].view(torch.int16).cpu().numpy().view(np.uint16)
         cpu = cpu_oracle_sample(Xfit, W["y"][tr[:nfit]], Xsc, len(tr), N)
+        ncores = os.cpu_count() or 1
+        if ncores > 1:   # the same sample with the oracle scoring on every host core
+            allc = cpu_oracle_sample(Xfit, W["y"][tr[:nfit]], Xsc, len(tr), N, nthreads=ncores)
+            cpu["all_cores"] = {k: allc[k] for k in ("value", "cores", "sample")}
         cpu.pop("step_s_extrapolated", None)
 
     files_per_s = job_rate(N, ms_step, ws)
