@@ -9,6 +9,12 @@
 
 namespace nbg {
 
+// Programmatic dependent launch: a kernel launched with launch_pdl() may start
+// while the previous kernel on its stream drains; it calls pdl_wait() before it
+// reads anything that kernel wrote (the wait returns at once when there is no
+// such kernel).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // 16-byte streaming load: read once, do not keep in L1.
 __device__ __forceinline__ uint4 ld_stream16(const void* p) {
   uint4 v;

@@ -487,42 +487,52 @@ __global__ void __launch_bounds__(1024) k_derive_c2(const double* log_theta, con
 }
 
 // Two-class finish of the fit in one launch (Sec. 4 likelihoods, Laplace
-// smoothing): every block of 256 features computes the class totals N_0, N_1
-// from the exact counts, log theta of its features in FP64, Delta =
-// log theta_1 - log theta_0 and its FP32 copies, and the centred weights of
-// the general-C tables (w_c = log theta_c - mean); the blocks' maxima of
+// smoothing).  FP64 is slow on this part, so the logs are spread thin: a block
+// of 2 * kFinF threads owns kFinF features, sums the class totals N_0, N_1 from
+// the exact counts (log(N_c + alpha F) once per block), takes one
+// log(n_cj + alpha) per thread, then one thread per feature forms
+// Delta = log theta_1 - log theta_0, its FP32 copies and the centred weights
+// of the general-C tables (w_c = log theta_c - mean).  The blocks' maxima of
 // |Delta| meet in fin[], and the last block to finish derives the fixed-point
 // scale S and writes the integer Delta and its limbs.  fin[] (zero before the
 // launch) is cleared again by that block.
-__global__ void __launch_bounds__(256) k_fit_finish_c2(
+constexpr int kFinF = 64;
+
+__global__ void __launch_bounds__(2 * kFinF) k_fit_finish_c2(
     const unsigned long long* counts, const unsigned long long* nc, int64_t n, int F, int F_pad,
     int nvec8, double alpha, int prior_given, double* log_theta, double* log_pi, C2Header* hdr,
     float* delta, int32_t* delta_q, uint4* limbs, float4* il4, float4* il8, float4* il16,
     float* w, float* bias, float* wmax, unsigned long long* fin, int* status) {
-  __shared__ unsigned long long part[2][256];
-  __shared__ double dmax[256];
-  __shared__ float fmax32[256], wm32[256];
+  constexpr int NT = 2 * kFinF, NW = NT / 32;
+  __shared__ unsigned long long part[2][NW];
+  __shared__ double ld[2];
+  __shared__ double lt[2][kFinF];
+  __shared__ double dmax[kFinF / 32];
+  __shared__ float fmax32[kFinF / 32], wm32[kFinF / 32];
   __shared__ int last;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  pdl_wait();   // the counting kernels' totals
   unsigned long long s0 = 0, s1 = 0;
-  for (int j = tid; j < F; j += 256) {
+#pragma unroll 4
+  for (int j = tid; j < F; j += NT) {
     s0 += counts[j];
     s1 += counts[(int64_t)F + j];
   }
-  part[0][tid] = s0;
-  part[1][tid] = s1;
-  __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if (tid < h) {
-      part[0][tid] += part[0][tid + h];
-      part[1][tid] += part[1][tid + h];
-    }
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
   }
-  const double ld0 = log((double)part[0][0] + alpha * (double)F);
-  const double ld1 = log((double)part[1][0] + alpha * (double)F);
-  if (blockIdx.x == 0 && tid < 2) {
-    if (!prior_given) {
+  if (lane == 0) {
+    part[0][warp] = s0;
+    part[1][warp] = s1;
+  }
+  __syncthreads();
+  if (tid < 2) {
+    unsigned long long t = 0;
+    for (int k = 0; k < NW; ++k) t += part[tid][k];
+    ld[tid] = log((double)t + alpha * (double)F);
+    if (blockIdx.x == 0 && !prior_given) {
       if (nc[tid] == 0) {
         atomicOr(status, ST_BAD_LABEL);
         log_pi[tid] = 0.0;
@@ -531,65 +541,84 @@ __global__ void __launch_bounds__(256) k_fit_finish_c2(
       }
     }
   }
-  const int j = blockIdx.x * 256 + tid;
-  double ad = 0.0;
-  float a32 = 0.f, aw = 0.f;
-  if (j < F_pad) {
-    double d = 0.0;
-    float w0 = 0.f, w1 = 0.f;
-    if (j < F) {
-      const double lt0 = log((double)counts[j] + alpha) - ld0;
-      const double lt1 = log((double)counts[(int64_t)F + j] + alpha) - ld1;
-      log_theta[j] = lt0;
-      log_theta[(int64_t)F + j] = lt1;
-      d = lt1 - lt0;
-      if (!isfinite(d)) atomicOr(status, ST_BAD_TABLE);
-      const double m = (lt0 + lt1) / 2.0;
-      w0 = (float)(lt0 - m);
-      w1 = (float)(lt1 - m);
-      ad = fabs(d);
-    }
-    const float d32 = (float)d;
-    a32 = fabsf(d32);
-    aw = fmaxf(fabsf(w0), fabsf(w1));
-    delta[j] = d32;
-    w[j] = w0;
-    w[(int64_t)F_pad + j] = w1;
-    // FP32 tables for 4 / 8 / 16 elements per vector: quad q of vector v is
-    // slot q * (F_pad / EPV) + v
-    {
-      float* t = reinterpret_cast<float*>(il4);
-      const int epv = 4, vv = j / epv, e = j % epv;
-      t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
-    }
-    {
-      float* t = reinterpret_cast<float*>(il8);
-      const int epv = 8, vv = j / epv, e = j % epv;
-      t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
-    }
-    {
-      float* t = reinterpret_cast<float*>(il16);
-      const int epv = 16, vv = j / epv, e = j % epv;
-      t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
-    }
-  }
-  dmax[tid] = ad;
-  fmax32[tid] = a32;
-  wm32[tid] = aw;
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if (tid < h) {
-      dmax[tid] = fmax(dmax[tid], dmax[tid + h]);
-      fmax32[tid] = fmaxf(fmax32[tid], fmax32[tid + h]);
-      wm32[tid] = fmaxf(wm32[tid], wm32[tid + h]);
+  {
+    // one (class, feature) log per thread
+    const int c = tid / kFinF, jl = tid % kFinF;
+    const int j = blockIdx.x * kFinF + jl;
+    double v = 0.0;
+    if (j < F) {
+      v = log((double)counts[(int64_t)c * F + j] + alpha) - ld[c];
+      log_theta[(int64_t)c * F + j] = v;
     }
-    __syncthreads();
+    lt[c][jl] = v;
   }
+  __syncthreads();
+  if (tid < kFinF) {
+    const int j = blockIdx.x * kFinF + tid;
+    double ad = 0.0;
+    float a32 = 0.f, aw = 0.f;
+    if (j < F_pad) {
+      double d = 0.0;
+      float w0 = 0.f, w1 = 0.f;
+      if (j < F) {
+        const double lt0 = lt[0][tid], lt1 = lt[1][tid];
+        d = lt1 - lt0;
+        if (!isfinite(d)) atomicOr(status, ST_BAD_TABLE);
+        const double m = (lt0 + lt1) / 2.0;
+        w0 = (float)(lt0 - m);
+        w1 = (float)(lt1 - m);
+        ad = fabs(d);
+      }
+      const float d32 = (float)d;
+      a32 = fabsf(d32);
+      aw = fmaxf(fabsf(w0), fabsf(w1));
+      delta[j] = d32;
+      w[j] = w0;
+      w[(int64_t)F_pad + j] = w1;
+      // FP32 tables for 4 / 8 / 16 elements per vector: quad q of vector v is
+      // slot q * (F_pad / EPV) + v
+      {
+        float* t = reinterpret_cast<float*>(il4);
+        const int epv = 4, vv = j / epv, e = j % epv;
+        t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
+      }
+      {
+        float* t = reinterpret_cast<float*>(il8);
+        const int epv = 8, vv = j / epv, e = j % epv;
+        t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
+      }
+      {
+        float* t = reinterpret_cast<float*>(il16);
+        const int epv = 16, vv = j / epv, e = j % epv;
+        t[((size_t)(e >> 2) * (F_pad / epv) + vv) * 4 + (e & 3)] = d32;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ad = fmax(ad, __shfl_down_sync(0xffffffffu, ad, o));
+      a32 = fmaxf(a32, __shfl_down_sync(0xffffffffu, a32, o));
+      aw = fmaxf(aw, __shfl_down_sync(0xffffffffu, aw, o));
+    }
+    if (lane == 0) {
+      dmax[warp] = ad;
+      fmax32[warp] = a32;
+      wm32[warp] = aw;
+    }
+  }
+  __syncthreads();
   if (tid == 0) {
+    double ad = dmax[0];
+    float a32 = fmax32[0], aw = wm32[0];
+    for (int k = 1; k < kFinF / 32; ++k) {
+      ad = fmax(ad, dmax[k]);
+      a32 = fmaxf(a32, fmax32[k]);
+      aw = fmaxf(aw, wm32[k]);
+    }
     // non-negative floating-point values order like their bit patterns
-    atomicMax(&fin[0], (unsigned long long)__double_as_longlong(dmax[0]));
-    atomicMax(reinterpret_cast<unsigned int*>(&fin[1]), __float_as_uint(fmax32[0]));
-    atomicMax(reinterpret_cast<unsigned int*>(&fin[1]) + 1, __float_as_uint(wm32[0]));
+    atomicMax(&fin[0], (unsigned long long)__double_as_longlong(ad));
+    atomicMax(reinterpret_cast<unsigned int*>(&fin[1]), __float_as_uint(a32));
+    atomicMax(reinterpret_cast<unsigned int*>(&fin[1]) + 1, __float_as_uint(aw));
     __threadfence();
     last = atomicAdd(&fin[2], 1ull) == (unsigned long long)(gridDim.x - 1);
   }
@@ -605,7 +634,7 @@ __global__ void __launch_bounds__(256) k_fit_finish_c2(
     S = 22 - e;
   }
   const double scale = ldexp(1.0, S);
-  for (int jj = tid; jj < F_pad; jj += 256) {
+  for (int jj = tid; jj < F_pad; jj += NT) {
     const double d = jj < F ? log_theta[(int64_t)F + jj] - log_theta[jj] : 0.0;
     const int32_t q = (int32_t)llrint(d * scale);   // |q| <= 2^22
     delta_q[jj] = q;
@@ -697,8 +726,12 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
                                  const double* log_prior_dev, cudaStream_t st) {
   const int C = m->C, F = m->F;
   ModelDev& d = m->d;
-  NB_TRY_CUDA(cudaMemsetAsync(d.counts, 0, sizeof(uint64_t) * (size_t)C * F, st), "memset");
-  NB_TRY_CUDA(cudaMemsetAsync(d.nc, 0, sizeof(uint64_t) * C, st), "memset");
+  // counts and nc are neighbours in the model's allocation: one clear for both
+  NB_TRY_CUDA(cudaMemsetAsync(d.counts, 0,
+                              (size_t)(reinterpret_cast<char*>(d.nc + C) -
+                                       reinterpret_cast<char*>(d.counts)),
+                              st),
+              "memset");
   if (log_prior_dev && log_prior_dev != d.log_pi)
     NB_TRY_CUDA(cudaMemcpyAsync(d.log_pi, log_prior_dev, sizeof(double) * C,
                                 cudaMemcpyDeviceToDevice, st),
@@ -795,12 +828,13 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
   }
   if (C == 2) {
     count_launch();
-    k_fit_finish_c2<<<(m->F_pad + 255) / 256, 256, 0, st>>>(
-        reinterpret_cast<unsigned long long*>(d.counts),
-        reinterpret_cast<unsigned long long*>(d.nc), n, F, m->F_pad, m->nvec8, m->alpha,
-        log_prior_dev != nullptr, d.p0, d.log_pi, d.c2, d.delta, d.delta_q, d.limbs, d.il[0],
-        d.il[1], d.il[2], d.w, d.bias, d.wmax, d.fin, d.status);
-    NB_TRY_CUDA(cudaGetLastError(), "k_fit_finish_c2");
+    NB_TRY_CUDA(launch_pdl(k_fit_finish_c2, dim3((m->F_pad + kFinF - 1) / kFinF), dim3(2 * kFinF),
+                           0, st, reinterpret_cast<const unsigned long long*>(d.counts),
+                           reinterpret_cast<const unsigned long long*>(d.nc), (int64_t)n, F,
+                           m->F_pad, m->nvec8, m->alpha, (int)(log_prior_dev != nullptr), d.p0,
+                           d.log_pi, d.c2, d.delta, d.delta_q, d.limbs, d.il[0], d.il[1],
+                           d.il[2], d.w, d.bias, d.wmax, d.fin, d.status),
+                "k_fit_finish_c2");
     return NB_OK;
   }
   count_launch();

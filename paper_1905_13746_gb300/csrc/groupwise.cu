@@ -682,6 +682,7 @@ struct GwArgs {
   float* logpost;
   int want_lp, recheck;
   int* status;
+  unsigned long long* marks;   // the call's n_rechecked: marked rows are counted here, or null
 };
 
 __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
@@ -727,7 +728,13 @@ __global__ void __launch_bounds__((kGwNCW + 1) * 32, 1)
       const float Dsum = (float)D * H.inv_scale;
       const float d = Dsum + H.b;
       const float tau = c2_tau_u8((float)rt, Dsum, H.b, H.inv_scale, H.maxabs);
-      c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, rrow, d, tau);
+      const bool flag = c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, rrow, d, tau);
+      if (a.marks) {
+        // one atomic per warp, so that the recheck can skip its scan when no row is marked
+        const unsigned act = __activemask();
+        const unsigned mk = __ballot_sync(act, flag);
+        if (mk && lane == __ffs(act) - 1) atomicAdd(a.marks, (unsigned long long)__popc(mk));
+      }
     }
     nres = 0;
   };
@@ -944,7 +951,7 @@ nb_status launch_recheck_gw(const unsigned char* X, int64_t ld, int64_t n, const
                             int64_t bin_bytes, int n_bins, int k, const int32_t* model_of,
                             const int32_t* cols, const nb_model* const* models, int n_models,
                             uint8_t* label, float* margin, float* logpost, int want_lp,
-                            int64_t* n_rechecked, cudaStream_t st);
+                            int64_t* n_rechecked, bool counted, cudaStream_t st);
 }  // namespace nbg
 
 extern "C" void nb_groupwise_destroy(nb_groupwise* g) {
@@ -1155,6 +1162,8 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   a.want_lp = g->want_lp;
   a.recheck = g->recheck;
   a.status = g->status;
+  const bool counted = n_rechecked != nullptr && g->recheck != NB_RECHECK_OFF;
+  a.marks = counted ? reinterpret_cast<unsigned long long*>(n_rechecked) : nullptr;
   if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gw, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(k_score_gw)");
@@ -1172,7 +1181,7 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   return launch_recheck_gw(static_cast<const unsigned char*>(X), ld, n, sizes, g->bin_bytes,
                            g->n_bins, g->k, g->model_of, g->cols, g->models.data(), g->n_models,
                            label, margin, g->want_lp ? logpost : nullptr, g->want_lp, n_rechecked,
-                           st);
+                           counted, st);
 }
 
 extern "C" nb_status nb_groupwise_classify(nb_groupwise* g, const void* X, int64_t ld,

@@ -175,6 +175,23 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
                           const nb_aux* aux, const ScoreOut& o, cudaStream_t st);
 
 int num_sms();
+
+// Launch k with programmatic stream serialisation (see pdl_wait()).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
 // process-wide count of kernels this library has launched
 void count_launch();
 

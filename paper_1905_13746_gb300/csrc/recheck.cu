@@ -123,6 +123,7 @@ struct RArgs {
 __global__ void __launch_bounds__(256) k_recheck(const RArgs a) {
   __shared__ double s_sh[8][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  pdl_wait();   // the scorer's labels and mark count
   if (a.counted && *a.n_rechecked == 0ull) return;   // the scorer marked no row
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   unsigned long long cnt = 0;
@@ -163,8 +164,9 @@ nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t 
   const int64_t chunks = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   count_launch();
-  k_recheck<<<(unsigned)(chunks < cap ? chunks : cap), 256, 0, st>>>(a);
-  NB_TRY_CUDA(cudaGetLastError(), "k_recheck launch");
+  NB_TRY_CUDA(launch_pdl(k_recheck, dim3((unsigned)(chunks < cap ? chunks : cap)), dim3(256), 0,
+                         st, a),
+              "k_recheck launch");
   return NB_OK;
 }
 
@@ -266,12 +268,15 @@ struct RGwArgs {
   float* margin;
   float* logpost;
   int want_lp;
+  int counted;   // *n_rechecked already holds the marked rows (skip when 0, do not add)
   unsigned long long* n_rechecked;
 };
 
 __global__ void __launch_bounds__(256) k_recheck_gw(const RGwArgs a) {
   __shared__ double s_sh[8][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  pdl_wait();   // the scorer's labels and mark count
+  if (a.counted && *a.n_rechecked == 0ull) return;   // the scorer marked no row
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   unsigned long long cnt = 0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < a.n; base += nwarps * 32) {
@@ -304,14 +309,14 @@ __global__ void __launch_bounds__(256) k_recheck_gw(const RGwArgs a) {
       ++cnt;
     }
   }
-  if (lane == 0 && cnt && a.n_rechecked) atomicAdd(a.n_rechecked, cnt);
+  if (lane == 0 && cnt && a.n_rechecked && !a.counted) atomicAdd(a.n_rechecked, cnt);
 }
 
 nb_status launch_recheck_gw(const unsigned char* X, int64_t ld, int64_t n, const int64_t* sizes,
                             int64_t bin_bytes, int n_bins, int k, const int32_t* model_of,
                             const int32_t* cols, const nb_model* const* models, int n_models,
                             uint8_t* label, float* margin, float* logpost, int want_lp,
-                            int64_t* n_rechecked, cudaStream_t st) {
+                            int64_t* n_rechecked, bool counted, cudaStream_t st) {
   if (n == 0) return NB_OK;
   RGwArgs a{};
   a.X = X;
@@ -331,12 +336,14 @@ nb_status launch_recheck_gw(const unsigned char* X, int64_t ld, int64_t n, const
   a.margin = margin;
   a.logpost = logpost;
   a.want_lp = want_lp;
+  a.counted = counted ? 1 : 0;
   a.n_rechecked = reinterpret_cast<unsigned long long*>(n_rechecked);
   const int64_t chunks = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   count_launch();
-  k_recheck_gw<<<(unsigned)(chunks < cap ? chunks : cap), 256, 0, st>>>(a);
-  NB_TRY_CUDA(cudaGetLastError(), "k_recheck_gw launch");
+  NB_TRY_CUDA(launch_pdl(k_recheck_gw, dim3((unsigned)(chunks < cap ? chunks : cap)), dim3(256),
+                         0, st, a),
+              "k_recheck_gw launch");
   return NB_OK;
 }
 
