@@ -634,22 +634,35 @@ __global__ void __launch_bounds__(2 * kFinF) k_fit_finish_c2(
     S = 22 - e;
   }
   const double scale = ldexp(1.0, S);
-  for (int jj = tid; jj < F_pad; jj += NT) {
-    const double d = jj < F ? log_theta[(int64_t)F + jj] - log_theta[jj] : 0.0;
-    const int32_t q = (int32_t)llrint(d * scale);   // |q| <= 2^22
-    delta_q[jj] = q;
-    // balanced base-256 digits q = q2*65536 + q1*256 + q0, each in [-128, 127]
-    const int32_t q0 = ((q + 128) & 255) - 128;
-    const int32_t r1 = (q - q0) >> 8;
-    const int32_t q1 = ((r1 + 128) & 255) - 128;
-    const int32_t q2 = (r1 - q1) >> 8;
-    // u8 vectors hold 16 features; limb L of vector v is slot L * nvec8 + v,
-    // byte (jj % 16) of it
-    const int v = jj >> 4, b = jj & 15;
-    unsigned char* L = reinterpret_cast<unsigned char*>(limbs);
-    L[((size_t)0 * nvec8 + v) * 16 + b] = (unsigned char)(q0 & 255);
-    L[((size_t)1 * nvec8 + v) * 16 + b] = (unsigned char)(q1 & 255);
-    L[((size_t)2 * nvec8 + v) * 16 + b] = (unsigned char)(q2 & 255);
+  // U features per thread at a time: their log theta loads all go out before
+  // the byte stores of the limbs (which may alias them) hold the next ones up
+  constexpr int U = 8;
+  for (int base = 0; base < F_pad; base += U * NT) {
+    double dd[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = base + u * NT + tid;
+      dd[u] = jj < F ? log_theta[(int64_t)F + jj] - log_theta[jj] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = base + u * NT + tid;
+      if (jj >= F_pad) continue;
+      const int32_t q = (int32_t)llrint(dd[u] * scale);   // |q| <= 2^22
+      delta_q[jj] = q;
+      // balanced base-256 digits q = q2*65536 + q1*256 + q0, each in [-128, 127]
+      const int32_t q0 = ((q + 128) & 255) - 128;
+      const int32_t r1 = (q - q0) >> 8;
+      const int32_t q1 = ((r1 + 128) & 255) - 128;
+      const int32_t q2 = (r1 - q1) >> 8;
+      // u8 vectors hold 16 features; limb L of vector v is slot L * nvec8 + v,
+      // byte (jj % 16) of it
+      const int v = jj >> 4, b = jj & 15;
+      unsigned char* L = reinterpret_cast<unsigned char*>(limbs);
+      L[((size_t)0 * nvec8 + v) * 16 + b] = (unsigned char)(q0 & 255);
+      L[((size_t)1 * nvec8 + v) * 16 + b] = (unsigned char)(q1 & 255);
+      L[((size_t)2 * nvec8 + v) * 16 + b] = (unsigned char)(q2 & 255);
+    }
   }
   if (tid < 2) bias[tid] = (float)log_pi[tid];
   if (tid == 0) {

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
     tm[q] = vb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * vb)) - 1u);
   }
   const int tail_v = f.F < nv * EPV ? nv - 1 : -1;
-  uint32_t cnt[2] = {0u, 0u};
+  uint32_t cnt0 = 0u, cnt1 = 0u;   // rows per class (lane 0); scalars, not an array indexed by c
   int since_flush = 0;
   bool dead = false;   // a wait ran out: skip to the common exit (the named barrier)
 
@@ -165,7 +165,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
         continue;
       }
       ++since_flush;
-      if (lane == 0) ++cnt[c];
+      if (lane == 0) {
+        cnt0 += c == 0;
+        cnt1 += c == 1;
+      }
       const unsigned char* rp = st + (size_t)rr * f.ld_bytes;
       const int8_t ex = (DT == NB_FP8E4M3 && f.row_exp) ? f.row_exp[m.row0 + rr] : (int8_t)0;
 #pragma unroll
@@ -239,8 +242,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
   }
   fit2_flush<DT, KV, NA, EPV>(acc, hist, f.F, f.F_pad, lane, nv);
   if (lane == 0) {
-    if (cnt[0]) atomicAdd(&ncount[0], cnt[0]);
-    if (cnt[1]) atomicAdd(&ncount[1], cnt[1]);
+    if (cnt0) atomicAdd(&ncount[0], cnt0);
+    if (cnt1) atomicAdd(&ncount[1], cnt1);
   }
   // consumer warps only (the producer has left): named barrier 1
   asm volatile("bar.sync 1, %0;" ::"r"(NCW * 32) : "memory");
