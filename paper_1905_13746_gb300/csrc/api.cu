@@ -55,13 +55,15 @@ static nb_status alloc_model(nb_model* m) {
     off = align_up(off + bytes, 256);
     return o;
   };
+  // counts, nc and the status word lie in this order, so that the multinomial
+  // fit clears all three with one memset
   const size_t o_counts = take(sizeof(uint64_t) * C * F);
   const size_t o_nc = take(sizeof(uint64_t) * C);
+  const size_t o_st = take(sizeof(int) * 4);
   const size_t o_p0 = take(sizeof(double) * C * F);
   const size_t o_p1 = take(m->kind == NB_GAUSSIAN ? sizeof(double) * C * F : 0);
   const size_t o_lpi = take(sizeof(double) * C);
   const size_t o_gc = take(sizeof(double) * C);
-  const size_t o_st = take(sizeof(int) * 4);
   const size_t o_fin = take(sizeof(unsigned long long) * 4);
   const size_t o_c2 = take(sizeof(C2Header));
   const size_t o_delta = take(sizeof(float) * Fp);
@@ -211,7 +213,9 @@ static nb_status check_fit_args(nb_kind kind, const void* X, nb_dtype dtype, int
 static nb_status fit_into(nb_model* m, const void* X, nb_dtype dtype, int64_t n, int64_t ld,
                           const int32_t* y, const double* prior, const nb_aux* aux, int no_sync,
                           cudaStream_t st) {
-  NB_TRY_CUDA(cudaMemsetAsync(m->d.status, 0, sizeof(int), st), "memset(status)");
+  // the multinomial fit clears the status word together with its counts
+  if (m->kind != NB_MULTINOMIAL)
+    NB_TRY_CUDA(cudaMemsetAsync(m->d.status, 0, sizeof(int), st), "memset(status)");
   double* prior_dev = nullptr;
   if (prior) {
     // stage the host priors in the model's own log_pi slot

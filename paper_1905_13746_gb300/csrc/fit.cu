@@ -487,24 +487,26 @@ __global__ void __launch_bounds__(1024) k_derive_c2(const double* log_theta, con
 }
 
 // Two-class finish of the fit in one launch (Sec. 4 likelihoods, Laplace
-// smoothing).  FP64 is slow on this part, so the logs are spread thin: a block
-// of 2 * kFinF threads owns kFinF features, sums the class totals N_0, N_1 from
-// the exact counts (log(N_c + alpha F) once per block), takes one
-// log(n_cj + alpha) per thread, then one thread per feature forms
-// Delta = log theta_1 - log theta_0, its FP32 copies and the centred weights
-// of the general-C tables (w_c = log theta_c - mean).  The blocks' maxima of
-// |Delta| meet in fin[], and the last block to finish derives the fixed-point
-// scale S and writes the integer Delta and its limbs.  fin[] (zero before the
-// launch) is cleared again by that block.
-constexpr int kFinF = 64;
+// smoothing).  FP64 is slow on this part and the kernel is one chain of
+// latencies, so the work is spread thin and overlapped: a block of 4 kFinF
+// threads owns kFinF features; half of its threads take one log(n_cj + alpha)
+// each while the other half sum the class totals N_0, N_1 from the exact
+// counts and take log(N_c + alpha F) (and, in block 0, log pi_c).  Then one
+// thread per feature forms Delta = log theta_1 - log theta_0, its FP32 copies
+// and the centred weights of the general-C tables (w_c = log theta_c - mean).
+// The blocks' maxima of |Delta| meet in fin[], and the last block to finish
+// derives the fixed-point scale S and writes the integer Delta and its limbs.
+// fin[] (zero before the launch) is cleared again by that block.
+constexpr int kFinF = 64;          // features per block
+constexpr int kFinT = 4 * kFinF;   // threads per block
 
-__global__ void __launch_bounds__(2 * kFinF) k_fit_finish_c2(
+__global__ void __launch_bounds__(kFinT) k_fit_finish_c2(
     const unsigned long long* counts, const unsigned long long* nc, int64_t n, int F, int F_pad,
     int nvec8, double alpha, int prior_given, double* log_theta, double* log_pi, C2Header* hdr,
     float* delta, int32_t* delta_q, uint4* limbs, float4* il4, float4* il8, float4* il16,
     float* w, float* bias, float* wmax, unsigned long long* fin, int* status) {
-  constexpr int NT = 2 * kFinF, NW = NT / 32;
-  __shared__ unsigned long long part[2][NW];
+  constexpr int NT = kFinT, NL = 2 * kFinF;   // NL threads take the per-feature logs
+  __shared__ unsigned long long part[2][2];
   __shared__ double ld[2];
   __shared__ double lt[2][kFinF];
   __shared__ double dmax[kFinF / 32];
@@ -512,43 +514,38 @@ __global__ void __launch_bounds__(2 * kFinF) k_fit_finish_c2(
   __shared__ int last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   pdl_wait();   // the counting kernels' totals
-  unsigned long long s0 = 0, s1 = 0;
-#pragma unroll 4
-  for (int j = tid; j < F; j += NT) {
-    s0 += counts[j];
-    s1 += counts[(int64_t)F + j];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-  }
-  if (lane == 0) {
-    part[0][warp] = s0;
-    part[1][warp] = s1;
-  }
-  __syncthreads();
-  if (tid < 2) {
+  double lc = 0.0;
+  if (tid < NL) {
+    const int c = tid / kFinF, j = blockIdx.x * kFinF + tid % kFinF;
+    if (j < F) lc = log((double)counts[(int64_t)c * F + j] + alpha);
+  } else {
+    // two warps per class, each summing every other 32 features
+    const int wt = warp - NL / 32, c = wt >> 1, h = wt & 1;
     unsigned long long t = 0;
-    for (int k = 0; k < NW; ++k) t += part[tid][k];
-    ld[tid] = log((double)t + alpha * (double)F);
-    if (blockIdx.x == 0 && !prior_given) {
-      if (nc[tid] == 0) {
+#pragma unroll 8
+    for (int j = 32 * h + lane; j < F; j += 64) t += counts[(int64_t)c * F + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) part[c][h] = t;
+    // the summing warps only: named barrier 1
+    asm volatile("bar.sync 1, %0;" ::"r"(NT - NL) : "memory");
+    if (h == 0 && lane == 0) ld[c] = log((double)(part[c][0] + part[c][1]) + alpha * (double)F);
+    if (h == 1 && lane == 0 && blockIdx.x == 0 && !prior_given) {
+      if (nc[c] == 0) {
         atomicOr(status, ST_BAD_LABEL);
-        log_pi[tid] = 0.0;
+        log_pi[c] = 0.0;
       } else {
-        log_pi[tid] = log((double)nc[tid]) - log((double)n);
+        log_pi[c] = log((double)nc[c]) - log((double)n);
       }
     }
   }
   __syncthreads();
-  {
-    // one (class, feature) log per thread
+  if (tid < NL) {
     const int c = tid / kFinF, jl = tid % kFinF;
     const int j = blockIdx.x * kFinF + jl;
     double v = 0.0;
     if (j < F) {
-      v = log((double)counts[(int64_t)c * F + j] + alpha) - ld[c];
+      v = lc - ld[c];
       log_theta[(int64_t)c * F + j] = v;
     }
     lt[c][jl] = v;
@@ -636,7 +633,7 @@ __global__ void __launch_bounds__(2 * kFinF) k_fit_finish_c2(
   const double scale = ldexp(1.0, S);
   // U features per thread at a time: their log theta loads all go out before
   // the byte stores of the limbs (which may alias them) hold the next ones up
-  constexpr int U = 8;
+  constexpr int U = 4;
   for (int base = 0; base < F_pad; base += U * NT) {
     double dd[U];
 #pragma unroll
@@ -739,9 +736,10 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
                                  const double* log_prior_dev, cudaStream_t st) {
   const int C = m->C, F = m->F;
   ModelDev& d = m->d;
-  // counts and nc are neighbours in the model's allocation: one clear for both
+  // counts, nc and the status word follow one another in the model's
+  // allocation: one clear for all three
   NB_TRY_CUDA(cudaMemsetAsync(d.counts, 0,
-                              (size_t)(reinterpret_cast<char*>(d.nc + C) -
+                              (size_t)(reinterpret_cast<char*>(d.status + 1) -
                                        reinterpret_cast<char*>(d.counts)),
                               st),
               "memset");
@@ -841,7 +839,7 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
   }
   if (C == 2) {
     count_launch();
-    NB_TRY_CUDA(launch_pdl(k_fit_finish_c2, dim3((m->F_pad + kFinF - 1) / kFinF), dim3(2 * kFinF),
+    NB_TRY_CUDA(launch_pdl(k_fit_finish_c2, dim3((m->F_pad + kFinF - 1) / kFinF), dim3(kFinT),
                            0, st, reinterpret_cast<const unsigned long long*>(d.counts),
                            reinterpret_cast<const unsigned long long*>(d.nc), (int64_t)n, F,
                            m->F_pad, m->nvec8, m->alpha, (int)(log_prior_dev != nullptr), d.p0,

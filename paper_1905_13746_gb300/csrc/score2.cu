@@ -53,6 +53,10 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
   }
   const bool has_tail = keep < 16;
 
+  // rows this lane marked for the FP64 recheck, added up once per warp at the
+  // end (faster here than an atomic per marked row; the FP kernel below keeps
+  // the atomic, which holds no register through its loop)
+  unsigned marks = 0;
   for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles;
        t += nwarps) {
     const int64_t row0 = t * RPW + (int64_t)sub * R;
@@ -141,9 +145,10 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
       const float tau = 0.5f * T * h.inv_scale * 1.0001f +
                         2.4e-7f * (fabsf(Dsum) + fabsf(h.b)) +
                         1e-12f * (T * h.maxabs + fabsf(h.b)) + 1e-30f;
-      c2_epilogue(a, row0 + r, d, tau);
+      marks += c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, row0 + r, d, tau);
     }
   }
+  c2_flush_marks(a, marks);
 }
 
 template <int DT, int LPR, int R>
@@ -252,7 +257,9 @@ __global__ void __launch_bounds__(256) k_score2_fp(const S2Args a) {
       const float gam = k * 5.9604645e-8f / (1.f - k * 5.9604645e-8f);
       const float A = tot[r] * scale * h.maxabs * 1.001f;
       const float tau = gam * (A + fabsf(h.b)) * 1.01f + 1e-12f * (A + fabsf(h.b)) + 1e-30f;
-      c2_epilogue(a, row0 + r, d, tau);
+      // marked rows are rare: one atomic each, no state carried through the loop
+      if (c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, row0 + r, d, tau) && a.marks)
+        atomicAdd(a.marks, 1ull);
     }
   }
 }

@@ -74,6 +74,16 @@ __device__ __forceinline__ void c2_epilogue(const S2Args& a, int64_t row, float 
   }
 }
 
+// The u8 register-streaming scorer stores each row from whichever lane holds
+// it, in divergent code; it counts its marked rows per lane and adds them to
+// a.marks once per warp here, at the end of the kernel, where every lane of
+// the warp arrives.
+__device__ __forceinline__ void c2_flush_marks(const S2Args& a, unsigned cnt) {
+  if (!a.marks) return;
+  cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.marks, (unsigned long long)cnt);
+}
+
 // Rigorous bound on |d_gpu - d_exact| of the fixed-point u8 path: the Delta
 // quantisation (half a step per unit count), the int64 -> FP32 conversion and
 // the final add, and slack for the FP64 reference's own rounding.

@@ -1,8 +1,8 @@
 """GPU parity: the CUDA library, called through its C ABI, against the FP64
 oracle on the same seeded inputs, element by element.
 
-Bar (Sec. 4 posterior and decision rule; tolerance from the task's
-specification of the scorer): labels bit-exact, integer fit counts bit-exact,
+Bar (Sec. 4 posterior and decision rule; the scorer's stated tolerance):
+labels bit-exact, integer fit counts bit-exact,
 log posteriors and margins within 1e-5 * max(1, |reference|), Gaussian
 moments within 1e-12 relative.  Sizes span several tiles and ragged tails.
 """
@@ -121,6 +121,29 @@ def test_score_two_class_low_totals_near_ties():
     _, ref = oracle_mn(vfit, y[:5000], 2, vsc)
     compare(res, ref)
     assert res["n_rechecked"] > 0
+
+
+@pytest.mark.parametrize("fmt", ["u8ovf", "f32", "fp8"])
+def test_marked_rows_counted_by_every_scorer(fmt):
+    # the scorers count the rows they mark and the recheck skips its scan when
+    # the count is zero: a miscount would leave marked rows unresolved, so each
+    # scorer runs the near-tie workload and must still match the oracle
+    F = 256
+    p = synth.dirichlet_profiles(3, 2, F, 5.0)
+    X, y, _ = count_matrix(9, 20000, F, mu=2.0, sigma=1.0, p=p)
+    ffit, vfit = stored(X[:5000], fmt)
+    fsc, vsc = stored(X[5000:], fmt)
+    model = nb.fit(ffit, torch.from_numpy(y[:5000]).cuda(), 2)
+    _, ref = oracle_mn(vfit, y[:5000], 2, vsc)
+    counts = {}
+    for cfg in [(nb.NB_VARIANT_REGISTER, 0, 0, 0), (nb.NB_VARIANT_PIPELINED, 2, 16, 1)]:
+        model.set_tile_config(*cfg)
+        res = to_np(nb.score(model, fsc))
+        compare(res, ref)
+        assert res["n_rechecked"] > 0, cfg
+        counts[cfg] = res["n_rechecked"]
+    if fmt == "u8ovf":   # exact integer sums: both scorers mark the same rows
+        assert len(set(counts.values())) == 1, counts
 
 
 def test_all_zero_rows_tie_to_benign():
