@@ -14,6 +14,10 @@
 // block; FP32 / BF16 / FP8 counts (below 2^24) flush their 32-bit lane sums
 // every 255 rows into a 64-bit block histogram.  Integer sums are exact in
 // any order.
+//
+// The overflow list of u8 storage (counts above 255) is not staged with the
+// rows: a second, short kernel (k_fit2_ovf) adds its entries to the counts,
+// so that the row pipeline streams plain u8 rows.
 #include <type_traits>
 
 #include "pipe.cuh"
@@ -29,9 +33,6 @@ struct Fit2Args {
   int F_pad;
   int nvec_row;
   const int32_t* y;
-  const int64_t* ovf_ptr;
-  const uint16_t* ovf_col;
-  const uint16_t* ovf_add;
   const int8_t* row_exp;
   unsigned long long* counts;   // 2 x F
   unsigned long long* nc;       // 2
@@ -111,8 +112,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
   __syncthreads();
 
   if (warp == NCW) {
-    const PipeSrc src{f.X, f.ld_bytes, f.n, f.ovf_ptr, f.ovf_col, f.ovf_add, f.y, nullptr,
-                      f.status};
+    const PipeSrc src{f.X, f.ld_bytes, f.n, nullptr, nullptr, nullptr, f.y, nullptr, f.status};
     pipe_produce(src, p, sm, full, empty, &tabbar, t0, ntl);
     return;
   }
@@ -155,9 +155,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
     const unsigned char* st = sm + p.stages_off + (size_t)s * p.stage_bytes;
     const StageMeta m = *reinterpret_cast<const StageMeta*>(st + p.meta_off);
     const int32_t* sy = reinterpret_cast<const int32_t*>(st + p.y_off);
-    const long long* sp = reinterpret_cast<const long long*>(st + p.ptr_off);
-    const uint16_t* scol = reinterpret_cast<const uint16_t*>(st + p.col_off);
-    const uint16_t* sadd = reinterpret_cast<const uint16_t*>(st + p.add_off);
     for (int rr = warp; rr < m.nr; rr += NCW) {
       const int c = sy[rr];
       if (c < 0 || c > 1) {
@@ -219,17 +216,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
           }
         }
       }
-      if (f.ovf_ptr) {
-        const long long k0 = sp[rr], k1 = sp[rr + 1];
-        for (long long e = k0 + lane; e < k1; e += 32) {
-          const uint32_t col = m.in_smem ? scol[e - m.ebase] : f.ovf_col[e];
-          const uint32_t add = m.in_smem ? sadd[e - m.ebase] : f.ovf_add[e];
-          if (col < (uint32_t)f.F)
-            atomicAdd(&hist[c * f.F_pad + col], (Fit2Hist<DT>)add);
-          else
-            atomicOr(f.status, ST_OVF_RANGE);
-        }
-      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -254,6 +240,85 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
   }
   if (threadIdx.x < 2 && ncount[threadIdx.x])
     atomicAdd(&f.nc[threadIdx.x], (unsigned long long)ncount[threadIdx.x]);
+}
+
+// Overflow entries of u8 rows (Sec. 4 counts; the part of each count above
+// 255), after the row pipeline.  A warp takes 32 rows and walks their entries
+// as one contiguous range (coalesced loads, 32 entries per pass); the row of
+// an entry is the last of the 32 row pointers at or below it, found by a
+// five-step search over the pointers held one per lane.  Entries go to 32-bit
+// (class, column) bins in shared memory, and the bins to the uint64 counts
+// once per block.  Rows labelled outside {0, 1} were flagged by the row kernel
+// and are skipped.  A bin takes at most 65,535 per row and a block at most
+// kFit2BlockRows rows, so 32 bits do not overflow.
+constexpr int kOvfThreads = 512;
+
+__global__ void __launch_bounds__(kOvfThreads) k_fit2_ovf(const int64_t* ptr, const uint16_t* col,
+                                                          const uint16_t* add, const int32_t* y,
+                                                          int64_t n, int F,
+                                                          unsigned long long* counts, int* status) {
+  extern __shared__ unsigned int bins[];   // [2][F]
+  for (int k = threadIdx.x; k < 2 * F; k += blockDim.x) bins[k] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunk = (n + 31) / 32;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunk;
+       ch += wstride) {
+    const int64_t r0 = ch * 32;
+    const int nr = (int)min((int64_t)32, n - r0);
+    // lane l holds the first entry of row r0 + l (lanes past the last row: the end)
+    const int64_t pl = ptr[r0 + (lane < nr ? lane : nr)];
+    const int64_t pend = ptr[r0 + nr];
+    const int yl = lane < nr ? y[r0 + lane] : -1;
+    const int64_t e0 = __shfl_sync(0xFFFFFFFFu, pl, 0);
+    for (int64_t base = e0; base < pend; base += 32) {
+      const int64_t e = base + lane;
+      const bool valid = e < pend;
+      uint32_t j = 0u, a = 0u;
+      if (valid) {
+        j = col[e];
+        a = add[e];
+      }
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t v = __shfl_sync(0xFFFFFFFFu, pl, lo + step);
+        if (v <= e) lo += step;
+      }
+      const int c = __shfl_sync(0xFFFFFFFFu, yl, lo);
+      if (valid && (c == 0 || c == 1)) {
+        if (j < (uint32_t)F)
+          atomicAdd(&bins[c * F + j], a);
+        else
+          atomicOr(status, ST_OVF_RANGE);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * F; k += blockDim.x)
+    if (bins[k]) atomicAdd(&counts[k], (unsigned long long)bins[k]);
+}
+
+static nb_status launch_fit2_ovf(nb_model* m, const nb_aux* aux, const int32_t* y, int64_t n,
+                                 cudaStream_t st) {
+  const int F = m->F;
+  const int smem = (int)(2 * sizeof(unsigned int) * (size_t)F);   // F <= 8,192 here
+  if (smem > kSmemOptIn)   // per device and function: set at every launch
+    NB_TRY_CUDA(cudaFuncSetAttribute(k_fit2_ovf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                "cudaFuncSetAttribute(k_fit2_ovf)");
+  // 32 rows per warp pass, four blocks per SM; at most kFit2BlockRows rows per block
+  const long long rows_per_block = 32LL * (kOvfThreads / 32);
+  long long blocks = (n + rows_per_block - 1) / rows_per_block;
+  const long long cap = (long long)num_sms() * 4;
+  if (blocks > cap) blocks = cap;
+  if (blocks < (n + kFit2BlockRows - 1) / kFit2BlockRows) blocks = (n + kFit2BlockRows - 1) / kFit2BlockRows;
+  count_launch();
+  k_fit2_ovf<<<(unsigned)blocks, kOvfThreads, smem, st>>>(aux->ovf_ptr, aux->ovf_col, aux->ovf_add, y, n,
+                                                  F, reinterpret_cast<unsigned long long*>(m->d.counts),
+                                                  m->d.status);
+  NB_TRY_CUDA(cudaGetLastError(), "k_fit2_ovf launch");
+  return NB_OK;
 }
 
 template <int DT, int KV, int kFitNCW>
@@ -290,9 +355,6 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
   f.F_pad = m->F_pad;
   f.nvec_row = (m->F * es + 15) / 16;
   f.y = y;
-  f.ovf_ptr = aux ? aux->ovf_ptr : nullptr;
-  f.ovf_col = aux ? aux->ovf_col : nullptr;
-  f.ovf_add = aux ? aux->ovf_add : nullptr;
   f.row_exp = aux ? aux->row_exp : nullptr;
   f.counts = reinterpret_cast<unsigned long long*>(m->d.counts);
   f.nc = reinterpret_cast<unsigned long long*>(m->d.nc);
@@ -301,8 +363,6 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
   const int kv = (f.nvec_row + 31) / 32;
   const int kv_max = dt == NB_F32 ? 8 : (dt == NB_FP8E4M3 ? 2 : 4);
   if (!aligned || kv > kv_max || f.ld_bytes > 8192) return NB_EUNSUPPORTED;
-  const bool side_ok = !f.ovf_ptr || ((reinterpret_cast<uintptr_t>(f.ovf_col) & 15) == 0 &&
-                                      (reinterpret_cast<uintptr_t>(f.ovf_add) & 15) == 0);
   // eight consumer warps and two blocks per SM for u8 rows of <= 64 vectors
   const int ncw = (dt == NB_U8 && kv <= 2) ? 8 : 12;
   // eight consumers (two blocks per SM): two stages of up to 48 rows (~48 KB);
@@ -313,15 +373,17 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
   if (f.ld_bytes >= 2048 && rs < ncw) rs = ncw;
   PipeArgs p{};
   const uint32_t hist_bytes = (uint32_t)((dt == NB_U8 || dt == NB_U16 ? 8 : 16) * m->F_pad);
-  pipe_layout(p, rs, 4, f.ld_bytes, side_ok, true, hist_bytes, n);
+  pipe_layout(p, rs, 4, f.ld_bytes, false, true, hist_bytes, n);
   int S = ncw == 8 ? 2 : 4;
   while (S > 2 && p.stages_off + (uint32_t)S * p.stage_bytes > 220u * 1024u) --S;
-  pipe_layout(p, rs, S, f.ld_bytes, side_ok, true, hist_bytes, n);
+  pipe_layout(p, rs, S, f.ld_bytes, false, true, hist_bytes, n);
   const int smem = (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
   if (smem > 220 * 1024) return NB_EUNSUPPORTED;
+  nb_status s = NB_EUNSUPPORTED;
 #define NB_FIT2_CASE(D, K)                                                \
   if (dt == D && kv == K)                                                 \
-    return ncw == 8 ? run_fit2<D, K, 8>(f, p, smem, st) : run_fit2<D, K, 12>(f, p, smem, st);
+    s = ncw == 8 ? run_fit2<D, K, 8>(f, p, smem, st) : run_fit2<D, K, 12>(f, p, smem, st); \
+  else
   NB_FIT2_CASE(NB_U8, 1) NB_FIT2_CASE(NB_U8, 2) NB_FIT2_CASE(NB_U8, 3) NB_FIT2_CASE(NB_U8, 4)
   NB_FIT2_CASE(NB_U16, 1) NB_FIT2_CASE(NB_U16, 2) NB_FIT2_CASE(NB_U16, 3)
   NB_FIT2_CASE(NB_U16, 4)
@@ -330,8 +392,11 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
   NB_FIT2_CASE(NB_F32, 1) NB_FIT2_CASE(NB_F32, 2) NB_FIT2_CASE(NB_F32, 3) NB_FIT2_CASE(NB_F32, 4)
   NB_FIT2_CASE(NB_F32, 5) NB_FIT2_CASE(NB_F32, 6) NB_FIT2_CASE(NB_F32, 7) NB_FIT2_CASE(NB_F32, 8)
   NB_FIT2_CASE(NB_FP8E4M3, 1) NB_FIT2_CASE(NB_FP8E4M3, 2)
+  {}
 #undef NB_FIT2_CASE
-  return NB_EUNSUPPORTED;
+  if (s != NB_OK) return s;
+  if (dt == NB_U8 && aux && aux->ovf_ptr) return launch_fit2_ovf(m, aux, y, n, st);
+  return NB_OK;
 }
 
 }  // namespace nbg

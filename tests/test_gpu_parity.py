@@ -282,6 +282,18 @@ def test_unaligned_leading_dimension_takes_general_path():
     compare(r, ref)
 
 
+def test_overflow_column_outside_F_rejected():
+    # an overflow entry naming a column outside [0, F) is skipped by every
+    # kernel that reads the list and reported as invalid input by the fit
+    X, y, _ = count_matrix(722, 2000, 64)
+    f, _ = stored(X, "u8ovf")
+    assert f.ovf_col.numel() > 0
+    f.ovf_col[0] = 64 + 5
+    with pytest.raises(nb.NbError) as ei:
+        nb.fit(f, torch.from_numpy(y).cuda(), 2)
+    assert ei.value.status == nb.NB_EINVAL
+
+
 def test_invalid_inputs_rejected():
     X, y, _ = count_matrix(720, 500, 16)
     f, _ = stored(X, "u16")
