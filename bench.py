@@ -313,6 +313,7 @@ def run_fsweep(args, device):
                          chunk_rows=max(1024, (1 << 27) // F))
         y_dev = torch.as_tensor(y, device=device)
         ntr = N // 3
+        torch.cuda.synchronize()   # inputs made on the default stream, used on `stream`
         with torch.cuda.stream(stream):
             m = nb.fit(nb.Features(X[:ntr], nb.NB_U8), y_dev[:ntr], 2, stream=stream)
         stream.synchronize()
@@ -326,9 +327,11 @@ def run_fsweep(args, device):
         u8_ms, u8_re = _time_score(m, fu8, stream)
         tuned = list(m.tile_config())
         m.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
-        f8 = nb.pack_fp8(X.to(torch.float32) if N * F * 4 <= (16 << 30) else
-                         X.to(torch.int32).to(torch.uint16), stream=stream)
+        src = X.to(torch.float32) if N * F * 4 <= (16 << 30) else X.to(torch.int32).to(torch.uint16)
+        torch.cuda.synchronize()   # the conversion ran on the default stream
+        f8 = nb.pack_fp8(src, stream=stream)
         stream.synchronize()
+        del src
         # FP32 accumulation: labels guaranteed (label-mode recheck); the rows a
         # log-posterior guarantee would send to FP64 are counted separately.
         # Each storage type gets its own shape: the autotuned pipelined shape
@@ -355,6 +358,7 @@ def run_fsweep(args, device):
         del f8
         n32 = min(N, (48 << 30) // (4 * F))
         f32 = nb.Features(X[:n32].to(torch.float32), nb.NB_F32)
+        torch.cuda.synchronize()
         f32_ms, f32_re, tc32 = best_for(f32)
         _, f32_lp = _time_score(m, f32, stream, reps=1, warm=0)
         m.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
@@ -394,6 +398,7 @@ def run_gaussian(args, device, reps=200):
     Xf = torch.from_numpy(w["X_fit"]).to(device)
     yf = torch.from_numpy(w["y_fit"]).to(device)
     Xs = torch.from_numpy(w["X_score"]).to(device)
+    torch.cuda.synchronize()   # inputs made on the default stream, used on `stream`
     stream = torch.cuda.Stream(device)
     with torch.cuda.stream(stream):
         m = nb.fit(nb.Features(Xf, nb.NB_F32), yf, 2, kind=nb.NB_GAUSSIAN,
@@ -448,6 +453,7 @@ def run_groupwise(args, device, reps=20, warm=3):
     ytr = torch.from_numpy(y[:n_tr]).to(device)
     s_tr = torch.from_numpy(s[:n_tr]).to(device)
     s_te = torch.from_numpy(s[n_tr:]).to(device)
+    torch.cuda.synchronize()   # inputs made on the default stream, used on `stream`
     stream = torch.cuda.Stream(device)
     rows = []
     ks = [int(v) for v in args.gw_k.split(",")] if args.gw_k else list(GW_KS)
@@ -692,6 +698,7 @@ def run_many_class(args, device):
     y_dev = torch.as_tensor(y, device=device)
     y_tr = y_dev.index_select(0, tr_dev).contiguous()
     ftr, fall = nb.Features(Xtr, nb.NB_U8), nb.Features(X, nb.NB_U8)
+    torch.cuda.synchronize()   # inputs made on the default stream, used on `stream`
     stream = torch.cuda.Stream(device)
     with torch.cuda.stream(stream):
         model = nb.fit(ftr, y_tr, C, stream=stream)
@@ -737,6 +744,7 @@ def run_many_class(args, device):
     cc_rechecked = int(osub["n_rechecked"].item())
     model.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
     f32 = nb.Features(X[:sub].to(torch.float32), nb.NB_F32)
+    torch.cuda.synchronize()
     f32_sub = time_score(f32, osub)
     del f32
     line = {
@@ -959,6 +967,7 @@ def main():
     # ---- plain FP32 step on the same data ---------------------------------
     f32_all = nb.Features(W["X16"].to(torch.int32).to(torch.float32), nb.NB_F32)
     f32_tr = nb.Features(W["X16_tr"].to(torch.int32).to(torch.float32), nb.NB_F32)
+    torch.cuda.synchronize()   # the conversions ran on the default stream
     with torch.cuda.stream(stream):
         m32 = nb.fit(f32_tr, W["y_tr"], C, stream=stream)
     stream.synchronize()

@@ -271,6 +271,24 @@ class Features:
         return b
 
 
+def _labels(y, n):
+    """Labels as the library reads them: n int32 values, contiguous."""
+    import torch
+    if not isinstance(y, torch.Tensor) or y.dtype != torch.int32 or y.dim() != 1 \
+            or not y.is_contiguous() or y.shape[0] != n:
+        raise TypeError("labels must be a contiguous 1-D int32 tensor of %d entries" % n)
+    return y
+
+
+def _sizes(s, n):
+    """File sizes as the library reads them: n int64 values, contiguous."""
+    import torch
+    if not isinstance(s, torch.Tensor) or s.dtype != torch.int64 or s.dim() != 1 \
+            or not s.is_contiguous() or s.shape[0] != n:
+        raise TypeError("sizes must be a contiguous 1-D int64 tensor of %d entries" % n)
+    return s
+
+
 def as_features(X):
     return X if isinstance(X, Features) else Features(X)
 
@@ -334,7 +352,8 @@ class Model:
 def fit(X, y, C, kind=NB_MULTINOMIAL, alpha=1.0, log_prior=None, var_smoothing=1e-9,
         no_sync=False, stream=None):
     Xf = as_features(X)
-    h = nb_fit(kind, Xf.data.data_ptr(), Xf.dtype_code, Xf.n, Xf.F, Xf.ld, y.data_ptr(), C,
+    h = nb_fit(kind, Xf.data.data_ptr(), Xf.dtype_code, Xf.n, Xf.F, Xf.ld,
+               _labels(y, Xf.n).data_ptr(), C,
                alpha=alpha, log_prior=log_prior, var_smoothing=var_smoothing, aux=Xf.aux(),
                no_sync=no_sync, stream=stream)
     return Model(h, kind, C, Xf.F)
@@ -343,7 +362,8 @@ def fit(X, y, C, kind=NB_MULTINOMIAL, alpha=1.0, log_prior=None, var_smoothing=1
 def refit(model, X, y, alpha=1.0, log_prior=None, var_smoothing=1e-9, no_sync=False,
           stream=None):
     Xf = as_features(X)
-    nb_refit(model.handle, Xf.data.data_ptr(), Xf.dtype_code, Xf.n, Xf.ld, y.data_ptr(),
+    nb_refit(model.handle, Xf.data.data_ptr(), Xf.dtype_code, Xf.n, Xf.ld,
+             _labels(y, Xf.n).data_ptr(),
              alpha=alpha, log_prior=log_prior, var_smoothing=var_smoothing, aux=Xf.aux(),
              no_sync=no_sync, stream=stream)
     return model
@@ -596,6 +616,9 @@ def route(sizes, bin_bytes=BIN_BYTES, n_bins=N_BINS, model_of=None, n_groups=Non
     import torch
     dev = sizes.device
     n = sizes.shape[0]
+    _sizes(sizes, n)
+    if y is not None:
+        _labels(y, n)
     G = int(n_groups) if n_groups is not None else n_bins
     ws = int(lib().nb_route_workspace(n, G))
     work = torch.empty(max(ws, 8), dtype=torch.uint8, device=dev)

@@ -97,3 +97,20 @@ def test_groupwise_arguments_rejected_before_any_device_work():
                          None) == nb.NB_EINVAL
     assert lib.nb_select_features(None, 0, 1, 0, None, None) == nb.NB_EINVAL
     assert lib.nb_route_workspace(10000, 100) >= 100 * 8
+
+
+def test_label_and_size_tensors_checked_before_the_call():
+    # the library reads labels as int32 and sizes as int64: any other tensor
+    # is refused in the binding instead of being misread
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    nb._labels(torch.zeros(4, dtype=torch.int32), 4)
+    for bad in (torch.zeros(4, dtype=torch.int64), torch.zeros(5, dtype=torch.int32),
+                torch.zeros((2, 2), dtype=torch.int32), torch.zeros(8, dtype=torch.int32)[::2]):
+        with pytest.raises(TypeError):
+            nb._labels(bad, 4)
+    nb._sizes(torch.zeros(3, dtype=torch.int64), 3)
+    for bad in (torch.zeros(3, dtype=torch.int32), torch.zeros(2, dtype=torch.int64)):
+        with pytest.raises(TypeError):
+            nb._sizes(bad, 3)
