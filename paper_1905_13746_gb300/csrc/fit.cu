@@ -370,27 +370,34 @@ __global__ void k_counts_ovf(const int64_t* ptr, const uint16_t* col, const uint
 }
 
 // ---------------------------------------------------------------------------
-// FP64 finalize: one block per class
+// FP64 finalize of the general-C tables
 // ---------------------------------------------------------------------------
-__global__ void k_finalize_mn(const unsigned long long* counts, const unsigned long long* nc,
-                              int64_t n, int F, double alpha, int prior_given, double* log_theta,
-                              double* log_pi, int* status) {
-  const int c = blockIdx.x;
-  __shared__ unsigned long long part[256];
+// General-C finish (Sec. 4 likelihoods, Laplace smoothing): block (c, t)
+// writes log theta_cj for the kFinTile features of tile t.  Every block sums
+// the class total N_c from the exact counts (they sit in L2) and one thread
+// takes log(N_c + alpha F): FP64 is slow on this part, so the per-feature
+// logs are spread over C * F / kFinTile blocks rather than C.
+constexpr int kFinTile = 512;
+
+__global__ void __launch_bounds__(256) k_finalize_mn(const unsigned long long* counts,
+                                                     const unsigned long long* nc, int64_t n,
+                                                     int F, double alpha, int prior_given,
+                                                     double* log_theta, double* log_pi,
+                                                     int* status) {
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ unsigned long long part[8];
+  __shared__ double log_den;
   unsigned long long s = 0;
-  for (int j = threadIdx.x; j < F; j += blockDim.x) s += counts[(int64_t)c * F + j];
-  part[threadIdx.x] = s;
+  for (int j = tid; j < F; j += blockDim.x) s += counts[(int64_t)c * F + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) part[warp] = s;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double Nc = (double)part[0];
-  const double log_den = log(Nc + alpha * (double)F);
-  for (int j = threadIdx.x; j < F; j += blockDim.x)
-    log_theta[(int64_t)c * F + j] = log((double)counts[(int64_t)c * F + j] + alpha) - log_den;
-  if (threadIdx.x == 0) {
-    if (!prior_given) {
+  if (tid == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += part[k];
+    log_den = log((double)t + alpha * (double)F);
+    if (blockIdx.y == 0 && !prior_given) {
       if (nc[c] == 0) {
         atomicOr(status, ST_BAD_LABEL);
         log_pi[c] = 0.0;
@@ -399,6 +406,11 @@ __global__ void k_finalize_mn(const unsigned long long* counts, const unsigned l
       }
     }
   }
+  __syncthreads();
+  const int j0 = blockIdx.y * kFinTile;
+  const int j1 = min(F, j0 + kFinTile);
+  for (int j = j0 + tid; j < j1; j += blockDim.x)
+    log_theta[(int64_t)c * F + j] = log((double)counts[(int64_t)c * F + j] + alpha) - log_den;
 }
 
 // two-class tables: Delta (FP64 -> FP32, fixed point + limbs), b, interleaved
@@ -849,9 +861,9 @@ nb_status launch_fit_multinomial(nb_model* m, const void* X, nb_dtype dt, int64_
     return NB_OK;
   }
   count_launch();
-  k_finalize_mn<<<C, 256, 0, st>>>(reinterpret_cast<unsigned long long*>(d.counts),
-                                   reinterpret_cast<unsigned long long*>(d.nc), n, F, m->alpha,
-                                   log_prior_dev != nullptr, d.p0, d.log_pi, d.status);
+  k_finalize_mn<<<dim3(C, (F + kFinTile - 1) / kFinTile), 256, 0, st>>>(
+      reinterpret_cast<unsigned long long*>(d.counts), reinterpret_cast<unsigned long long*>(d.nc),
+      n, F, m->alpha, log_prior_dev != nullptr, d.p0, d.log_pi, d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_finalize_mn");
   if (C == 2) {
     count_launch();
