@@ -114,3 +114,26 @@ def test_label_and_size_tensors_checked_before_the_call():
     for bad in (torch.zeros(3, dtype=torch.int32), torch.zeros(2, dtype=torch.int64)):
         with pytest.raises(TypeError):
             nb._sizes(bad, 3)
+
+
+def test_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference times the FP64 oracle on the host cores (no GPU)
+    # and prints one JSON line carrying the same metric as the GPU arm
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--ref-fit-rows", "2000", "--ref-score-rows", "4000",
+                          "--n", "20000"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "files/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["warmup"] >= 3 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] and d["metric"]
