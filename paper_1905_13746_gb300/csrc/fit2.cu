@@ -298,6 +298,11 @@ __global__ void __launch_bounds__(kOvfThreads) k_fit2_ovf(const int64_t* ptr, co
   __syncthreads();
   for (int k = threadIdx.x; k < 2 * F; k += blockDim.x)
     if (bins[k]) atomicAdd(&counts[k], (unsigned long long)bins[k]);
+  // launched programmatically after the row kernel, whose output this kernel
+  // does not read: it starts on SMs as row blocks leave, and waits for the row
+  // kernel only here, so that its own completion (which the finish kernel
+  // waits for) implies the row kernel's
+  pdl_wait();
 }
 
 static nb_status launch_fit2_ovf(nb_model* m, const nb_aux* aux, const int32_t* y, int64_t n,
@@ -314,10 +319,10 @@ static nb_status launch_fit2_ovf(nb_model* m, const nb_aux* aux, const int32_t* 
   if (blocks > cap) blocks = cap;
   if (blocks < (n + kFit2BlockRows - 1) / kFit2BlockRows) blocks = (n + kFit2BlockRows - 1) / kFit2BlockRows;
   count_launch();
-  k_fit2_ovf<<<(unsigned)blocks, kOvfThreads, smem, st>>>(aux->ovf_ptr, aux->ovf_col, aux->ovf_add, y, n,
-                                                  F, reinterpret_cast<unsigned long long*>(m->d.counts),
-                                                  m->d.status);
-  NB_TRY_CUDA(cudaGetLastError(), "k_fit2_ovf launch");
+  NB_TRY_CUDA(launch_pdl(k_fit2_ovf, dim3((unsigned)blocks), dim3(kOvfThreads), (size_t)smem, st,
+                         aux->ovf_ptr, aux->ovf_col, aux->ovf_add, y, (int64_t)n, F,
+                         reinterpret_cast<unsigned long long*>(m->d.counts), m->d.status),
+              "k_fit2_ovf launch");
   return NB_OK;
 }
 
