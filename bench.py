@@ -799,7 +799,58 @@ def cpu_oracle_sample(X16_host_fit, y_fit, X16_host_score, n_train_total, n_tota
             "sample": f"FP64 C oracle, {threads}: fit on {nf} training files "
                       f"({t_fit:.2f} s) + score {ns} files ({t_score:.2f} s), "
                       f"extrapolated linearly to fit {n_train_total} + score {n_total}",
-            "step_s_extrapolated": step_s}
+            "step_s_extrapolated": step_s, "sample_s": t_fit + t_score,
+            "sample_files": {"fit": nf, "score": ns}}
+
+
+def validate_sample(W, rows, got, workers=8, step=32768):
+    """The oracle's check of the timed run (CPU-oracle leg, rank 0, N = 1).
+
+    The oracle counts every training file (row chunks on a few host threads;
+    the integer counts are added, exactly), finalises the FP64 tables and
+    scores the sampled files; the timed run's outputs for those files must
+    have the same labels and log posteriors within 1e-5 * max(1, |lp|).
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    import oracle
+    Xtr, y_tr = W["X16_tr"], W["y"][W["tr"]]
+    n, F = Xtr.shape
+
+    def worker(w):
+        counts = np.zeros((2, F), np.uint64)
+        nc = np.zeros(2, np.uint64)
+        for lo in range(w * step, n, workers * step):
+            hi = min(n, lo + step)
+            Xc = Xtr.view(torch.int16)[lo:hi].cpu().numpy().view(np.uint16)
+            m = oracle.mn_fit(Xc, y_tr[lo:hi], 2)
+            counts += m["counts"]
+            nc += m["nc"]
+        return counts, nc
+
+    t = time.perf_counter()
+    counts = np.zeros((2, F), np.uint64)
+    nc = np.zeros(2, np.uint64)
+    with ThreadPoolExecutor(workers) as ex:
+        for c, k in ex.map(worker, range(workers)):
+            counts += c
+            nc += k
+    ref_model = oracle.mn_finalize(counts, nc, n)
+    rv = torch.as_tensor(rows, device=W["X16"].device)
+    Xs = W["X16"].view(torch.int16).index_select(0, rv).cpu().numpy().view(np.uint16)
+    ref = oracle.score(Xs, ref_model)
+    bad = int((got["label"] != ref["label"]).sum())
+    lp_err = float((np.abs(got["lp"].astype(np.float64) - ref["lp"]) /
+                    np.maximum(1.0, np.abs(ref["lp"]))).max())
+    m_err = float((np.abs(got["margin"].astype(np.float64) - ref["margin"]) /
+                   np.maximum(1.0, np.abs(ref["margin"]))).max())
+    return {"validated": bad == 0 and lp_err <= 1e-5 and m_err <= 1e-5,
+            "rows": int(len(rows)), "label_mismatches": bad, "max_lp_err": lp_err,
+            "max_margin_err": m_err, "oracle_s": time.perf_counter() - t,
+            "how": "labels, margins and log posteriors of a seeded sample of the last timed "
+                   "step's files against the FP64 oracle fitted on every training file"}
 
 
 def workload_config(N, F, n_train, ws):
@@ -840,9 +891,16 @@ def run_reference(args):
     for _ in range(args.steps):
         vals.append(cpu_oracle_sample(Xfit, y[tr[:n_fit]], Xsc, len(tr), N))
     v = statistics.median([x["value"] for x in vals])
+    # ms_per_step is the measured time of one step as run here (the oracle's fit
+    # of the training sample + its scoring of the score sample); value is the
+    # files/s of that run, i.e. the rate at which the full step would go
+    # (ms_per_step_full_extrapolated)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "files/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": statistics.median([x["step_s_extrapolated"] for x in vals]) * 1e3,
+            "ms_per_step": statistics.median([x["sample_s"] for x in vals]) * 1e3,
+            "step_sample_files": vals[0]["sample_files"],
+            "ms_per_step_full_extrapolated":
+                statistics.median([x["step_s_extrapolated"] for x in vals]) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": workload_config(N, F, len(tr), ws),
@@ -963,6 +1021,20 @@ def main():
         dist.barrier()
     ms_step = total_ms / args.steps
     n_rechecked = int(out["n_rechecked"].item())
+    # the timed calls' own status: a bounded wait that ran out or a bad input
+    # in any of them raises here (scoring errors stay set until checked)
+    model.check()
+    # the last timed step's outputs: properties of every file, and a seeded
+    # sample kept for the oracle's check below
+    lab_all = out["label"]
+    run_ok = bool((lab_all <= 1).all().item()) and \
+        bool((out["margin"] >= 0).all().item())
+    import synth
+    vrows = np.sort(np.random.default_rng(synth.seed_for(2) + 9).choice(N, 4096, replace=False))
+    vr = torch.as_tensor(vrows, device=device)
+    snap = {"label": out["label"].index_select(0, vr).cpu().numpy(),
+            "margin": out["margin"].index_select(0, vr).cpu().numpy(),
+            "lp": out["logpost"].index_select(0, vr).cpu().numpy()}
 
     # ---- plain FP32 step on the same data ---------------------------------
     f32_all = nb.Features(W["X16"].to(torch.int32).to(torch.float32), nb.NB_F32)
@@ -976,6 +1048,7 @@ def main():
     p_total, p_fit, p_sc, _ = time_steps(m32, f32_tr, W["y_tr"], f32_all, out, args.steps,
                                          args.warmup, stream)
     p_rechecked = int(out["n_rechecked"].item())
+    m32.check()
     del f32_all, f32_tr, m32
     torch.cuda.empty_cache()
 
@@ -1023,6 +1096,7 @@ def main():
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) -----------------
     cpu = None
+    validation = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         tr = W["tr"]
         nfit = min(args.cpu_fit_rows, len(tr))
@@ -1035,6 +1109,7 @@ def main():
             allc = cpu_oracle_sample(Xfit, W["y"][tr[:nfit]], Xsc, len(tr), N, nthreads=ncores)
             cpu["all_cores"] = {k: allc[k] for k in ("value", "cores", "sample")}
         cpu.pop("step_s_extrapolated", None)
+        validation = validate_sample(W, vrows, snap)
 
     files_per_s = job_rate(N, ms_step, ws)
     line = {
@@ -1070,11 +1145,17 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "gpu_launches": launches,
+        "status_checked": True,
+        "outputs_valid": run_ok,
+        "validated": (validation["validated"] and run_ok) if validation else None,
+        "validation": validation,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+    if not run_ok or (validation is not None and not validation["validated"]):
+        return 1
     return 0
 
 

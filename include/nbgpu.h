@@ -102,7 +102,12 @@ typedef struct {
 
 /* Recheck policy for rows whose FP32/fixed-point result might differ from
  * the FP64 definition:
- *   NB_RECHECK_OFF   -- no recheck (labels may differ on near-ties);
+ *   NB_RECHECK_OFF   -- no recheck of near-ties (labels may differ there);
+ *                       rows that a fast path cannot compute at all are still
+ *                       recomputed in FP64: a two-class u8 row whose stored
+ *                       counts total 2^24 or more (its int32 limb sums could
+ *                       wrap) and tensor-core rows of 2^17 or more counts
+ *                       beyond the scorer's exact-redo capacity;
  *   NB_RECHECK_LABEL -- rows whose margin is within the rigorous error bound
  *                       of the fast path are recomputed in FP64, so every
  *                       label equals the FP64 decision;
@@ -176,24 +181,36 @@ NB_API nb_status nb_refit(nb_model* model, const void* X, nb_dtype dtype, int64_
 
 /* Allocation-free re-fit of a Gaussian model (this entry point has no
  * counterpart in the paper; it is a deployment convenience).
- * Same work and results as nb_refit on a Gaussian model, for callers that may
- * not allocate device memory when they re-train -- a thread held to a fixed
- * memory budget, code between a CUDA graph's instantiation and its replays,
- * an embedded runtime that forbids allocation after start-up.  Its scratch
- * (per-chunk partial sums) is a fixed 8 MiB device array inside the library,
- * present on every GPU that loads the library until the process exits:
- * requests needing more than ceil(n/256) * (C+1) * F + 2F doubles <= 2^20 are
- * rejected with NB_EINVAL (use nb_refit for those).  The first call made on a
- * device looks up the array's device address; make that first call before
- * any stream capture.  All calls share the array, so calls that may run at
- * the same time on the GPU (unordered streams) race; order them.  X (F32,
- * n x ld) and y are device pointers; opts->log_prior (host), var_smoothing
- * and no_sync act as for nb_refit (alpha and aux are ignored). */
+ * Same work and the same bits as nb_refit on a Gaussian model (the same row
+ * chunks and summation order), for callers that may not allocate device
+ * memory when they re-train -- a thread held to a fixed memory budget, code
+ * between a CUDA graph's instantiation and its replays, an embedded runtime
+ * that forbids allocation after start-up.  Its scratch (per-chunk partial
+ * sums) is a fixed 8 MiB device array inside the library.  The 8 MiB are
+ * committed on a device when nb_fit first creates a Gaussian model there
+ * (the library then looks up the array's address, which makes the CUDA
+ * runtime load the array's module; with lazy module loading, the default,
+ * merely loading the library commits nothing), or else at the first call of
+ * this entry point on that device; they stay until the process exits.  Make
+ * that first call, or the Gaussian nb_fit, before any stream capture.
+ * Requests needing more than ceil(n/r) * (C+1) * F + 2F doubles <= 2^20, with
+ * r = 32 rows per partial sum for n <= 65,536 and 256 above, are rejected
+ * with NB_EINVAL (use nb_refit for those).  All calls share the array, so
+ * calls that may run at the same time on the GPU (unordered streams) race;
+ * order them.  X (F32, n x ld) and y are device pointers; opts->log_prior
+ * (host), var_smoothing and no_sync act as for nb_refit (alpha and aux are
+ * ignored); errors as nb_refit. */
 NB_API nb_status nb_refit_gaussian_noalloc(nb_model* model, const float* X, int64_t n,
                                            int64_t ld, const int32_t* y,
                                            const nb_fit_opts* opts, void* cuda_stream);
 
-/* Waits for the model's fit and returns NB_EINVAL if its data were invalid. */
+/* Waits for the model's stream, then reports, in this order: NB_ETIMEOUT if
+ * a bounded device wait ran out (in the last fit, or in a scoring call with
+ * this model since the previous check: the outputs of that call are not
+ * valid); NB_EINVAL if the last fit's data were invalid or a scoring call met
+ * an overflow-list column outside [0, F).  Errors of scoring calls are kept
+ * (a later re-fit does not clear them) until this call reports them, and
+ * cleared then; errors of the fit are cleared by the next fit. */
 NB_API nb_status nb_model_check(const nb_model* model);
 
 /* Copies the exact multinomial counts N_cj (C x F) and n_c (C) to HOST

@@ -96,6 +96,7 @@ static nb_status alloc_model(nb_model* m) {
   d.log_pi = reinterpret_cast<double*>(b + o_lpi);
   d.gconst = reinterpret_cast<double*>(b + o_gc);
   d.status = reinterpret_cast<int*>(b + o_st);
+  d.sstatus = d.status + 1;   // outside the fit's clear of counts, nc and status
   d.fin = reinterpret_cast<unsigned long long*>(b + o_fin);
   d.c2 = reinterpret_cast<C2Header*>(b + o_c2);
   d.delta = reinterpret_cast<float*>(b + o_delta);
@@ -116,7 +117,7 @@ static nb_status alloc_model(nb_model* m) {
   return NB_OK;
 }
 
-static nb_status status_from_word(int w) {
+nb_status status_from_word(int w) {
   if (w & ST_TIMEOUT) {
     set_error("a bounded device wait ran out");
     return NB_ETIMEOUT;
@@ -274,6 +275,10 @@ extern "C" nb_status nb_fit(nb_kind kind, const void* X, nb_dtype dtype, int64_t
     delete m;
     return s;
   }
+  // a Gaussian model may later be re-fitted by nb_refit_gaussian_noalloc,
+  // whose fixed scratch is committed on this device now, while allocating is
+  // still allowed; if that fails here, that entry point's first call retries
+  if (kind == NB_GAUSSIAN && noalloc_scratch_prepare() != NB_OK) cudaGetLastError();
   cudaError_t e = cudaMemsetAsync(m->mem, 0, m->mem_bytes, m->stream);
   if (e == cudaSuccess) s = fit_into(m, X, dtype, n, ld, y, prior, aux, no_sync, m->stream);
   else s = cuda_status(e, "memset(model)");
@@ -307,11 +312,18 @@ extern "C" nb_status nb_model_check(const nb_model* m) {
     set_error("nb_model_check: NULL model");
     return NB_EINVAL;
   }
-  int w = 0;
-  cudaError_t e = cudaMemcpyAsync(&w, m->d.status, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+  int w[2] = {0, 0};
+  cudaError_t e =
+      cudaMemcpyAsync(w, m->d.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return cuda_status(e, "nb_model_check");
-  return status_from_word(w);
+  // the scoring word is reported once: clear it (in stream order) when set
+  if (w[1] != 0) {
+    e = cudaMemsetAsync(m->d.sstatus, 0, sizeof(int), m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_status(e, "nb_model_check");
+  }
+  return status_from_word(w[0] | w[1]);
 }
 
 extern "C" nb_status nb_model_counts(const nb_model* m, uint64_t* host_counts, uint64_t* host_nc) {
@@ -428,7 +440,7 @@ extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype d
   if (m->kind == NB_MULTINOMIAL && m->C == 2 && aligned) {
     // the two-class scorers count the rows they mark, so the recheck can skip
     // its scan when there are none
-    o.counted = n_rechecked != nullptr && recheck != NB_RECHECK_OFF;
+    o.counted = n_rechecked != nullptr;
     s = launch_score2(m, X, dtype, n, ld, aux, o, st);
   }
   else if (tc_eligible(m, dtype, X, ld))

@@ -92,14 +92,13 @@ static nb_status batch_launch(nb_batch* b, cudaStream_t st) {
                                       b->recheck, b->status, st);
     if (s != NB_OK) return s;
   }
-  if (b->recheck != NB_RECHECK_OFF) {
-    for (int f = 0; f < kFamilies; ++f) {
-      if (b->fam[f].empty()) continue;
-      nb_status s = launch_recheck_seg(list_of(b->dev, f, b->max_groups), dh + f,
-                                       b->fam[f].data(), (int)b->fam[f].size(), b->dtype, b->F,
-                                       b->want_lp, b->counter, st);
-      if (s != NB_OK) return s;
-    }
+  // also under NB_RECHECK_OFF: rows a scorer could not compute at all are marked
+  for (int f = 0; f < kFamilies; ++f) {
+    if (b->fam[f].empty()) continue;
+    nb_status s = launch_recheck_seg(list_of(b->dev, f, b->max_groups), dh + f,
+                                     b->fam[f].data(), (int)b->fam[f].size(), b->dtype, b->F,
+                                     b->want_lp, b->counter, st);
+    if (s != NB_OK) return s;
   }
   return NB_OK;
 }

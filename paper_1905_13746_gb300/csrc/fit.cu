@@ -1023,9 +1023,7 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
   k_label_hist<<<(unsigned)(g < sms * 4 ? g : sms * 4), 256, 0, st>>>(
       y, n, C, reinterpret_cast<unsigned long long*>(d.nc), d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_label_hist");
-  // row chunks: 32 rows for small fits (more blocks in flight), else 256; the
-  // partials are summed in chunk order, so the result depends only on n
-  const int64_t chunk_rows = n <= 65536 ? 32 : kGChunkRows;
+  const int64_t chunk_rows = gauss_chunk_rows(n);
   const int nchunk = (int)((n + chunk_rows - 1) / chunk_rows);
   const size_t part_elems = (size_t)nchunk * S * F;
   const size_t extra = (size_t)F * 2;   // mu_all, m2_all

@@ -1162,7 +1162,7 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   a.want_lp = g->want_lp;
   a.recheck = g->recheck;
   a.status = g->status;
-  const bool counted = n_rechecked != nullptr && g->recheck != NB_RECHECK_OFF;
+  const bool counted = n_rechecked != nullptr;
   a.marks = counted ? reinterpret_cast<unsigned long long*>(n_rechecked) : nullptr;
   if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(k_score_gw, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
@@ -1177,7 +1177,6 @@ static nb_status groupwise_fused(nb_groupwise* g, const void* X, int64_t ld, con
   count_launch();
   k_score_gw<<<(unsigned)blocks, (kGwNCW + 1) * 32, smem, st>>>(a, p);
   NB_TRY_CUDA(cudaGetLastError(), "k_score_gw launch");
-  if (g->recheck == NB_RECHECK_OFF) return NB_OK;
   return launch_recheck_gw(static_cast<const unsigned char*>(X), ld, n, sizes, g->bin_bytes,
                            g->n_bins, g->k, g->model_of, g->cols, g->models.data(), g->n_models,
                            label, margin, g->want_lp ? logpost : nullptr, g->want_lp, n_rechecked,

@@ -85,7 +85,9 @@ struct ModelDev {
   double* p1;          // C x F      var (Gaussian)
   double* log_pi;      // C
   double* gconst;      // C          Gaussian: log pi_c - 1/2 sum_j log(2 pi var_cj)
-  int* status;         // 1 int: ST_* bits raised while fitting
+  int* status;         // 1 int: ST_* bits raised while fitting (cleared by each fit)
+  int* sstatus;        // 1 int: ST_* bits raised by scoring calls (kept until
+                       // nb_model_check reports them)
   unsigned long long* fin;   // 4 words of the two-class fit finish (zero between fits)
   // two-class multinomial tables
   C2Header* c2;        // 1
@@ -198,6 +200,17 @@ void count_launch();
 // Gaussian fit: rows per deterministic partial sum, features per block tile
 constexpr int kGChunkRows = 256;
 constexpr int kGTile = 64;
+// rows per partial sum of a fit of n rows: 32 for small fits (more blocks in
+// flight), else kGChunkRows; the partials are summed in chunk order, so the
+// result depends only on n (every Gaussian fit path uses this rule)
+inline int64_t gauss_chunk_rows(int64_t n) { return n <= 65536 ? 32 : kGChunkRows; }
+
+// ST_* bits of a status word -> status code and error text (first error wins)
+nb_status status_from_word(int w);
+
+// Looks up the allocation-free re-fit's device scratch for the current device
+// (noalloc.cu); under lazy module loading this is what commits it.
+nb_status noalloc_scratch_prepare();
 
 // Gaussian fit kernels (fit.cu)
 __global__ void k_label_hist(const int32_t* y, int64_t n, int C, unsigned long long* nc,

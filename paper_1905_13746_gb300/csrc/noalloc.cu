@@ -9,13 +9,17 @@
 // does the same work with the partials in a file-scope device array instead,
 // so the call itself allocates nothing.
 //
-// The array holds kScratchDoubles doubles (8 MiB) on every GPU that loads the
-// library, until the process exits.  Its device address is looked up once per
-// device, on the first call made with that device current.  All calls share
-// the one array and each leaves its partials there: calls that overlap on the
-// GPU (different streams, no ordering between them) race on it.  Every value a
-// call reads from the array is first written by the same call, so nothing has
-// to be cleared between calls.
+// The array holds kScratchDoubles doubles (8 MiB).  It lives in this file's
+// own device module, which the CUDA runtime loads on a device when the
+// library first asks for the array's address there (with lazy module loading,
+// the default, not when the library is loaded): nb_fit asks when it creates a
+// Gaussian model, and so does the first call of this entry point on a device
+// where that has not happened.  From then on the 8 MiB stay committed on that
+// device until the process exits.  The address is looked up once per device.
+// All calls share the one array and each leaves its partials there: calls
+// that overlap on the GPU (different streams, no ordering between them) race
+// on it.  Every value a call reads from the array is first written by the
+// same call, so nothing has to be cleared between calls.
 #include <mutex>
 
 #include "internal.cuh"
@@ -47,6 +51,11 @@ static nb_status scratch_for_current_device(double** out) {
   return NB_OK;
 }
 
+nb_status noalloc_scratch_prepare() {
+  double* p = nullptr;
+  return scratch_for_current_device(&p);
+}
+
 }  // namespace nbg
 
 using namespace nbg;
@@ -75,12 +84,14 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
         set_error("nb_refit_gaussian_noalloc: log priors must be finite");
         return NB_EINVAL;
       }
-  const long long nchunk = (n + kGChunkRows - 1) / kGChunkRows;
+  // the same row chunks as nb_refit, so the partial sums and their order match
+  const int64_t chunk_rows = gauss_chunk_rows(n);
+  const long long nchunk = (n + chunk_rows - 1) / chunk_rows;
   const size_t need = (size_t)nchunk * S * F + 2 * (size_t)F;
   if (need > kScratchDoubles) {
-    set_error("nb_refit_gaussian_noalloc: ceil(n/%d)*(C+1)*F + 2F = %zu doubles exceeds the "
+    set_error("nb_refit_gaussian_noalloc: ceil(n/%lld)*(C+1)*F + 2F = %zu doubles exceeds the "
               "fixed scratch of %zu doubles; use nb_refit",
-              kGChunkRows, need, kScratchDoubles);
+              (long long)chunk_rows, need, kScratchDoubles);
     return NB_EINVAL;
   }
   double* scratch = nullptr;
@@ -115,7 +126,7 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
   for (int pass = 0; pass < 2; ++pass) {
     count_launch();
     k_gauss_partial<<<grid, 256, smem, st>>>(X, ld, n, F, C, y, pass, d.p0, mu_all, partial,
-                                             (int64_t)kGChunkRows, d.status);
+                                             chunk_rows, d.status);
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_partial");
     count_launch();
     k_gauss_reduce<<<rb < 1024 ? rb : 1024, 256, 0, st>>>(
@@ -134,10 +145,7 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
     NB_TRY_CUDA(cudaMemcpyAsync(&w, d.status, sizeof(int), cudaMemcpyDeviceToHost, st),
                 "memcpy(status)");
     NB_TRY_CUDA(cudaStreamSynchronize(st), "sync");
-    if (w) {
-      set_error("nb_refit_gaussian_noalloc: invalid labels or feature values (status 0x%x)", w);
-      return (w & ST_TIMEOUT) ? NB_ETIMEOUT : NB_EINVAL;
-    }
+    return status_from_word(w);
   }
   return NB_OK;
 }

@@ -143,7 +143,9 @@ __global__ void __launch_bounds__(256) k_recheck(const RArgs a) {
 
 nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t n, int64_t ld,
                          const nb_aux* aux, const ScoreOut& o, cudaStream_t st) {
-  if (n == 0 || o.recheck == NB_RECHECK_OFF) return NB_OK;
+  // NB_RECHECK_OFF still recomputes the rows a scorer could not compute at all
+  // (see NB_RECHECK_OFF in the header); in that mode nothing else is marked
+  if (n == 0) return NB_OK;
   RArgs a{};
   a.v.X = static_cast<const char*>(X);
   a.v.ld = ld;

@@ -140,11 +140,9 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
       if (!ok[r] || (r % LPR) != li) continue;
       const float Dsum = (float)D[r] * h.inv_scale;
       const float d = Dsum + h.b;
-      const float T = (float)tot[r];
-      // quantisation of Delta + int64->f32 and final-add roundings + FP64 slack
-      const float tau = 0.5f * T * h.inv_scale * 1.0001f +
-                        2.4e-7f * (fabsf(Dsum) + fabsf(h.b)) +
-                        1e-12f * (T * h.maxabs + fabsf(h.b)) + 1e-30f;
+      // quantisation of Delta + int64->f32 and final-add roundings + FP64 slack;
+      // +inf past the int32 range of the limb sums
+      const float tau = c2_tau_u8((float)tot[r], Dsum, h.b, h.inv_scale, h.maxabs);
       marks += c2_store(a.label, a.margin, a.logpost, a.want_lp, a.recheck, row0 + r, d, tau);
     }
   }
@@ -352,7 +350,7 @@ nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt, int64_t n
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
   a.marks = o.counted ? reinterpret_cast<unsigned long long*>(o.n_rechecked) : nullptr;
-  a.status = m->d.status;
+  a.status = m->d.sstatus;
   int smem;
   if (dt == NB_U8) {
     a.nvec_tab = m->nvec8;

@@ -43,13 +43,16 @@ __device__ __forceinline__ float softplusf(float z) {
 
 // Outputs of one row from its log-odds d and the bound tau on |d - d_exact|:
 // label (or the recheck mark), margin |d|, log posteriors -softplus(-+d).
+// tau = +inf says that the fast path's sums are not valid for this row at all
+// (see c2_tau_u8): the row is marked in every recheck mode, NB_RECHECK_OFF
+// included.
 __device__ __forceinline__ bool c2_store(uint8_t* label, float* margin, float* logpost,
                                          int want_lp, int recheck, int64_t row, float d,
                                          float tau) {
-  bool flag = false;
+  bool flag = !(tau < INFINITY);
   const float ad = fabsf(d);
   if (recheck != NB_RECHECK_OFF) {
-    flag = !(ad > tau);  // also true for NaN
+    flag = flag || !(ad > tau);  // also true for NaN
     if (recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, ad)) flag = true;
   }
   label[row] = flag ? kLabelRecheck : (d > 0.f ? 1 : 0);
@@ -87,8 +90,14 @@ __device__ __forceinline__ void c2_flush_marks(const S2Args& a, unsigned cnt) {
 // Rigorous bound on |d_gpu - d_exact| of the fixed-point u8 path: the Delta
 // quantisation (half a step per unit count), the int64 -> FP32 conversion and
 // the final add, and slack for the FP64 reference's own rounding.
+// Each of the three limb sums is bounded by 128 T (|limb| <= 128) and is held
+// in an int32, which is exact only while 128 T < 2^31: a row of T >= 2^24
+// stored counts (possible with the overflow list, whose entries add up to
+// 65,535 each) gets tau = +inf, i.e. the FP64 recheck in every mode.  T is the
+// exact integer total converted to FP32, which keeps the comparison exact.
 __device__ __forceinline__ float c2_tau_u8(float T, float Dsum, float b, float inv_scale,
                                            float maxabs) {
+  if (T >= 16777216.f) return INFINITY;
   return 0.5f * T * inv_scale * 1.0001f + 2.4e-7f * (fabsf(Dsum) + fabsf(b)) +
          1e-12f * (T * maxabs + fabsf(b)) + 1e-30f;
 }

@@ -45,10 +45,7 @@ __device__ __forceinline__ void finish_row(const S2Args& a, float hb, float inv_
     const long long D = ((long long)r.a2 << 16) + ((long long)r.a1 << 8) + (long long)r.a0;
     const float Dsum = (float)D * inv_scale;
     const float d = Dsum + hb;
-    const float T = (float)r.t;
-    const float tau = 0.5f * T * inv_scale * 1.0001f + 2.4e-7f * (fabsf(Dsum) + fabsf(hb)) +
-                      1e-12f * (T * maxabs + fabsf(hb)) + 1e-30f;
-    c2_epilogue(a, row, d, tau);
+    c2_epilogue(a, row, d, c2_tau_u8((float)r.t, Dsum, hb, inv_scale, maxabs));
   } else {
     float scale = 1.f;
     if (DT == NB_FP8E4M3 && a.row_exp) scale = exp2f((float)a.row_exp[row]);

@@ -514,7 +514,7 @@ nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt, in
   a.logpost = o.logpost;
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
-  a.status = m->d.status;
+  a.status = m->d.sstatus;
   const int C_pad = ((m->C + 3) / 4) * 4;
   const int smem =
       (int)sizeof(float) * (GBK * (GBM + 4) + GBK * (GCB + 4) + GBM * C_pad + GBM + GBM * 8);

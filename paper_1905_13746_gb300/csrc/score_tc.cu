@@ -31,8 +31,8 @@
 //               128 rows x 128 features per box, 128-byte swizzle, zero fill
 //               past the last row and feature);
 //   warp 17     allocates tensor memory and issues the MMAs (one thread);
-//   warp 18     streams the weight-limb stages (bulk copies, multicast to the
-//               CTAs of a cluster).
+//   warp 18     streams the weight-limb stages (one bulk copy per stage into
+//               this CTA's own shared memory).
 // Every wait is bounded; a wait that runs out raises ST_TIMEOUT, all roles
 // stop, outstanding copies and MMAs are waited for, and tensor memory is freed.
 #include <cuda.h>
@@ -86,7 +86,6 @@ struct TcArgs {
   TcModelArg models[kSegMaxModels];
   int F, nks, nraw, want_lp, recheck;
   int single;               // 1: one accumulation per row, heavy rows redone exactly
-  int cs;                   // CTAs per cluster sharing each weight stage (multicast)
   uint32_t b_bytes;         // bytes of one weight stage (largest model)
   int* status;
 };
@@ -102,7 +101,6 @@ struct TcShared {
   uint64_t b_full[TC_NAB], a_full[TC_NAB], ab_empty[TC_NAB];
   uint64_t acc_full[2], acc_empty[2], fin, redo_ready;
   uint64_t xfull, xfree;        // exchange written by all parts / read by all parts
-  uint64_t bclu_empty[TC_NAB];  // cluster leader: weight stage consumed by every CTA
   uint32_t tmem;
   int abort;
   int redo_flag[2];
@@ -431,25 +429,19 @@ __device__ __forceinline__ bool tc_drain(const TcArgs& a, TcShared& sh, TcXch* x
 
 // Tiles of this CTA: phase 0 its share of all tiles (blockIdx.x + i gridDim.x),
 // phase 1 the tiles it queued for the exact pass.
-// Phase 0 deals groups of cs consecutive tiles to the clusters in turn; CTA r
-// of a cluster takes tile r of each group (a tile past the end is a dummy that
-// reads zeros and writes nothing), so every CTA of a cluster runs through the
-// same weight stages.
 __device__ __forceinline__ long long tc_ntiles(const TcArgs& a, TcShared& sh, long long n_tiles,
                                                int phase) {
   if (phase) {
     const int c = *reinterpret_cast<volatile int*>(&sh.redo_n);
     return c < TC_REDO_CAP ? c : TC_REDO_CAP;
   }
-  const long long ncl = gridDim.x / a.cs, k = blockIdx.x / a.cs;
-  const long long groups = (n_tiles + a.cs - 1) / a.cs;
-  return k < groups ? (groups - k + ncl - 1) / ncl : 0;
+  const long long k = blockIdx.x;
+  return k < n_tiles ? (n_tiles - k + gridDim.x - 1) / gridDim.x : 0;
 }
 __device__ __forceinline__ long long tc_tile_at(const TcArgs& a, TcShared& sh, int phase,
                                                 long long i) {
   if (phase) return (long long)sh.redo_list[i];
-  const long long ncl = gridDim.x / a.cs, k = blockIdx.x / a.cs;
-  return (k + i * ncl) * a.cs + blockIdx.x % a.cs;
+  return (long long)blockIdx.x + i * (long long)gridDim.x;
 }
 // MMA stages per accumulation chunk: the whole row in the single-accumulation
 // phase, 512 features (always exact) otherwise
@@ -488,7 +480,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
     mbar_init(&sh.xfull, TC_WORK);
     mbar_init(&sh.xfree, TC_WORK);
     mbar_init(&sh.redo_ready, TC_WORK);
-    for (int i = 0; i < TC_NAB; ++i) mbar_init(&sh.bclu_empty[i], (uint32_t)a.cs);
     sh.abort = 0;
     sh.redo_flag[0] = sh.redo_flag[1] = 0;
     sh.redo_n = 0;
@@ -496,7 +487,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
   if (warp == TC_WORK + 1) tmem_alloc(&sh.tmem, 512);
   tc_fence_before();
   __syncthreads();
-  if (a.cs > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = sh.tmem;
 
@@ -597,26 +587,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
           ok = false;
           break;
         }
-        int okl = 1;
         if (lane == 0) {
           mbar_expect_tx(&sh.b_full[slot], sb);
-          const void* src = M.wlay + (size_t)ks * sb;
-          if (a.cs == 1 || phase == 1) {
-            bulk_g2s(B + (size_t)slot * a.b_bytes, src, sb, &sh.b_full[slot]);
-          } else if (cluster_rank() == 0) {
-            // the leader refills a slot once every CTA of the cluster consumed it
-            if (tc_wait(sh, &sh.bclu_empty[slot], bpar ^ 1u, a.status))
-              bulk_g2s_multicast(B + (size_t)slot * a.b_bytes, src, sb, &sh.b_full[slot],
-                                 (uint16_t)((1u << a.cs) - 1u));
-            else
-              okl = 0;
-          }
+          bulk_g2s(B + (size_t)slot * a.b_bytes, M.wlay + (size_t)ks * sb, sb, &sh.b_full[slot]);
         }
         last[slot] = bi;
-        if (!__shfl_sync(0xFFFFFFFFu, okl, 0)) {
-          ok = false;
-          break;
-        }
+        __syncwarp();
       }
      }
     }
@@ -665,7 +641,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             tc_mma_f16(d, tc_desc(as + 256u * j, 128u, 1024u), tc_desc(bs + 256u * j, 128u, 1024u),
                        idesc, (uint32_t)(kc | j));
           tc_commit(&sh.ab_empty[slot]);
-          if (a.cs > 1 && phase == 0) tc_commit_multicast(&sh.bclu_empty[slot], 1);
           if (++kc == chunk || ks == nks - 1) {
             tc_commit(&sh.acc_full[buf]);
             ++di;
@@ -812,7 +787,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
   }
   tc_fence_before();
   __syncthreads();
-  if (a.cs > 1) cluster_sync_all();   // no CTA leaves while others may still signal it
   tc_fence_after();
   if (warp == TC_WORK + 1) tmem_dealloc(tmem, 512);
 }
@@ -924,39 +898,12 @@ static nb_status run_tc(TcArgs& a, int maxN, long long tiles_hint, cudaStream_t 
                                    (int)launch_smem),
               "cudaFuncSetAttribute(k_score_tc)");
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(TC_THREADS);
   cfg.dynamicSmemBytes = launch_smem;
   cfg.stream = st;
-  // clusters of cs CTAs share each weight stage (multicast from the leader)
-  int cs = a.cs < 1 ? 1 : a.cs;
-  int max_clusters = 0;
-  if (cs > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3((unsigned)(num_sms() / cs * cs));
-    if (cudaOccupancyMaxActiveClusters(&max_clusters, k_score_tc, &cfg) != cudaSuccess ||
-        max_clusters < 1) {
-      cudaGetLastError();
-      cs = 1;
-    }
-  }
-  a.cs = cs;
-  if (cs == 1) {
-    long long grid = num_sms();
-    if (tiles_hint > 0 && tiles_hint < grid) grid = tiles_hint;
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.attrs = nullptr;
-    cfg.numAttrs = 0;
-  } else {
-    long long ncl = (tiles_hint + cs - 1) / cs;
-    if (ncl > max_clusters) ncl = max_clusters;
-    cfg.gridDim = dim3((unsigned)(ncl * cs));
-  }
+  long long grid = num_sms();
+  if (tiles_hint > 0 && tiles_hint < grid) grid = tiles_hint;
+  cfg.gridDim = dim3((unsigned)grid);
   count_launch();
   NB_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_score_tc, a), "k_score_tc launch");
   return NB_OK;
@@ -1029,9 +976,8 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   a.nks = (m->F + TC_KS - 1) / TC_KS;
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
-  a.status = m->d.status;
+  a.status = m->d.sstatus;
   a.single = 1;
-  a.cs = a.tiles0 >= 8 ? 4 : (a.tiles0 >= 4 ? 2 : 1);
   return run_tc(a, a.models[0].N, a.tiles0, st);
 }
 
@@ -1062,7 +1008,6 @@ nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, cons
   a.recheck = recheck;
   a.status = status;
   a.single = 1;
-  a.cs = 1;   // neighbouring tiles may belong to groups of different models
   return run_tc(a, maxN, 0, st);
 }
 

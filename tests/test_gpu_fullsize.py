@@ -105,16 +105,40 @@ def _rows_host(X, rows):
     return X.index_select(0, torch.as_tensor(rows, device=X.device)).cpu().numpy()
 
 
-def _cols_counts_oracle(Xtr, ytr, C, cols):
-    # exact counts of the sampled columns over every training row
-    sub = Xtr.index_select(1, torch.as_tensor(cols, device=Xtr.device)).cpu().numpy()
-    return oracle.mn_fit(sub, ytr, C)
+def _oracle_counts(Xtr, ytr, C, step=4096, workers=8):
+    """Exact class counts of every training row and column, by the oracle.
+
+    The rows go to the host in chunks of ``step``; the oracle counts each
+    chunk and the integer counts are added (exact, in any order).  Chunks run
+    on a few host threads (the oracle and the copies release the GIL).
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
+    n, F = Xtr.shape
+
+    def worker(w):   # chunks w, w + workers, ...
+        counts = np.zeros((C, F), np.uint64)
+        nc = np.zeros(C, np.uint64)
+        for lo in range(w * step, n, workers * step):
+            hi = min(n, lo + step)
+            m = oracle.mn_fit(Xtr[lo:hi].cpu().numpy(), ytr[lo:hi], C)
+            counts += m["counts"]
+            nc += m["nc"]
+        return counts, nc
+
+    counts = np.zeros((C, F), np.uint64)
+    nc = np.zeros(C, np.uint64)
+    with ThreadPoolExecutor(workers) as ex:
+        for c, k in ex.map(worker, range(workers)):
+            counts += c
+            nc += k
+    return counts, nc
 
 
 def test_many_class_workload_full_size():
     # C = 64 (Zipf 1.1 priors), F = 8,192 u8 counts, N = 2M files: the
-    # tensor-core scorer on the whole group, the oracle on sampled rows and
-    # on the counts of sampled columns
+    # tensor-core scorer on the whole group; the oracle's exact counts over
+    # every training row and column, its scores on sampled rows
     seed = synth.seed_for(4)
     C, Fm, Nm = 64, 8192, 2_000_000
     p = synth.dirichlet_profiles(seed, C, Fm, 0.1)
@@ -131,11 +155,10 @@ def test_many_class_workload_full_size():
     torch.cuda.synchronize()
 
     g_counts, g_nc = model.counts()
-    cols = _sample(Fm, 32, 11)
-    sub = _cols_counts_oracle(Xtr, ytr, C, cols)
-    assert (g_counts[:, cols] == sub["counts"]).all()
-    assert (g_nc == sub["nc"]).all()
-    ref_model = oracle.mn_finalize(g_counts, g_nc, len(tr))
+    counts, nc = _oracle_counts(Xtr, ytr, C)
+    assert (g_counts == counts).all()
+    assert (g_nc == nc).all()
+    ref_model = oracle.mn_finalize(counts, nc, len(tr))
     lt, _, lpi = model.params()
     assert np.allclose(lt, ref_model["log_theta"], rtol=1e-14, atol=1e-13)
 
@@ -166,11 +189,10 @@ def test_feature_sweep_widest_point_full_size():
     res = to_np(nb.score(model, nb.Features(X, nb.NB_U8)))
 
     g_counts, g_nc = model.counts()
-    cols = _sample(Fs, 32, 21)
-    sub = _cols_counts_oracle(X[:ntr], y[:ntr], 2, cols)
-    assert (g_counts[:, cols] == sub["counts"]).all()
-    assert (g_nc == sub["nc"]).all()
-    ref_model = oracle.mn_finalize(g_counts, g_nc, ntr)
+    counts, nc = _oracle_counts(X[:ntr], y[:ntr], 2)
+    assert (g_counts == counts).all()
+    assert (g_nc == nc).all()
+    ref_model = oracle.mn_finalize(counts, nc, ntr)
 
     rows = _sample(Ns, 2048, 22)
     Xs = _rows_host(X, rows)

@@ -146,6 +146,76 @@ def test_marked_rows_counted_by_every_scorer(fmt):
         assert len(set(counts.values())) == 1, counts
 
 
+def _heavy_rows(seed, F, n):
+    """u16 rows whose stored counts total 2^24 or more (beside rows just below).
+
+    Row kinds, cycling: (0) every column in [20,000, 65,535] (T ~ 4e7);
+    (1) 256 columns at 65,535 (T = 2^24 - 256, the largest total the int32
+    limb sums hold for every table); (2) the same plus 256 columns of 1
+    (T = 2^24 exactly); (3) a random half of the columns in [30,000, 65,535].
+    """
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, F), np.int64)
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:
+            X[i] = rng.integers(20_000, 65_536, F)
+        elif kind in (1, 2):
+            cols = rng.permutation(F)
+            X[i, cols[:256]] = 65_535
+            if kind == 2:
+                X[i, cols[256:512]] = 1
+        else:
+            cols = rng.permutation(F)[: F // 2]
+            X[i, cols] = rng.integers(30_000, 65_536, cols.size)
+    return X
+
+
+@pytest.mark.parametrize("path", ["register", "pipelined", "batch"])
+@pytest.mark.parametrize("recheck", [nb.NB_RECHECK_LP, nb.NB_RECHECK_OFF])
+def test_u8_rows_past_the_int32_limb_range(path, recheck):
+    # The exact u8 path sums three limbs of |q| <= 128 in int32s, exact while a
+    # row's stored total T < 2^24.  Heavier rows (reachable with the overflow
+    # list) must reach the FP64 recheck in every mode and match the oracle.
+    F, n_fit = 1024, 3001
+    X, y, _ = count_matrix(321, n_fit + 1200, F)
+    H = _heavy_rows(322, F, 203)
+    Xs = np.concatenate([X[n_fit:], H])
+    perm = np.random.default_rng(323).permutation(len(Xs))
+    Xs = Xs[perm]
+    T = Xs.sum(axis=1)
+    n_heavy = int((T >= 2**24).sum())
+    assert n_heavy >= 100 and int(((T < 2**24) & (T >= 2**24 - 256)).sum()) > 0
+    ffit, vfit = stored(X[:n_fit], "u8ovf")
+    fsc, vsc = stored(Xs, "u8ovf")
+    assert (vsc == Xs).all()
+    model = nb.fit(ffit, torch.from_numpy(y[:n_fit]).cuda(), 2)
+    _, ref = oracle_mn(vfit, y[:n_fit], 2, vsc)
+    if path == "batch":
+        batch = nb.Batch([model], nb.NB_U8, fsc.ld, 4, recheck=recheck)
+        out = batch.outputs(0, fsc.n)
+        nre = torch.zeros(1, dtype=torch.int64, device="cuda")
+        batch.score([(0, fsc, out)], n_rechecked=nre)
+        torch.cuda.synchronize()
+        res = to_np(dict(out, n_rechecked=nre))
+    else:
+        model.set_tile_config(nb.NB_VARIANT_REGISTER if path == "register"
+                              else nb.NB_VARIANT_PIPELINED, 0, 0, 0)
+        res = to_np(nb.score(model, fsc, recheck=recheck))
+    heavy = T >= 2**24
+    if recheck == nb.NB_RECHECK_OFF:
+        rows = np.nonzero(heavy)[0]
+        compare(res, {k: v[rows] for k, v in ref.items()}, rows=rows)
+    else:
+        compare(res, ref)
+    assert (res["label"] != 255).all()
+    assert res["n_rechecked"] >= n_heavy
+    if recheck == nb.NB_RECHECK_OFF:
+        assert res["n_rechecked"] == n_heavy
+        # the other rows: fast-path labels, which may differ only on near-ties
+        assert (res["label"][~heavy] == ref["label"][~heavy]).mean() > 0.999
+
+
 def test_all_zero_rows_tie_to_benign():
     X, y, _ = count_matrix(11, 2000, 64)
     f, _ = stored(X, "u16")
@@ -288,10 +358,21 @@ def test_overflow_column_outside_F_rejected():
     X, y, _ = count_matrix(722, 2000, 64)
     f, _ = stored(X, "u8ovf")
     assert f.ovf_col.numel() > 0
+    good, _ = stored(X, "u8ovf")
     f.ovf_col[0] = 64 + 5
     with pytest.raises(nb.NbError) as ei:
         nb.fit(f, torch.from_numpy(y).cuda(), 2)
     assert ei.value.status == nb.NB_EINVAL
+    # a scoring call reports it through nb_model_check, even after a re-fit,
+    # once: the scoring error word is cleared when it has been reported
+    model = nb.fit(good, torch.from_numpy(y).cuda(), 2)
+    model.check()
+    nb.score(model, f)
+    nb.refit(model, good, torch.from_numpy(y).cuda())
+    with pytest.raises(nb.NbError) as ei:
+        model.check()
+    assert ei.value.status == nb.NB_EINVAL
+    model.check()
 
 
 def test_invalid_inputs_rejected():
