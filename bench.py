@@ -38,9 +38,8 @@ METRIC = ("files/sec & HBM-roofline % at F=1024, plain FP32 vs low-prec; "
 # u8 two-class scorer on the default workload: an ncu capture of the same
 # kernel and tile configuration on 500,000 files of the same recipe, scaled by
 # the files processed (summarised under profiles/); reported only for that
-# workload and tile configuration.
-SCORE_TRAFFIC = {(1_000_000, 1024, (1, 4, 48, 2)): 2 * (523_985_920 + 7_966_208),
-                 (1_000_000, 1024, (1, 2, 48, 2)): 2 * (525_441_536 + 8_657_408)}
+# workload and tile configuration, and only for the kernel as measured.
+SCORE_TRAFFIC = {(1_000_000, 1024, (1, 2, 48, 2)): 2 * (524_048_384 + 7_884_288)}
 
 
 def _dist():
@@ -291,7 +290,7 @@ def _time_score(model, f, stream, reps=5, warm=2, recheck=None):
     return e0.elapsed_time(e1) / reps, int(out["n_rechecked"].item())
 
 
-def run_fsweep(args, device):
+def run_fsweep(args, device, Fs=(64, 256, 1024, 4096, 16384)):
     """Two classes, F in {64 .. 16384}: u8 (counts clamped at 255), FP8 E4M3 with a
     per-row exponent, and plain FP32 rows, scored with log posteriors and the
     FP64 recheck.  Dirichlet(0.05) profiles with 30% of the features shared."""
@@ -303,7 +302,7 @@ def run_fsweep(args, device):
     seed = synth.seed_for(3)
     stream = torch.cuda.Stream(device)
     rows = []
-    for F in (64, 256, 1024, 4096, 16384):
+    for F in Fs:
         N = args.fs_n if F <= 4096 else args.fs_n // 4
         p = synth.dirichlet_profiles(seed + F, 2, F, 0.05, shared_frac=0.3)
         y = synth.labels_bernoulli(seed + F + 1, N)
@@ -598,18 +597,20 @@ def serve_ours(models, st, files_per_s, budget=4 << 30, slots=64):
     return r
 
 
-def serve_per_group_fp32(models, pool32, st, files_per_s, device):
-    """Baseline: one group at a time with plain FP32 storage -- H2D of the
-    group's FP32 rows, one nb_score_group call, D2H of the results, wait."""
+def serve_per_group(models, pool_h, dtype, st, files_per_s, device):
+    """Baseline: one group at a time -- H2D of the group's rows (plain FP32, or
+    the same u8 rows the server takes), one nb_score_group call with log
+    posteriors and the FP64 recheck, D2H of the results, wait for the stream."""
     import torch
 
     import paper_1905_13746_gb300 as nb
     nmax = int(st.sizes.max())
     cmax = max(SERVE_CLASSES)
-    xd = torch.empty((nmax, SERVE_F), dtype=torch.float32, device=device)
+    xd = torch.empty((nmax, SERVE_F), dtype=pool_h.dtype, device=device)
     ld = torch.empty(nmax, dtype=torch.uint8, device=device)
     md = torch.empty(nmax, dtype=torch.float32, device=device)
     pd = torch.empty(nmax * cmax, dtype=torch.float32, device=device)
+    nre = torch.zeros(len(st.sizes), dtype=torch.int64, device=device)
     stream = torch.cuda.Stream(device)
     clock = nb.Server.clock_us
     sched = st.arrivals(clock() + 2000.0, files_per_s)
@@ -622,10 +623,10 @@ def serve_per_group_fp32(models, pool32, st, files_per_s, device):
             n, mid = int(st.sizes[g]), int(st.mids[g])
             C = SERVE_CLASSES[mid]
             o = int(st.offs[g])
-            xd[:n].copy_(pool32[o:o + n], non_blocking=True)
-            nb.nb_score_group(models[mid].handle, xd.data_ptr(), nb.NB_F32, n, SERVE_F,
+            xd[:n].copy_(pool_h[o:o + n], non_blocking=True)
+            nb.nb_score_group(models[mid].handle, xd.data_ptr(), dtype, n, SERVE_F,
                               ld.data_ptr(), md.data_ptr(), pd.data_ptr(), want_logpost=True,
-                              stream=stream)
+                              stream=stream, n_rechecked=nre[g:].data_ptr())
             c0, cc = int(st.cum[g]), int(st.cumc[g])
             st.label[c0:c0 + n].copy_(ld[:n], non_blocking=True)
             st.margin[c0:c0 + n].copy_(md[:n], non_blocking=True)
@@ -634,7 +635,8 @@ def serve_per_group_fp32(models, pool32, st, files_per_s, device):
             lat[g] = clock() - sched[g]
         last = clock()
     return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
-            "files_per_s": st.files / ((last - first) * 1e-6)}
+            "files_per_s": st.files / ((last - first) * 1e-6),
+            "n_rechecked": int(nre.sum().item())}
 
 
 def run_serving(device, n_groups, loads, seed_off=0):
@@ -657,18 +659,24 @@ def run_serving(device, n_groups, loads, seed_off=0):
         out["loads"].append({"offered_frac": f, "offered_files_per_s": f * cap["files_per_s"],
                              "files_per_s": r["files_per_s"], "p50_ms": r["p50_us"] / 1e3,
                              "p99_ms": r["p99_us"] / 1e3})
+    # per-group baselines: the same kernels one group and one sync at a time,
+    # on the u8 rows the server takes and on plain FP32 rows
+    import paper_1905_13746_gb300 as nb
     pool32 = pool.to(torch.float32).pin_memory()
-    bcap = serve_per_group_fp32(models, pool32, st, None, device)
-    eq = 0.5 * bcap["files_per_s"]
-    b_eq = serve_per_group_fp32(models, pool32, st, eq, device)
-    o_eq = serve_ours(models, st, eq)
-    out["per_group_fp32"] = {
-        "capacity_files_per_s": bcap["files_per_s"],
-        "at_equal_load": {"offered_files_per_s": eq,
-                          "per_group_fp32": {"p50_ms": b_eq["p50_us"] / 1e3,
-                                             "p99_ms": b_eq["p99_us"] / 1e3},
-                          "server": {"p50_ms": o_eq["p50_us"] / 1e3,
-                                     "p99_ms": o_eq["p99_us"] / 1e3}}}
+    for name, ph, code in (("per_group_u8", pool, nb.NB_U8),
+                           ("per_group_fp32", pool32, nb.NB_F32)):
+        bcap = serve_per_group(models, ph, code, st, None, device)
+        eq = 0.5 * bcap["files_per_s"]
+        b_eq = serve_per_group(models, ph, code, st, eq, device)
+        o_eq = serve_ours(models, st, eq)
+        out[name] = {
+            "capacity_files_per_s": bcap["files_per_s"],
+            "n_rechecked_at_capacity": bcap["n_rechecked"],
+            "at_equal_load": {"offered_files_per_s": eq,
+                              name: {"p50_ms": b_eq["p50_us"] / 1e3,
+                                     "p99_ms": b_eq["p99_us"] / 1e3},
+                              "server": {"p50_ms": o_eq["p50_us"] / 1e3,
+                                         "p99_ms": o_eq["p99_us"] / 1e3}}}
     del pool32
     return out
 
@@ -676,7 +684,7 @@ def run_serving(device, n_groups, loads, seed_off=0):
 # ----------------------------------------------------------------------------
 # many-class workload: C = 64 classes, F = 8192 counts, N = 2M files
 # ----------------------------------------------------------------------------
-def run_many_class(args, device):
+def run_many_class(args, device, steps=None):
     """Fit on the 2:1 per-class split + score all N files on the tensor-core
     scorer (u8 counts, fixed-point limbs); the CUDA-core scorer of the same
     model and the plain FP32 path are timed on a subset beside it."""
@@ -704,8 +712,9 @@ def run_many_class(args, device):
         model = nb.fit(ftr, y_tr, C, stream=stream)
     stream.synchronize()
     out = _out(N, C, device)
+    steps = args.steps if steps is None else steps
     with ClockSampler(device.index or 0) as clk:
-        total, fit_ms, sc_ms, launches = time_steps(model, ftr, y_tr, fall, out, args.steps,
+        total, fit_ms, sc_ms, launches = time_steps(model, ftr, y_tr, fall, out, steps,
                                                     args.warmup, stream)
     n_rechecked = int(out["n_rechecked"].item())
     hbm_peak, peak_kind = _peaks()
@@ -752,8 +761,8 @@ def run_many_class(args, device):
                     f"(Dirichlet(0.1) profiles, lognormal(8.5, 1) totals, clamped at 255, "
                     f"stored u8); fit on the 2:1 split ({len(tr)} files) + score all N with "
                     f"log posteriors and FP64 recheck",
-        "steps": args.steps, "ms_per_step": total / args.steps,
-        "files_per_s": N / (total / args.steps * 1e-3),
+        "steps": steps, "ms_per_step": total / steps,
+        "files_per_s": N / (total / steps * 1e-3),
         "fit_ms": statistics.mean(fit_ms), "score_ms": sc,
         "score_files_per_s": N / (sc * 1e-3), "n_rechecked": n_rechecked,
         "roofline": {"bound": "ridge", "kernel": "k_score_tc",
@@ -932,6 +941,8 @@ def main():
                     help="variant,stages,rows_per_stage,rows_per_warp for the two-class "
                          "scorer instead of autotuning (e.g. 1,4,48,2)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the compact F-sweep and many-class legs of the default line")
     ap.add_argument("--serving-groups", type=int, default=4000)
     ap.add_argument("--fsweep", action="store_true",
                     help="print only the feature-count sweep (u8 / FP8 / FP32)")
@@ -1092,7 +1103,18 @@ def main():
     # ---- serving under Poisson arrivals (N = 1 only) ------------------------
     serving = None
     if ws == 1 and not args.no_serving:
-        serving = run_serving(device, args.serving_groups, [0.5, 0.9])
+        serving = run_serving(device, args.serving_groups, [0.25, 0.5, 0.75, 0.9])
+
+    # ---- the other benchmark workloads in compact form (N = 1 only) ---------
+    # feature-count sweep at F = 1,024 and 4,096 (u8 / FP8 / FP32 rows) and the
+    # C = 64, F = 8,192 many-class workload (tensor cores; CUDA-core and plain
+    # FP32 scorers on a subset beside it)
+    fsweep = many = None
+    if ws == 1 and not args.no_extra:
+        fsweep = run_fsweep(args, device, Fs=(1024, 4096))
+        torch.cuda.empty_cache()
+        many = run_many_class(args, device, steps=5)
+        torch.cuda.empty_cache()
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) -----------------
     cpu = None
@@ -1142,6 +1164,8 @@ def main():
                        "n_rechecked": p_rechecked},
         "e2e": e2e,
         "serving": serving,
+        "fsweep": fsweep,
+        "many_class": many,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "gpu_launches": launches,

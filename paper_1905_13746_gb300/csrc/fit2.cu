@@ -89,7 +89,8 @@ __device__ __forceinline__ void fit2_flush(uint32_t (&acc)[2][KV][NA], Fit2Hist<
   }
 }
 
-template <int DT, int KV, int NCW>
+// FULL: every lane's KV vectors lie inside the row (no bound or tail checks).
+template <int DT, int KV, int NCW, bool FULL>
 __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(const Fit2Args f, const PipeArgs p) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t full[kMaxStages], empty[kMaxStages], tabbar;
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
     vb = vb < 0 ? 0 : (vb > 4 ? 4 : vb);
     tm[q] = vb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * vb)) - 1u);
   }
-  const int tail_v = f.F < nv * EPV ? nv - 1 : -1;
+  const int tail_v = (!FULL && f.F < nv * EPV) ? nv - 1 : -1;
   uint32_t cnt0 = 0u, cnt1 = 0u;   // rows per class (lane 0); scalars, not an array indexed by c
   int since_flush = 0;
   bool dead = false;   // a wait ran out: skip to the common exit (the named barrier)
@@ -171,10 +172,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1) k_fit2_pipe(
 #pragma unroll
       for (int kv = 0; kv < KV; ++kv) {
         const int v = lane + 32 * kv;
-        if (v >= nv) continue;
+        if (!FULL && v >= nv) continue;
         const uint4 xv = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
         uint32_t w[4] = {xv.x, xv.y, xv.z, xv.w};
-        if (v == tail_v) {
+        if (!FULL && v == tail_v) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) w[q] &= tm[q];
         }
@@ -326,9 +327,9 @@ static nb_status launch_fit2_ovf(nb_model* m, const nb_aux* aux, const int32_t* 
   return NB_OK;
 }
 
-template <int DT, int KV, int kFitNCW>
+template <int DT, int KV, int kFitNCW, bool FULL>
 static nb_status run_fit2(const Fit2Args& f, const PipeArgs& p, int smem, cudaStream_t st) {
-  auto kern = k_fit2_pipe<DT, KV, kFitNCW>;
+  auto kern = k_fit2_pipe<DT, KV, kFitNCW, FULL>;
   if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(fit2)");
@@ -385,9 +386,14 @@ nb_status launch_fit2_pipe(nb_model* m, const void* X, nb_dtype dt, int64_t n, i
   const int smem = (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
   if (smem > 220 * 1024) return NB_EUNSUPPORTED;
   nb_status s = NB_EUNSUPPORTED;
-#define NB_FIT2_CASE(D, K)                                                \
-  if (dt == D && kv == K)                                                 \
-    s = ncw == 8 ? run_fit2<D, K, 8>(f, p, smem, st) : run_fit2<D, K, 12>(f, p, smem, st); \
+  // rows that fill every lane's vectors exactly take the branch-free kernel
+  const bool full = f.nvec_row == 32 * kv && (m->F * es) % 16 == 0;
+#define NB_FIT2_CASE(D, K)                                                              \
+  if (dt == D && kv == K)                                                               \
+    s = ncw == 8 ? (full ? run_fit2<D, K, 8, true>(f, p, smem, st)                      \
+                         : run_fit2<D, K, 8, false>(f, p, smem, st))                    \
+                 : (full ? run_fit2<D, K, 12, true>(f, p, smem, st)                     \
+                         : run_fit2<D, K, 12, false>(f, p, smem, st));                  \
   else
   NB_FIT2_CASE(NB_U8, 1) NB_FIT2_CASE(NB_U8, 2) NB_FIT2_CASE(NB_U8, 3) NB_FIT2_CASE(NB_U8, 4)
   NB_FIT2_CASE(NB_U16, 1) NB_FIT2_CASE(NB_U16, 2) NB_FIT2_CASE(NB_U16, 3)

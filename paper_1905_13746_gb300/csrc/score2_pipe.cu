@@ -59,7 +59,15 @@ __device__ __forceinline__ void finish_row(const S2Args& a, float hb, float inv_
   }
 }
 
-template <int DT, int KV, int RPW, int NCW>
+// mask of the first vb (clamped to 0..4) bytes of a 32-bit word
+__device__ __forceinline__ uint32_t u8_keep_mask(int vb) {
+  vb = vb < 0 ? 0 : (vb > 4 ? 4 : vb);
+  return vb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * vb)) - 1u);
+}
+
+// FULL: every lane's KV vectors lie inside the row (no bound or tail checks);
+// the kernel then carries no per-vector branches.
+template <int DT, int KV, int RPW, int NCW, bool FULL>
 __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
     k_score2_pipe(const S2Args a, const PipeArgs p) {
   constexpr int LPR = 32 / RPW;
@@ -104,26 +112,18 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
     if (DT == NB_U8) {
       const uint4* tab = reinterpret_cast<const uint4*>(sm);
       const uint4 z = make_uint4(0, 0, 0, 0);
-      q0[kv] = v < nv ? tab[v] : z;
-      q1[kv] = v < nv ? tab[nt + v] : z;
-      q2[kv] = v < nv ? tab[2 * nt + v] : z;
+      q0[kv] = (FULL || v < nv) ? tab[v] : z;
+      q1[kv] = (FULL || v < nv) ? tab[nt + v] : z;
+      q2[kv] = (FULL || v < nv) ? tab[2 * nt + v] : z;
     } else {
       const float4* tab = reinterpret_cast<const float4*>(sm);
 #pragma unroll
       for (int q = 0; q < QPV; ++q)
-        wq[kv][q] = v < nv ? tab[q * nt + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        wq[kv][q] = (FULL || v < nv) ? tab[q * nt + v] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   const signed char* limb = reinterpret_cast<const signed char*>(sm);   // u8 overflow limbs
-  const int keep = a.F * (16 / EPV) - 16 * (nv - 1);   // valid bytes of the last vector
-  uint32_t tm[4];
-#pragma unroll
-  for (int w = 0; w < 4; ++w) {
-    int vb = keep - 4 * w;
-    vb = vb < 0 ? 0 : (vb > 4 ? 4 : vb);
-    tm[w] = vb >= 4 ? 0xFFFFFFFFu : ((1u << (8 * vb)) - 1u);
-  }
-  const int tail_v = a.F < nv * EPV ? nv - 1 : -1;
+  const int tail_v = (!FULL && a.F < nv * EPV) ? nv - 1 : -1;
 
   RowSum res{0, 0, 0, 0u, 0.f, 0.f};
   long long rrow = -1;
@@ -161,10 +161,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 #pragma unroll
         for (int kv = 0; kv < KV; ++kv) {
           const int v = li + LPR * kv, e = kv & 1;
-          if (v < nv) {
+          if (FULL || v < nv) {
             uint4 x = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
-            if (v == tail_v) {
-              x.x &= tm[0]; x.y &= tm[1]; x.z &= tm[2]; x.w &= tm[3];
+            if (!FULL && v == tail_v) {   // zero the bytes past F (masks made here: rare)
+              const int keep = a.F - 16 * (nv - 1);   // valid bytes of the last vector
+              x.x &= u8_keep_mask(keep);
+              x.y &= u8_keep_mask(keep - 4);
+              x.z &= u8_keep_mask(keep - 8);
+              x.w &= u8_keep_mask(keep - 12);
             }
             c0[e] = dp4a_us(x.x, q0[kv].x, c0[e]);
             c1[e] = dp4a_us(x.x, q1[kv].x, c1[e]);
@@ -209,11 +213,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 #pragma unroll
         for (int kv = 0; kv < KV; ++kv) {
           const int v = li + LPR * kv;
-          if (v < nv) {
+          if (FULL || v < nv) {
             const uint4 x = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
             float val[EPV];
             Dec::run(x, val);
-            if (v == tail_v) {
+            if (!FULL && v == tail_v) {
 #pragma unroll
               for (int e = 0; e < EPV; ++e)
                 if (v * EPV + e >= a.F) val[e] = 0.f;
@@ -268,9 +272,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 // launcher: NB_EUNSUPPORTED when the row does not fit (the caller then uses
 // the register-streaming kernel)
 // ---------------------------------------------------------------------------
-template <int DT, int KV, int RPW, int NCW>
+template <int DT, int KV, int RPW, int NCW, bool FULL>
 static nb_status run_pipe(const S2Args& a, const PipeArgs& p, int smem, cudaStream_t st) {
-  auto kern = k_score2_pipe<DT, KV, RPW, NCW>;
+  auto kern = k_score2_pipe<DT, KV, RPW, NCW, FULL>;
   if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(pipe)");
@@ -336,8 +340,12 @@ nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_
   // accumulators, the lane-group butterfly, the weight and final roundings
   S2Args ak = a;
   ak.k_base = kv * ((16 / elem_size(dt)) / 4) + 2 + (rpw == 2 ? 4 : 5) + 2;
-#define NB_PIPE_CASE(D, K, R, N) \
-  if (dt == D && kv == K && rpw == R && ncw == N) return run_pipe<D, K, R, N>(ak, p, smem, st);
+  // rows that fill every lane's vectors exactly take the branch-free kernel
+  const bool full = a.nvec_row == kv * lpr && (a.F * elem_size(dt)) % 16 == 0;
+#define NB_PIPE_CASE(D, K, R, N)                                               \
+  if (dt == D && kv == K && rpw == R && ncw == N)                              \
+    return full ? run_pipe<D, K, R, N, true>(ak, p, smem, st)                  \
+                : run_pipe<D, K, R, N, false>(ak, p, smem, st);
 #define NB_PIPE_DT(D)                                                                        \
   NB_PIPE_CASE(D, 1, 1, 8) NB_PIPE_CASE(D, 2, 1, 8) NB_PIPE_CASE(D, 3, 1, 12)                 \
   NB_PIPE_CASE(D, 4, 1, 12) NB_PIPE_CASE(D, 1, 2, 12) NB_PIPE_CASE(D, 2, 2, 12)               \
