@@ -307,7 +307,7 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
                                     g.X, g.n, b->F, g.ld);
       if (ms != NB_OK) return ms;
     }
-    tiles[f] += f == 0 ? (g.n + rs - 1) / rs : (f == 1 ? (g.n + 63) / 64 : (g.n + 127) / 128);
+    tiles[f] += f == 0 ? (g.n + rs - 1) / rs : (f == 1 ? (g.n + 63) / 64 : (g.n + 255) / 256);
     chunks[f] += (g.n + 31) / 32;
   }
   for (int f = 0; f < kFamilies; ++f) {

@@ -4,37 +4,50 @@
 // theta_cj and takes the class of largest posterior.  With the centred table
 // w_cj = log theta_cj - mean_c log theta_cj (the per-feature shift is common to
 // all classes and cancels in the label, the margin and the log posteriors)
-// the scores of a tile of 128 files against C <= 64 classes are one dense
-// contraction S = X W^T, done here with tcgen05.mma (kind::f16, FP32
-// accumulators in tensor memory).
+// the scores of 128 files against C <= 64 classes are one dense contraction
+// S = X W^T, done here with tcgen05.mma (kind::f16, FP32 accumulators in
+// tensor memory).
 //
 // Exactness.  The weights are held in fixed point, Q_cj = round(w_cj 2^S)
 // with |Q| <= 2^22, split into three balanced limbs Q = q0 + 2^8 q1 + 2^16 q2
 // with |q_l| <= 128, each an exact FP16 integer.  Stored u8 counts (0..255)
-// are exact FP16 integers as well, so every product is exact and every
-// partial sum of one limb over 512 features is an integer of magnitude below
-// 255 * 512 * 128 < 2^24: the FP32 accumulator holds it exactly, whatever the
-// order of the tensor core's additions.  Every 512 features the accumulators
-// are drained and the limbs joined into one exact int64 sum per class, kept in
-// tensor memory next to the two accumulator buffers (2 x 192 + 128 columns);
-// overflow-list entries (counts above 255) are added exactly on the CUDA cores.
-// The only errors are the weight quantisation, at most T 2^-(S+1) with T the
-// file's token count, and two FP32 roundings when the score is formed; the
-// epilogue bounds both and marks the row for the FP64 recheck when the bound
-// does not settle the label (or the log posteriors).
+// are exact FP16 integers as well, so every product is exact, and a limb's
+// sum over a row stays an integer below 2^24 -- exact in the FP32 accumulator
+// whatever the order of the tensor core's additions -- when the row holds
+// fewer than 2^17 stored counts.  Overflow-list entries (counts above 255) are
+// added exactly on the CUDA cores.  The only errors are the weight
+// quantisation, at most T 2^-(S+1) with T the file's token count, and two FP32
+// roundings when the score is formed; the epilogue bounds both and marks the
+// row for the FP64 recheck when the bound does not settle the label (or the
+// log posteriors).
 //
+// Data flow.  The operand A (the files' counts as FP16) lives in tensor
+// memory: the rows arrive in shared memory by 2-D tensor TMA (128 rows x 128
+// bytes per box, 128-byte swizzle, zero fill past the last row and feature),
+// converter warps read their rows' bytes, convert them and store them with
+// tcgen05.st, so the MMA reads only the weight operand B from shared memory.
+// One weight stage (3 C_p limb rows x 64 features, one bulk copy) feeds the
+// MMAs of two 128-file tiles, which halves the weight traffic per file.
+//
+// Two launches of one kernel:
+//   pass "pair"    units of 256 files (two 128-file tiles sharing each weight
+//                  stage), one FP32 accumulation per row in tensor memory
+//                  (2 x 192 columns) plus a ring of two A stages (128
+//                  columns); rows of 2^17 or more stored counts could have
+//                  rounded and are put on a list of heavy rows;
+//   pass "chunked" units of 128 listed heavy rows (read by the converter warps
+//                  straight from global memory), accumulated in 512-feature
+//                  chunks (255 * 512 * 128 < 2^24: always exact) and joined in
+//                  exact int64 sums in tensor memory (2 columns per class).
 // Roles of one persistent CTA per SM (608 threads):
-//   warps 0-15  convert u8 rows to FP16 operand tiles (four warps per tensor-
-//               memory lane quadrant), drain the accumulators, run the
-//               epilogue (arg-max, top-2 margin, log-sum-exp), 16 classes each;
-//   warp 16     streams each tile's rows into shared memory (2-D tensor TMA,
-//               128 rows x 128 features per box, 128-byte swizzle, zero fill
-//               past the last row and feature);
+//   warps 0-15  convert rows to FP16 A stages, then run the epilogue (drain,
+//               arg-max, top-2 margin, log-sum-exp, log posteriors);
+//   warp 16     streams the weight-limb stages (one bulk copy each into this
+//               CTA's own shared memory);
 //   warp 17     allocates tensor memory and issues the MMAs (one thread);
-//   warp 18     streams the weight-limb stages (one bulk copy per stage into
-//               this CTA's own shared memory).
+//   warp 18     streams the rows of the pair pass (tensor TMA).
 // Every wait is bounded; a wait that runs out raises ST_TIMEOUT, all roles
-// stop, outstanding copies and MMAs are waited for, and tensor memory is freed.
+// stop, issued MMAs are waited for, and tensor memory is freed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -48,25 +61,40 @@
 namespace nbg {
 
 constexpr int TC_M = 128;                  // files per tile (tensor-memory lanes)
-constexpr int TC_KS = 64;                  // features per MMA stage (4 MMAs, K = 16)
-constexpr int TC_KR = 128;                 // features per row stage (one TMA box)
-constexpr int TC_BOX = 128;                // features per TMA box (128-byte swizzle span)
-constexpr uint32_t TC_RAW_BYTES = TC_M * TC_KR;   // 16 KB
-constexpr int TC_CHUNK = 8;                // MMA stages per chunk of the exact mode
-constexpr float TC_T_EXACT = 131072.f;     // 128 T < 2^24: one accumulator is exact
-constexpr int TC_REDO_CAP = 64;            // tiles a CTA can queue for the exact pass
-constexpr int TC_PF = 6;                   // row stages prefetched into L2 ahead of the loads
-constexpr int TC_NAB = 4;                  // operand stages
-constexpr int TC_MAX_RAW = 4;              // row stages
-constexpr int TC_ACC_COLS = 192;           // tensor-memory columns per FP32 accumulator
-constexpr int TC_SUM_COL = 2 * TC_ACC_COLS; // exact int64 sums: 2 columns per class
-constexpr int TC_WORK = 16;                // converter / epilogue warps (4 per lane quadrant)
-constexpr int TC_PARTS = TC_WORK / 4;      // class parts per row
-constexpr int TC_CLS = 16;                 // classes per part (kTcMaxC = TC_PARTS * TC_CLS)
+constexpr int TC_KS = 64;                  // features per stage (4 MMAs, K = 16)
+constexpr int TC_NB = 5;                   // weight stages in shared memory
+constexpr int TC_ACC = 192;                // tensor-memory columns per FP32 accumulator
+constexpr int TC_ACOL = 384;               // first A column (128 columns of A stages)
+constexpr int TC_SUMCOL = 192;             // chunked pass: int64 sums, 2 columns per class
+constexpr int TC_CHUNK = 8;                // stages per chunk of the chunked pass
+constexpr float TC_T_EXACT = 131072.f;     // 128 T < 2^24: one accumulation is exact
+constexpr int TC_WORK = 16;                // converter / epilogue warps
 constexpr int TC_THREADS = (TC_WORK + 3) * 32;
-constexpr int TC_LAG = 2;                  // stages converted before a drain
+constexpr int TC_BOX = 128;                // features per TMA box (128-byte swizzle span)
+constexpr int TC_NRAW = 2;                 // row stages in shared memory (pair pass)
+constexpr uint32_t TC_RAW_BYTES = 2 * TC_M * TC_BOX;   // both tiles, 128 features
+constexpr int TC_PD = 3;                   // row stages loaded ahead into registers
 constexpr long long TC_WAIT = 2000000000LL;
-constexpr uint32_t TC_A_BYTES = TC_M * TC_KS * 2;   // 16 KB
+constexpr int kTcHeavyCap = 262144;        // heavy rows one call redoes exactly
+
+// Per-pass constants: H tiles per unit (two in the pair pass), P class parts
+// per row (the 16 warps cover H x 4 lane quadrants x P parts), BPT bytes of
+// its row each converter thread converts per A stage, KA features per A
+// stage, NA A stages in the 128 A columns of tensor memory.
+template <int MODE>
+struct TcPass {
+  static constexpr int H = MODE == 0 ? 2 : 1;
+  static constexpr int P = 4 / H;
+  static constexpr int BPT = MODE == 0 ? 32 : 16;  // bytes per thread per A stage
+  static constexpr int NV = BPT / 16;              // 16-byte vectors per thread per A stage
+  static constexpr int COLS = BPT / 2;             // A columns per thread per A stage
+  static constexpr int KA = BPT * P;               // features per A stage
+  static constexpr int SUB = TC_KS / KA;           // A stages per weight stage
+  static constexpr int ACOLS = KA / 2;             // A columns per tile per A stage
+  static constexpr int NA = 128 / (ACOLS * H);     // A stages in the 128 A columns
+  static constexpr int CPP = kTcMaxC / P;          // classes per part
+  static constexpr int ROWS = TC_M * H;            // files per unit
+};
 
 struct TcModelArg {
   const uint8_t* wlay;
@@ -77,57 +105,56 @@ struct TcModelArg {
 };
 
 struct TcArgs {
-  CUtensorMap tmap;         // u8 rows of the group (single-group launch)
+  CUtensorMap tmap;         // u8 rows of g0 (single-group launch)
   const CUtensorMap* maps;  // group list: one map per group (device), else nullptr
   const SegGroup* groups;   // group list on the device, or nullptr: g0 alone
-  const SegHeader* hdr;     // its header (tiles = 128-row tiles of the list)
+  const SegHeader* hdr;     // its header (tiles = 256-row units of the list)
   SegGroup g0;
-  long long tiles0;
+  long long units0;         // 256-row units of g0
   TcModelArg models[kSegMaxModels];
-  int F, nks, nraw, want_lp, recheck;
-  int single;               // 1: one accumulation per row, heavy rows redone exactly
-  uint32_t b_bytes;         // bytes of one weight stage (largest model)
+  int F, nks, want_lp, recheck;
+  int pf;                   // stages between the L2 prefetch of a row's bytes and their load
+  uint32_t b_bytes;         // bytes of one weight stage slot (largest model)
+  long long* heavy;         // pair pass: rows of 2^17+ stored counts (g0 only), or nullptr
+  unsigned long long* heavy_n;   // their count (may exceed heavy_cap)
+  int heavy_cap;
   int* status;
 };
 
-struct TcXch {               // partial epilogue results of each class part and row
-  float best[TC_PARTS][TC_M], second[TC_PARTS][TC_M], se[TC_PARTS][TC_M];
-  float smax[TC_PARTS][TC_M], bmax[TC_PARTS][TC_M], T[TC_PARTS][TC_M], Tplane[TC_PARTS][TC_M];
-  int idx[TC_PARTS][TC_M];
+struct TcXch {               // partial epilogue results of each class part and row:
+                             // entry part * rows-per-unit + row
+  float best[512], second[512], se[512];
+  float emax[512], T[512], Tplane[512];
+  int idx[512];
 };
 
 struct TcShared {
-  uint64_t raw_full[TC_MAX_RAW], raw_empty[TC_MAX_RAW];
-  uint64_t b_full[TC_NAB], a_full[TC_NAB], ab_empty[TC_NAB];
-  uint64_t acc_full[2], acc_empty[2], fin, redo_ready;
+  uint64_t raw_full[TC_NRAW], raw_empty[TC_NRAW];
+  uint64_t b_full[TC_NB], b_empty[TC_NB];
+  uint64_t a_full[4], a_empty[4];
+  uint64_t acc_full, acc_empty, fin;
   uint64_t xfull, xfree;        // exchange written by all parts / read by all parts
   uint32_t tmem;
   int abort;
-  int redo_flag[2];
-  int redo_n;                   // tiles queued for the exact pass (phase 1)
-  int redo_list[TC_REDO_CAP];
 };
 
-struct TcTile {
-  long long row0;
-  int nr, g;
+struct TcUnit {
+  long long row0;   // first row of the unit within its group (pair pass)
+  int g;            // group
+  long long n;      // rows of the group
 };
 
 __device__ __forceinline__ const SegGroup& tc_group(const TcArgs& a, int g) {
   return a.groups ? a.groups[g] : a.g0;
 }
 
-__device__ __forceinline__ TcTile tc_tile(const TcArgs& a, int n_groups, long long t) {
+// unit t of the pair pass: group and first row
+__device__ __forceinline__ TcUnit tc_unit(const TcArgs& a, int n_groups, long long t) {
   int g = 0;
   if (a.groups && n_groups > 1)
     g = seg_find(n_groups, t, [&](int i) { return a.groups[i].tile0; });
   const SegGroup& G = tc_group(a, g);
-  TcTile r;
-  r.g = g;
-  r.row0 = (t - G.tile0) * TC_M;
-  const long long left = G.n - r.row0;
-  r.nr = (int)(left <= 0 ? 0 : (left < TC_M ? left : TC_M));
-  return r;
+  return TcUnit{(t - G.tile0) * 256, g, G.n};
 }
 
 __device__ __forceinline__ uint4 lds16(uint32_t addr) {
@@ -137,12 +164,6 @@ __device__ __forceinline__ uint4 lds16(uint32_t addr) {
                : "r"(addr)
                : "memory");
   return v;
-}
-
-__device__ __forceinline__ void sts16(uint32_t addr, const uint4& v) {
-  asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-               "r"(v.w)
-               : "memory");
 }
 
 // two u8 counts (bytes picked by sel) -> two exact FP16 values: 1024 + b is
@@ -163,15 +184,15 @@ __device__ __forceinline__ bool tc_wait_sleep(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+__device__ __forceinline__ bool tc_aborted(TcShared& sh) {
+  return *reinterpret_cast<volatile int*>(&sh.abort) != 0;
+}
+
 __device__ __forceinline__ bool tc_wait(TcShared& sh, uint64_t* bar, uint32_t parity, int* status) {
   if (tc_wait_sleep(bar, parity)) return true;
   atomicOr(status, ST_TIMEOUT);
   *reinterpret_cast<volatile int*>(&sh.abort) = 1;
   return false;
-}
-
-__device__ __forceinline__ bool tc_aborted(TcShared& sh) {
-  return *reinterpret_cast<volatile int*>(&sh.abort) != 0;
 }
 
 // every lane waits (each observes the phase, so each may read what it
@@ -187,302 +208,350 @@ __device__ __forceinline__ bool tc_wait_warp(TcShared& sh, uint64_t* bar, uint32
   return all;
 }
 
-struct TcDrain {
-  long long row0;
-  uint32_t T;
-  int trigger;
-  int nr, g, tile;
-  int bits;        // accumulator buffer | phase << 1 | last chunk of the tile << 2
-};
-
-// score of class c from its exact sum q: q = hi 2^24 + lo exactly, one
-// rounding to FP32, one in the FMA with the prior
-__device__ __forceinline__ float tc_score(uint32_t lo, uint32_t hi, float scale, float b) {
-  const long long q = (long long)(((unsigned long long)hi << 32) | lo);
-  const float v = fmaf((float)(int)(q >> 24), 16777216.f, (float)(int)(q & 0xFFFFFF));
-  return fmaf(v, scale, b);
+// D[tmem] (+)= A[tmem] * B[smem]^T, issued by one thread (A: 128 lanes = rows,
+// two FP16 values of consecutive features per 32-bit column)
+__device__ __forceinline__ void tc_mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
-// Epilogue of a tile: the thread's exact sums stay in its tensor-memory lane
-// until it starts its next tile, so they are read twice, 8 classes at a time
-// (pass 1: arg-max, second best and sum of exponentials; pass 2: log
-// posteriors), which keeps the epilogue's registers small.
-__device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch* xch,
-                                            long long row0, int nr, int g, int tile,
-                                            bool check_heavy, uint32_t Tpart,
-                                            int qd, int part, int lane, uint32_t tmem,
-                                            int& ep) {
-  const int r = 32 * qd + lane;
-  const int F = a.F;
-  const int c0 = TC_CLS * part;
-  const SegGroup& G = tc_group(a, g);
-  const TcModelArg& M = a.models[G.model];
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
-  const long long gr = row0 + r;
-  const bool valid = r < nr;
-  long long k0 = 0, k1 = 0;
-  if (valid && G.ovf_ptr) {
-    k0 = G.ovf_ptr[gr];
-    k1 = G.ovf_ptr[gr + 1];
-  }
-  const float scale = M.hdr->scale, tau_unit = M.hdr->tau_unit;
-  float T = (float)Tpart;
-  // overflow entries (counts above 255) join the sums exactly (rare path)
-  if (__any_sync(0xFFFFFFFFu, k1 > k0)) {
-#pragma unroll 1
-    for (int hh = 0; hh < 2; ++hh) {
-      const int cb = c0 + 8 * hh;
-      if (cb >= M.Cp) break;
-      uint32_t sw[16];
-      const uint32_t addr = lane_base + (uint32_t)(TC_SUM_COL + 2 * cb);
-      tmem_ld16(addr, sw);
-      tmem_ld_wait();
-#pragma unroll 1
-      for (long long k = k0; k < k1; ++k) {
-        const int j = G.ovf_col[k];
-        if (j >= F) continue;
-        const long long add = G.ovf_add[k];
-        if (part == 0 && hh == 0) T += (float)add;
+
+// ---------------------------------------------------------------------------
+// epilogue
+// ---------------------------------------------------------------------------
+// Exact fixed-point sums of classes cb .. cb+7 of this thread's row from the
+// int64 sums of the chunked pass (warp-uniform arguments: the tensor-memory
+// loads are warp-wide).
+__device__ __forceinline__ void tc_load_sums8(uint32_t lane_base, int cb, long long (&q)[8]) {
+  uint32_t sw[16];
+  tmem_ld16(lane_base + (uint32_t)(TC_SUMCOL + 2 * cb), sw);
+  tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (cb + i >= M.C) break;
-          unsigned long long x = ((unsigned long long)sw[2 * i + 1] << 32) | sw[2 * i];
-          x += (unsigned long long)(add * M.q[(long long)(cb + i) * F + j]);
-          sw[2 * i] = (uint32_t)x;
-          sw[2 * i + 1] = (uint32_t)(x >> 32);
-        }
-      }
-      __syncwarp();   // the lanes' overflow loops differ in length
-      tmem_st16(addr, sw);
-      tmem_st_wait();
-    }
-  }
-  // pass 1
-  float best = -INFINITY, second = -INFINITY, smax = 0.f, bmax = 0.f, se = 0.f;
-  int bidx = 0x7FFFFFFF;
-#pragma unroll 1
-  for (int hh = 0; hh < 2; ++hh) {
-    const int cb = c0 + 8 * hh;
-    if (cb >= M.Cp) break;
-    uint32_t sw[16];
-    tmem_ld16(lane_base + (uint32_t)(TC_SUM_COL + 2 * cb), sw);
+  for (int i = 0; i < 8; ++i)
+    q[i] = (long long)(((unsigned long long)sw[2 * i + 1] << 32) | sw[2 * i]);
+}
+
+// The exact limb sums of classes cb .. cb+7 of tile h (FP32 integers of the
+// pair pass), q[i] = a0 + 2^8 a1 + 2^16 a2, one limb at a time.
+__device__ __forceinline__ void tc_load_acc8(uint32_t lane_base, int h, int Cp, int cb,
+                                             long long (&q)[8]) {
+  const uint32_t acc = lane_base + (uint32_t)(TC_ACC * h + cb);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    uint32_t v[8];
+    tmem_ld8(acc + (uint32_t)(l * Cp), v);
     tmem_ld_wait();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int c = cb + i;
-      if (c >= M.C) break;
-      const float b = M.bias[c];
-      const float sc = tc_score(sw[2 * i], sw[2 * i + 1], scale, b);
-      smax = fmaxf(smax, fabsf(sc));
-      bmax = fmaxf(bmax, fabsf(b));
-      if (sc > best) {            // running sum of exp(s - best)
-        se = se * expf(best - sc) + 1.f;
-        second = best;
-        best = sc;
-        bidx = c;
-      } else {
-        se += expf(sc - best);
-        if (sc > second) second = sc;
-      }
+      const long long x = (long long)__float2int_rn(__uint_as_float(v[i])) << (8 * l);
+      q[i] = l == 0 ? x : q[i] + x;
     }
   }
-  TcXch& xe = *xch;
+}
+
+// Scores s of classes cb .. cb+7 of this thread's row, and per class e = the
+// sum of the magnitudes of the prior and of every rounded FP32 result on the
+// way (each rounding is within 2^-24 of its result, the prior's within 2^-24
+// of itself).  Pair pass: s = ((a0 sc + b) + a1 2^8 sc) + a2 2^16 sc from the
+// exact FP32 limb sums (sc = 2^-S: the products are exact, each FMA rounds
+// once), then + (float)(overflow sum) sc.  Chunked pass: the exact int64 sum
+// q (overflow entries included) is rounded once to FP32 and enters one FMA
+// with the prior.  `added` receives the overflow entries' counts.
+template <int MODE>
+__device__ __forceinline__ void tc_scores8(const SegGroup& G, const TcModelArg& M, int F,
+                                           uint32_t lane_base, int h, int cb, bool any_ovf,
+                                           long long k0, long long k1, float (&s)[8],
+                                           float (&e)[8], float& added) {
+  const float sc = M.hdr->scale;
+  added = 0.f;
+  if (MODE == 0) {
+    // the three limbs' loads in flight together, one wait
+    const uint32_t acc = lane_base + (uint32_t)(TC_ACC * h + cb);
+    uint32_t v[3][8];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) tmem_ld8(acc + (uint32_t)(l * M.Cp), v[l]);
+    float b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = cb + i < M.C ? M.bias[cb + i] : 0.f;
+    tmem_ld_wait();
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const float w = sc * (float)(1 << (8 * l));
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        s[i] = fmaf(__uint_as_float(v[l][i]), w, l == 0 ? b[i] : s[i]);
+        e[i] = (l == 0 ? fabsf(b[i]) : e[i]) + fabsf(s[i]);
+      }
+    }
+  } else {
+    long long q[8];
+    tc_load_sums8(lane_base, cb, q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float b = cb + i < M.C ? M.bias[cb + i] : 0.f;
+      const float v = fmaf((float)(int)(q[i] >> 24), 16777216.f, (float)(int)(q[i] & 0xFFFFFF));
+      s[i] = fmaf(v, sc, b);
+      e[i] = fabsf(b) + fabsf(v * sc) + fabsf(s[i]);
+    }
+  }
+  if (any_ovf) {   // overflow entries (counts above 255): exact int64 sums per class
+#pragma unroll 1
+    for (long long k = k0; k < k1; ++k) {
+      const int j = G.ovf_col[k];
+      if (j < F) added += (float)G.ovf_add[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (cb + i >= M.C) break;
+      long long o = 0;
+#pragma unroll 1
+      for (long long k = k0; k < k1; ++k) {
+        const int j = G.ovf_col[k];
+        if (j < F) o += (long long)G.ovf_add[k] * (long long)M.q[(long long)(cb + i) * F + j];
+      }
+      // the sum joins the score with two roundings (the conversion, the add)
+      const float t = (float)o * sc;
+      const float si = s[i] + t;
+      e[i] += fabsf(t) + fabsf(si);
+      s[i] = si;
+    }
+  }
+}
+
+// Epilogue of one row for this thread's class part: pass 1 (arg-max, second
+// best, sum of exponentials) over the part's classes, exchange with the other
+// parts through shared memory, label / margin / recheck mark by part 0, pass 2
+// (log posteriors, the scores formed again).  grow < 0: a row past the end
+// (every lane still runs the warp-wide tensor-memory loads).
+template <int MODE>
+__device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch& xe,
+                                            const SegGroup& G, const TcModelArg& M,
+                                            long long grow, int xr, int h, int part,
+                                            uint32_t Tpart, uint32_t lane_base, int& ep) {
+  using PS = TcPass<MODE>;
+  const int lane = threadIdx.x & 31;
+  const bool valid = grow >= 0;
+  const int F = a.F;
+  const int c0 = PS::CPP * part;
+  long long k0 = 0, k1 = 0;
+  if (valid && G.ovf_ptr) {
+    k0 = G.ovf_ptr[grow];
+    k1 = G.ovf_ptr[grow + 1];
+  }
+  const bool any_ovf = __any_sync(0xFFFFFFFFu, k1 > k0);
+  const float tau_unit = M.hdr->tau_unit;
+  float T = (float)Tpart;
+  // pass 1
+  float best = -INFINITY, second = -INFINITY, emax = 0.f, se = 0.f;
+  int bidx = 0x7FFFFFFF;
+#pragma unroll 1
+  for (int cb = c0; cb < c0 + PS::CPP; cb += 8) {
+    if (cb >= M.Cp) break;
+    float sc[8], er[8], added;
+    tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
+    if (part == 0 && cb == c0) T += added;
+    // the chunk's best, second best and sum of exp(s - chunk best), in class
+    // order (ties keep the lower index); the exponentials are independent
+    float b8 = -INFINITY, s8b = -INFINITY;
+    int i8 = 0x7FFFFFFF;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (cb + i >= M.C) break;
+      emax = fmaxf(emax, er[i]);
+      if (sc[i] > b8) {
+        s8b = b8;
+        b8 = sc[i];
+        i8 = cb + i;
+      } else if (sc[i] > s8b) {
+        s8b = sc[i];
+      }
+    }
+    float e8 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (cb + i < M.C) e8 += expf(sc[i] - b8);
+    // merge into the running values (sum of exp(s - best))
+    if (b8 > best) {
+      se = se * expf(best - b8) + e8;
+      second = fmaxf(best, s8b);
+      best = b8;
+      bidx = i8;
+    } else {
+      se += e8 * expf(b8 - best);
+      second = fmaxf(second, b8);
+    }
+  }
   const int eph = ep & 1;
-  // the exchange of the previous tile must have been read by every part
+  // the exchange of the previous row set must have been read by every part
   if (!tc_wait_warp(sh, &sh.xfree, (uint32_t)eph ^ 1u, a.status)) return false;
-  // the flag of the next tile of the other parity is free once xfull passes
-  if (r == 0 && part == 0) sh.redo_flag[eph ^ 1] = 0;
-  xe.best[part][r] = best;
-  xe.second[part][r] = second;
-  xe.se[part][r] = se;
-  xe.smax[part][r] = smax;
-  xe.bmax[part][r] = bmax;
-  xe.T[part][r] = T;
-  xe.Tplane[part][r] = (float)Tpart;
-  xe.idx[part][r] = bidx;
+  xe.best[part * PS::ROWS + xr] = best;
+  xe.second[part * PS::ROWS + xr] = second;
+  xe.se[part * PS::ROWS + xr] = se;
+  xe.emax[part * PS::ROWS + xr] = emax;
+  xe.T[part * PS::ROWS + xr] = T;
+  xe.Tplane[part * PS::ROWS + xr] = (float)Tpart;
+  xe.idx[part * PS::ROWS + xr] = bidx;
   __syncwarp();
   if (lane == 0) mbar_arrive(&sh.xfull);
   if (!tc_wait_warp(sh, &sh.xfull, (uint32_t)eph, a.status)) return false;
   ++ep;
-  // combine the parts in class order (ties go to the lower class index); every
-  // lane stays to the end, since the tensor-memory loads below need the warp
-  // converged, and only rows of the tile store results
-  float Bv = -INFINITY, S2 = -INFINITY, sm = 0.f, bm = 0.f, Tt = 0.f, Tp = 0.f;
+  // combine the parts in class order (ties go to the lower class index)
+  float Bv = -INFINITY, S2 = -INFINITY, em = 0.f, Tt = 0.f, Tp = 0.f;
   int Bi = 0x7FFFFFFF;
-#pragma unroll 1
-  for (int k = 0; k < TC_PARTS; ++k) {
-    const float xb = xe.best[k][r];
-    Tp += xe.Tplane[k][r];
+#pragma unroll
+  for (int k = 0; k < PS::P; ++k) {
+    const float xb = xe.best[k * PS::ROWS + xr];
+    Tp += xe.Tplane[k * PS::ROWS + xr];
     if (xb > Bv) {
-      S2 = fmaxf(Bv, xe.second[k][r]);
+      S2 = fmaxf(Bv, xe.second[k * PS::ROWS + xr]);
       Bv = xb;
-      Bi = xe.idx[k][r];
+      Bi = xe.idx[k * PS::ROWS + xr];
     } else {
       S2 = fmaxf(S2, xb);
     }
-    sm = fmaxf(sm, xe.smax[k][r]);
-    bm = fmaxf(bm, xe.bmax[k][r]);
-    Tt += xe.T[k][r];
+    em = fmaxf(em, xe.emax[k * PS::ROWS + xr]);
+    Tt += xe.T[k * PS::ROWS + xr];
   }
   float sum = 0.f;
-#pragma unroll 1
-  for (int k = 0; k < TC_PARTS; ++k) {
-    const float xs = xe.se[k][r];
-    if (xs > 0.f) sum += xs * expf(xe.best[k][r] - Bv);
+#pragma unroll
+  for (int k = 0; k < PS::P; ++k) {
+    const float xs = xe.se[k * PS::ROWS + xr];
+    if (xs > 0.f) sum += xs * expf(xe.best[k * PS::ROWS + xr] - Bv);
   }
   __syncwarp();
-  if (lane == 0) mbar_arrive(&sh.xfree);   // this tile's exchange is read
+  if (lane == 0) mbar_arrive(&sh.xfree);   // this row set's exchange is read
   const float lse = Bv + logf(sum);
   const float margin = Bv - S2;
-  // |s_c - exact| <= T 2^-(S+1) (weight quantisation) + 2^-23 (|s| + |b|) (the
-  // FP32 roundings of the score and of the prior); two classes form the margin
-  const float tau =
-      2.f * Tt * tau_unit * (1.f + 1.f / 1048576.f) + 2.3841858e-7f * (sm + bm) + 1e-30f;
+  // |s_c - exact| <= T 2^-(S+1) (weight quantisation) + 2^-24 e_c (FP32
+  // roundings); two classes form the margin
+  const float tau = 2.f * (Tt * tau_unit + 5.9604645e-8f * em) * (1.f + 1.f / 1048576.f) + 1e-30f;
   bool flag = false;
   if (a.recheck != NB_RECHECK_OFF) {
     flag = !(margin > tau);
     if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
   }
-  // A row of 2^17 or more stored counts may have rounded in the single
-  // accumulation: it is marked for the FP64 recheck and its tile queued for the
-  // exact (chunked) pass, which overwrites the tile's results.
-  const bool heavy = check_heavy && !(Tp < TC_T_EXACT);
+  // pair pass: a row of 2^17 or more stored counts may have rounded in its
+  // single accumulation: marked, and listed for the chunked pass (beyond the
+  // list's capacity, or in a batch, the FP64 recheck resolves it)
+  const bool heavy = MODE == 0 && !(Tp < TC_T_EXACT);
   if (valid && part == 0) {
-    G.label[gr] = (flag || heavy) ? kLabelRecheck : (uint8_t)Bi;
-    G.margin[gr] = margin;
-    if (heavy && atomicExch(&sh.redo_flag[eph], 1) == 0) {
-      const int k = atomicAdd(&sh.redo_n, 1);
-      if (k < TC_REDO_CAP) sh.redo_list[k] = tile;   // beyond: the FP64 recheck
+    G.label[grow] = (flag || heavy) ? kLabelRecheck : (uint8_t)Bi;
+    G.margin[grow] = margin;
+    if (heavy && a.heavy) {
+      const unsigned long long k = atomicAdd(a.heavy_n, 1ull);
+      if (k < (unsigned long long)a.heavy_cap) a.heavy[k] = grow;
     }
   }
   if (a.want_lp && G.logpost) {
-    // pass 2
-    float* lp = G.logpost + (valid ? gr : 0) * M.C;
+    // pass 2; a full chunk of 8 classes goes out as two 16-byte stores when the
+    // row's log posteriors are 16-byte aligned
+    float* lp = G.logpost + (valid ? grow : 0) * M.C;
+    const bool vec = (reinterpret_cast<uintptr_t>(lp) & 15) == 0;
 #pragma unroll 1
-    for (int hh = 0; hh < 2; ++hh) {
-      const int cb = c0 + 8 * hh;
+    for (int cb = c0; cb < c0 + PS::CPP; cb += 8) {
       if (cb >= M.Cp) break;
-      uint32_t sw[16];
-      tmem_ld16(lane_base + (uint32_t)(TC_SUM_COL + 2 * cb), sw);
-      tmem_ld_wait();
+      float sc[8], er[8], added;
+      tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
+      if (!valid) continue;
+      if (vec && cb + 8 <= M.C) {
+        float4* d = reinterpret_cast<float4*>(lp + cb);
+        d[0] = make_float4(sc[0] - lse, sc[1] - lse, sc[2] - lse, sc[3] - lse);
+        d[1] = make_float4(sc[4] - lse, sc[5] - lse, sc[6] - lse, sc[7] - lse);
+      } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int c = cb + i;
-        if (c >= M.C) break;
-        if (valid) lp[c] = tc_score(sw[2 * i], sw[2 * i + 1], scale, M.bias[c]) - lse;
+        for (int i = 0; i < 8; ++i)
+          if (cb + i < M.C) lp[cb + i] = sc[i] - lse;
       }
     }
   }
   return true;
 }
 
-// Drain one accumulation chunk: add its three limb sums (exact integers
-// below 2^24 in FP32) into this thread's 16 exact int64 sums, which live in
-// tensor memory (2 columns per class, low word first), 8 classes at a time.
-// After the last chunk of a tile, run the epilogue.
-__device__ __forceinline__ bool tc_drain(const TcArgs& a, TcShared& sh, TcXch* xch,
-                                         const TcDrain& p, int qd, int part, int lane,
-                                         uint32_t tmem, int& ep) {
-  const int c0 = TC_CLS * part;
-  const int buf = p.bits & 1;
-  if (!tc_wait_warp(sh, &sh.acc_full[buf], (uint32_t)(p.bits >> 1) & 1u, a.status)) return false;
-  tc_fence_after();
-  const int Cp = a.models[tc_group(a, p.g).model].Cp;
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+// chunked pass: add the chunk's three limb sums (exact integers below 2^24 in
+// FP32) into this thread's int64 sums in tensor memory (2 columns per class,
+// low word first), 8 classes at a time
+__device__ __forceinline__ void tc_drain_chunk(int Cp, int c0, int cpp, bool first,
+                                               uint32_t lane_base) {
+#pragma unroll 1
+  for (int cb = c0; cb < c0 + cpp; cb += 8) {
+    if (cb >= Cp) break;
+    uint32_t sw[16];
+    const uint32_t sum_addr = lane_base + (uint32_t)(TC_SUMCOL + 2 * cb);
+    if (first) {
 #pragma unroll
-  for (int hh = 0; hh < 2; ++hh) {
-    const int cb = c0 + 8 * hh;
-    if (cb < Cp) {
-      uint32_t sw[16];
-      const uint32_t sum_addr = lane_base + (uint32_t)(TC_SUM_COL + 2 * cb);
-      if (p.bits & 8) {        // first chunk of the tile
-#pragma unroll
-        for (int i = 0; i < 16; ++i) sw[i] = 0;
-      } else {
-        tmem_ld16(sum_addr, sw);
-        tmem_ld_wait();
-      }
-#pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        uint32_t v[8];
-        tmem_ld8(lane_base + (uint32_t)(buf * TC_ACC_COLS + l * Cp + cb), v);
-        tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          unsigned long long x = ((unsigned long long)sw[2 * i + 1] << 32) | sw[2 * i];
-          x += (unsigned long long)((long long)__float2int_rn(__uint_as_float(v[i])) << (8 * l));
-          sw[2 * i] = (uint32_t)x;
-          sw[2 * i + 1] = (uint32_t)(x >> 32);
-        }
-      }
-      tmem_st16(sum_addr, sw);
-      tmem_st_wait();
+      for (int i = 0; i < 16; ++i) sw[i] = 0;
+    } else {
+      tmem_ld16(sum_addr, sw);
+      tmem_ld_wait();
     }
+    long long q[8];
+    tc_load_acc8(lane_base, 0, Cp, cb, q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      unsigned long long x = ((unsigned long long)sw[2 * i + 1] << 32) | sw[2 * i];
+      x += (unsigned long long)q[i];
+      sw[2 * i] = (uint32_t)x;
+      sw[2 * i + 1] = (uint32_t)(x >> 32);
+    }
+    tmem_st16(sum_addr, sw);
+    tmem_st_wait();
   }
-  tc_fence_before();
-  __syncwarp();
-  if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
-  if (!(p.bits & 4)) return true;
-  return tc_epilogue(a, sh, xch, p.row0, p.nr, p.g, p.tile, (p.bits & 16) != 0, p.T, qd,
-                     part, lane, tmem, ep);
 }
 
-// Tiles of this CTA: phase 0 its share of all tiles (blockIdx.x + i gridDim.x),
-// phase 1 the tiles it queued for the exact pass.
-__device__ __forceinline__ long long tc_ntiles(const TcArgs& a, TcShared& sh, long long n_tiles,
-                                               int phase) {
-  if (phase) {
-    const int c = *reinterpret_cast<volatile int*>(&sh.redo_n);
-    return c < TC_REDO_CAP ? c : TC_REDO_CAP;
-  }
-  const long long k = blockIdx.x;
-  return k < n_tiles ? (n_tiles - k + gridDim.x - 1) / gridDim.x : 0;
-}
-__device__ __forceinline__ long long tc_tile_at(const TcArgs& a, TcShared& sh, int phase,
-                                                long long i) {
-  if (phase) return (long long)sh.redo_list[i];
-  return (long long)blockIdx.x + i * (long long)gridDim.x;
-}
-// MMA stages per accumulation chunk: the whole row in the single-accumulation
-// phase, 512 features (always exact) otherwise
-__device__ __forceinline__ int tc_chunk(const TcArgs& a, int phase) {
-  return (a.single && phase == 0) ? a.nks : TC_CHUNK;
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+// units of this CTA: the pass's unit count, dealt round-robin
+template <int MODE>
+__device__ __forceinline__ long long tc_units(const TcArgs& a) {
+  if (MODE == 0) return a.groups ? a.hdr->tiles : a.units0;
+  unsigned long long c = *a.heavy_n;
+  if (c > (unsigned long long)a.heavy_cap) c = (unsigned long long)a.heavy_cap;
+  return (long long)((c + TC_M - 1) / TC_M);
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constant__ TcArgs a) {
+  using PS = TcPass<MODE>;
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   TcShared& sh = *reinterpret_cast<TcShared*>(tc_smem);
-  TcXch* xch = reinterpret_cast<TcXch*>(tc_smem + 1024);
-  uint8_t* raw = tc_smem + 1024 + sizeof(TcXch);            // 1 KB aligned
-  uint8_t* A = raw + (size_t)a.nraw * TC_RAW_BYTES;
-  uint8_t* B = A + (size_t)TC_NAB * TC_A_BYTES;
+  TcXch& xe = *reinterpret_cast<TcXch*>(tc_smem + 1024);
+  // 1 KB aligned: the swizzled row stages (pair pass only), then the weights
+  uint8_t* raw = tc_smem + 1024 + ((sizeof(TcXch) + 1023) / 1024) * 1024;
+  uint8_t* B = raw + (MODE == 0 ? (size_t)TC_NRAW * TC_RAW_BYTES : 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_groups = a.groups ? a.hdr->n_groups : 1;
-  const long long n_tiles = a.groups ? a.hdr->tiles : a.tiles0;
+  const long long n_units = tc_units<MODE>(a);
+  const long long my_units =
+      n_units > (long long)blockIdx.x ? (n_units - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int nks = a.nks, F = a.F;
+  // chunked pass: the listed rows' count
+  long long n_heavy = 0;
+  if (MODE == 1) n_heavy = (long long)min(*a.heavy_n, (unsigned long long)a.heavy_cap);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < a.nraw; ++i) {
+    for (int i = 0; i < TC_NRAW; ++i) {
       mbar_init(&sh.raw_full[i], 1);
       mbar_init(&sh.raw_empty[i], TC_WORK);
     }
-    for (int i = 0; i < TC_NAB; ++i) {
+    for (int i = 0; i < TC_NB; ++i) {
       mbar_init(&sh.b_full[i], 1);
+      mbar_init(&sh.b_empty[i], 1);
+    }
+    for (int i = 0; i < PS::NA; ++i) {
       mbar_init(&sh.a_full[i], TC_WORK);
-      mbar_init(&sh.ab_empty[i], 1);
+      mbar_init(&sh.a_empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&sh.acc_full[i], 1);
-      mbar_init(&sh.acc_empty[i], TC_WORK);
-
-    }
+    mbar_init(&sh.acc_full, 1);
+    mbar_init(&sh.acc_empty, TC_WORK);
     mbar_init(&sh.fin, 1);
     mbar_init(&sh.xfull, TC_WORK);
     mbar_init(&sh.xfree, TC_WORK);
-    mbar_init(&sh.redo_ready, TC_WORK);
     sh.abort = 0;
-    sh.redo_flag[0] = sh.redo_flag[1] = 0;
-    sh.redo_n = 0;
   }
   if (warp == TC_WORK + 1) tmem_alloc(&sh.tmem, 512);
   tc_fence_before();
@@ -491,163 +560,133 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
   const uint32_t tmem = sh.tmem;
 
   if (warp == TC_WORK) {
-    // ---- row producer -------------------------------------------------
-    long long ri = 0, last[TC_MAX_RAW] = {-1, -1, -1, -1};
-    uint32_t lastp[TC_MAX_RAW] = {0, 0, 0, 0};
-    int rs = 0;          // slot of the next row stage
-    uint32_t rp = 0;     // its phase parity
-    if ((smem_addr(raw) & 1023u) != 0) {   // the swizzled reads assume 1 KB alignment
-      if (lane == 0) {
+    // ---- weight-limb producer -----------------------------------------
+    if (lane == 0) {
+      long long bi = 0, last[TC_NB] = {-1, -1, -1, -1, -1};
+      bool ok = true;
+      for (long long it = 0; it < my_units && ok && !tc_aborted(sh); ++it) {
+        const long long t = blockIdx.x + it * gridDim.x;
+        const int g = MODE == 0 ? tc_unit(a, n_groups, t).g : 0;
+        const TcModelArg& M = a.models[tc_group(a, g).model];
+        const uint32_t sb = (uint32_t)M.N * 128u;
+        for (int ks = 0; ks < nks; ++ks, ++bi) {
+          const int slot = (int)(bi % TC_NB);
+          const uint32_t par = (uint32_t)((bi / TC_NB) & 1);
+          if (!tc_wait(sh, &sh.b_empty[slot], par ^ 1u, a.status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&sh.b_full[slot], sb);
+          bulk_g2s(B + (size_t)slot * a.b_bytes, M.wlay + (size_t)ks * sb, sb, &sh.b_full[slot]);
+          last[slot] = bi;
+        }
+      }
+      // copies still in flight land before the CTA exits
+      for (int s = 0; s < TC_NB; ++s)
+        if (last[s] >= 0)
+          tc_wait(sh, &sh.b_full[s], (uint32_t)((last[s] / TC_NB) & 1), a.status);
+    }
+    __syncwarp();
+  } else if (warp == TC_WORK + 2) {
+    // ---- row producer (pair pass) ----------------------------------------
+    if (MODE == 0 && lane == 0) {
+      long long ri = 0, last[TC_NRAW] = {-1, -1};
+      bool ok = (smem_addr(raw) & 1023u) == 0;   // the swizzled reads assume 1 KB alignment
+      if (!ok) {
         atomicOr(a.status, ST_TIMEOUT);
         *reinterpret_cast<volatile int*>(&sh.abort) = 1;
       }
-    }
-    bool ok = true;
-    const uint64_t map = reinterpret_cast<uint64_t>(&a.tmap);
-    // L2 prefetch cursor of phase 0, TC_PF row stages ahead of the loads: the
-    // shared-memory stages then fill from L2, so few of them keep HBM busy
-    long long pit = 0, npf = 0;
-    int pf0 = 0;
-    const long long nt0 = tc_ntiles(a, sh, n_tiles, 0);
-    for (int phase = 0; phase < 2 && ok; ++phase) {
-     if (phase == 1 && !tc_wait_warp(sh, &sh.redo_ready, 0, a.status)) break;
-     const long long nt = tc_ntiles(a, sh, n_tiles, phase);
-     for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
-      const long long t = tc_tile_at(a, sh, phase, it);
-      const TcTile tl = tc_tile(a, n_groups, t);
-      // a group's map sits in the work list, rewritten between calls: drop any
-      // stale copy the tensor-map proxy may hold
-      const uint64_t tmap = a.maps ? reinterpret_cast<uint64_t>(a.maps + tl.g) : map;
-      if (a.maps && lane == 0)
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
-                     : "memory");
-      for (int f0 = 0; f0 < F; f0 += TC_KR, ++ri) {
-        if (phase == 0 && lane == 0)
-          for (; npf < ri + TC_PF && pit < nt0; ++npf) {
-            const TcTile pt = tc_tile(a, n_groups, tc_tile_at(a, sh, 0, pit));
-#pragma unroll
-            for (int b = 0; b < TC_KR / TC_BOX; ++b)
-              asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                               a.maps ? reinterpret_cast<uint64_t>(a.maps + pt.g) : map),
-                           "r"(pf0 + b * TC_BOX), "r"((int)pt.row0)
-                           : "memory");
-            pf0 += TC_KR;
-            if (pf0 >= F) {
-              pf0 = 0;
-              ++pit;
-            }
+      const uint64_t map0 = reinterpret_cast<uint64_t>(&a.tmap);
+      for (long long it = 0; it < my_units && ok && !tc_aborted(sh); ++it) {
+        const long long t = blockIdx.x + it * gridDim.x;
+        const TcUnit U = tc_unit(a, n_groups, t);
+        // a group's map sits in the work list, rewritten between calls: drop
+        // any stale copy the tensor-map proxy may hold
+        const uint64_t tmap = a.maps ? reinterpret_cast<uint64_t>(a.maps + U.g) : map0;
+        if (a.maps)
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
+                       : "memory");
+        for (int f0 = 0; f0 < F; f0 += TC_BOX, ++ri) {
+          const int slot = (int)(ri % TC_NRAW);
+          const uint32_t par = (uint32_t)((ri / TC_NRAW) & 1);
+          if (!tc_wait(sh, &sh.raw_empty[slot], par ^ 1u, a.status)) {
+            ok = false;
+            break;
           }
-        const int slot = rs;
-        const uint32_t rpar = rp;
-        if (++rs == a.nraw) {
-          rs = 0;
-          rp ^= 1u;
-        }
-        if (!tc_wait_warp(sh, &sh.raw_empty[slot], rpar ^ 1u, a.status)) {
-          ok = false;
-          break;
-        }
-        if (lane == 0) {
           mbar_expect_tx(&sh.raw_full[slot], TC_RAW_BYTES);
           uint8_t* dst = raw + (size_t)slot * TC_RAW_BYTES;
-          const int y = (int)tl.row0;
 #pragma unroll
-          for (int b = 0; b < TC_KR / TC_BOX; ++b)
+          for (int h = 0; h < 2; ++h)
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst + b * (TC_M * TC_BOX))),
-                "l"(tmap), "r"(f0 + b * TC_BOX), "r"(y), "r"(smem_addr(&sh.raw_full[slot]))
+                " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst + h * (TC_M * TC_BOX))),
+                "l"(tmap), "r"(f0), "r"((int)(U.row0 + TC_M * h)),
+                "r"(smem_addr(&sh.raw_full[slot]))
                 : "memory");
+          last[slot] = ri;
         }
-        last[slot] = ri;
-        lastp[slot] = rpar;
-        __syncwarp();
       }
-     }
-    }
-    // the phases of a slot complete in order: wait for its last copies
-    if (lane == 0)
-      for (int s = 0; s < a.nraw; ++s)
-        if (last[s] >= 0) tc_wait(sh, &sh.raw_full[s], lastp[s], a.status);
-  } else if (warp == TC_WORK + 2) {
-    // ---- weight-limb producer -----------------------------------------
-    long long bi = 0, last[TC_NAB] = {-1, -1, -1, -1};
-    bool ok = true;
-    for (int phase = 0; phase < 2 && ok; ++phase) {
-     if (phase == 1 && !tc_wait_warp(sh, &sh.redo_ready, 0, a.status)) break;
-     const long long nt = tc_ntiles(a, sh, n_tiles, phase);
-     for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
-      const TcTile tl = tc_tile(a, n_groups, tc_tile_at(a, sh, phase, it));
-      const TcModelArg& M = a.models[tc_group(a, tl.g).model];
-      const uint32_t sb = (uint32_t)M.N * 128u;
-      for (int ks = 0; ks < nks; ++ks, ++bi) {
-        const int slot = (int)((unsigned long long)bi & (TC_NAB - 1));
-        const uint32_t bpar = (uint32_t)(((unsigned long long)bi / TC_NAB) & 1);
-        if (!tc_wait_warp(sh, &sh.ab_empty[slot], bpar ^ 1u, a.status)) {
-          ok = false;
-          break;
-        }
-        if (lane == 0) {
-          mbar_expect_tx(&sh.b_full[slot], sb);
-          bulk_g2s(B + (size_t)slot * a.b_bytes, M.wlay + (size_t)ks * sb, sb, &sh.b_full[slot]);
-        }
-        last[slot] = bi;
-        __syncwarp();
-      }
-     }
-    }
-    if (lane == 0)
-      for (int s = 0; s < TC_NAB; ++s)
+      // copies still in flight land before the CTA exits
+      for (int s = 0; s < TC_NRAW; ++s)
         if (last[s] >= 0)
-          tc_wait(sh, &sh.b_full[s], (uint32_t)(((unsigned long long)last[s] / TC_NAB) & 1),
-                  a.status);
+          tc_wait(sh, &sh.raw_full[s], (uint32_t)((last[s] / TC_NRAW) & 1), a.status);
+    }
+    __syncwarp();
   } else if (warp == TC_WORK + 1) {
-    // ---- MMA issuer ---------------------------------------------------
+    // ---- MMA issuer -----------------------------------------------------
     if (lane == 0) {
-      long long bi = 0, di = 0;
+      long long bi = 0, ai = 0, ci = 0;
       bool ok = true;
-      for (int phase = 0; phase < 2 && ok; ++phase) {
-       if (phase == 1 && !tc_wait(sh, &sh.redo_ready, 0, a.status)) break;
-       const long long nt = tc_ntiles(a, sh, n_tiles, phase);
-       const int chunk = tc_chunk(a, phase);
-       for (long long it = 0; it < nt && ok && !tc_aborted(sh); ++it) {
-        const TcTile tl = tc_tile(a, n_groups, tc_tile_at(a, sh, phase, it));
-        const TcModelArg& M = a.models[tc_group(a, tl.g).model];
+      const int chunk = MODE == 0 ? nks : TC_CHUNK;
+      for (long long it = 0; it < my_units && ok && !tc_aborted(sh); ++it) {
+        const long long t = blockIdx.x + it * gridDim.x;
+        const int g = MODE == 0 ? tc_unit(a, n_groups, t).g : 0;
+        const TcModelArg& M = a.models[tc_group(a, g).model];
         const uint32_t idesc = tc_idesc_f16(TC_M, M.N);
-        uint32_t d = tmem;
-        int buf = 0, kc = 0;   // kc: MMA stage within the accumulation chunk
-        for (int ks = 0; ks < nks; ++ks, ++bi) {
-          if (kc == 0) {
-            buf = (int)(di & 1);
-            if (!tc_wait(sh, &sh.acc_empty[buf], (uint32_t)((di >> 1) & 1) ^ 1u, a.status)) {
+        int kc = 0;
+        for (int ks = 0; ks < nks && ok; ++ks) {
+          if (kc == 0 && ci > 0) {   // the accumulators were drained
+            if (!tc_wait(sh, &sh.acc_empty, (uint32_t)((ci - 1) & 1), a.status)) {
+              ok = false;
+              break;
+            }
+          }
+          const int bslot = (int)(bi % TC_NB);
+          if (!tc_wait(sh, &sh.b_full[bslot], (uint32_t)((bi / TC_NB) & 1), a.status)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bs = smem_addr(B + (size_t)bslot * a.b_bytes);
+          // the weight stage's A stages, KA features each
+#pragma unroll
+          for (int sub = 0; sub < PS::SUB; ++sub) {
+            const int aslot = (int)(ai % PS::NA);
+            if (!tc_wait(sh, &sh.a_full[aslot], (uint32_t)((ai / PS::NA) & 1), a.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            d = tmem + (uint32_t)(buf * TC_ACC_COLS);
-          }
-          const int slot = (int)((unsigned long long)bi & (TC_NAB - 1));
-          const uint32_t par = (uint32_t)(((unsigned long long)bi / TC_NAB) & 1);
-          if (!tc_wait(sh, &sh.b_full[slot], par, a.status) ||
-              !tc_wait(sh, &sh.a_full[slot], par, a.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t as = smem_addr(A + (size_t)slot * TC_A_BYTES);
-          const uint32_t bs = smem_addr(B + (size_t)slot * a.b_bytes);
 #pragma unroll
-          for (int j = 0; j < TC_KS / 16; ++j)
-            tc_mma_f16(d, tc_desc(as + 256u * j, 128u, 1024u), tc_desc(bs + 256u * j, 128u, 1024u),
-                       idesc, (uint32_t)(kc | j));
-          tc_commit(&sh.ab_empty[slot]);
+            for (int h = 0; h < PS::H; ++h)
+#pragma unroll
+              for (int j = 0; j < PS::KA / 16; ++j)
+                tc_mma_f16_ts(tmem + (uint32_t)(TC_ACC * h),
+                              tmem + (uint32_t)(TC_ACOL + aslot * PS::ACOLS * PS::H +
+                                                PS::ACOLS * h + 8 * j),
+                              tc_desc(bs + 256u * (uint32_t)(sub * (PS::KA / 16) + j), 128u, 1024u),
+                              idesc, (uint32_t)(kc | sub | j));
+            tc_commit(&sh.a_empty[aslot]);
+            ++ai;
+          }
+          if (!ok) break;
+          tc_commit(&sh.b_empty[bslot]);
+          ++bi;
           if (++kc == chunk || ks == nks - 1) {
-            tc_commit(&sh.acc_full[buf]);
-            ++di;
+            tc_commit(&sh.acc_full);
+            ++ci;
             kc = 0;
           }
         }
-       }
       }
       // every MMA issued so far has completed once this arrives
       tc_commit(&sh.fin);
@@ -655,134 +694,190 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
     }
     __syncwarp();
   } else {
-    // ---- converters / drain / epilogue (warps 0 .. TC_WORK-1) ----------
-    const int qd = warp & 3, part = warp >> 2;
-    const int r = 32 * qd + lane;          // tile row = tensor-memory lane
-    TcDrain p0{}, p1{};      // pending drains, oldest first
-    int np = 0;
-    int ri = 0, bi = 0, di = 0, gs = 0, ep = 0;   // ring counters of this CTA
-    int rs = 0;          // slot of the next row stage
-    uint32_t rp = 0;     // its phase parity
-    const uint32_t raw_s = smem_addr(raw), a_s = smem_addr(A);
+    // ---- converters / drains / epilogue (warps 0 .. TC_WORK-1) ----------
+    const int qd = warp & 3, rest = warp >> 2;
+    const int h = rest % PS::H, part = rest / PS::H;
+    const int xr = TC_M * h + 32 * qd + lane;     // exchange row of this thread
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+    const uint32_t a_col = (uint32_t)(TC_ACOL + PS::ACOLS * h + PS::COLS * part);
+    const int nka = nks * PS::SUB;                // A stages per row
+    const long long total = my_units * nka;
+    const int chunk = MODE == 0 ? nka : TC_CHUNK * PS::SUB;   // A stages per accumulation
+    int ep = 0;
+    long long ai = 0, ci = 0;
     bool ok = true;
 
-
-    for (int phase = 0; phase < 2 && ok; ++phase) {
-     if (phase == 1) {
-      // every epilogue of phase 0 is done once all converter warps arrive
-      while (ok && np > 0) {
-        if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) ok = false;
-        p0 = p1;
-        --np;
+    // row of this thread in unit ordinal i (-1: past the end)
+    auto row_of = [&](long long i, int& g) -> long long {
+      const long long t = blockIdx.x + i * gridDim.x;
+      if (MODE == 0) {
+        const TcUnit U = tc_unit(a, n_groups, t);
+        g = U.g;
+        const long long r = U.row0 + TC_M * h + 32 * qd + lane;
+        return r < U.n ? r : -1;
       }
-      if (!ok) break;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.redo_ready);
-      if (!tc_wait_warp(sh, &sh.redo_ready, 0, a.status)) break;
-     }
-     const long long nt = tc_ntiles(a, sh, n_tiles, phase);
-     const int chunk = tc_chunk(a, phase);
-     const int heavy_bit = (a.single && phase == 0) ? 16 : 0;
-     for (long long it = 0; it < nt && ok; ++it) {
-      const long long t = tc_tile_at(a, sh, phase, it);
-      const TcTile tl = tc_tile(a, n_groups, t);
-      uint32_t T = 0, rpar = 0;
-      int rslot = 0, kc = 0;
-      for (int ks = 0; ks < nks; ++ks) {
+      g = 0;
+      const long long idx = t * TC_M + 32 * qd + lane;
+      return idx < n_heavy ? a.heavy[idx] : -1;
+    };
+
+    // chunked pass: the listed rows' bytes come from global memory, TC_PD - 1
+    // A stages ahead of the conversion
+    long long l_i = 0;
+    int l_ka = 0, l_g = 0;
+    long long l_row = (MODE == 1 && total > 0) ? row_of(0, l_g) : -1;
+    const unsigned char* l_rp =
+        l_row >= 0 ? reinterpret_cast<const unsigned char*>(tc_group(a, l_g).X) +
+                         l_row * tc_group(a, l_g).ld_bytes
+                   : nullptr;
+    auto load_next = [&](uint4& dst) {
+      const int f = PS::KA * l_ka + PS::BPT * part;
+      // the same bytes a.pf stages on are fetched into L2 now
+      if (l_rp && f + PS::KA * a.pf < F)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(l_rp + f + PS::KA * a.pf));
+      uint4 x = make_uint4(0, 0, 0, 0);
+      if (l_rp && f < F) {
+        x = ld_stream16(l_rp + f);
+        if (f + 16 > F) {   // zero the bytes past F
+          const int keep = F - f;
+          uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int vb = keep - 4 * k;
+            w[k] &= vb >= 4 ? 0xFFFFFFFFu : (vb <= 0 ? 0u : ((1u << (8 * vb)) - 1u));
+          }
+          x = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      dst = x;
+      if (++l_ka == nka) {
+        l_ka = 0;
+        if (++l_i < my_units) {
+          l_row = row_of(l_i, l_g);
+          const SegGroup& G = tc_group(a, l_g);
+          l_rp = l_row >= 0 ? reinterpret_cast<const unsigned char*>(G.X) + l_row * G.ld_bytes
+                            : nullptr;
+        } else {
+          l_rp = nullptr;
+        }
+      }
+    };
+    uint4 buf[MODE == 1 ? TC_PD : 1];
+    if constexpr (MODE == 1) {
+#pragma unroll
+      for (int d = 0; d < TC_PD - 1; ++d)
+        if (d < total) load_next(buf[d]);
+    }
+    long long ri = 0;   // pair pass: row stages consumed
+    const uint32_t raw_s = smem_addr(raw) + (uint32_t)(h * TC_M * TC_BOX);
+    const int rr = 32 * qd + lane;   // row within the tile
+    constexpr int RAW_A = TC_BOX / PS::KA;   // A stages per row stage
+
+    // consumer state
+    long long c_i = 0;
+    int c_ka = 0, kc = 0;
+    uint32_t T = 0;
+    for (long long base = 0; base < total && ok; base += TC_PD) {
+#pragma unroll
+      for (int d = 0; d < TC_PD; ++d) {
+        if (base + d >= total || !ok) break;
         if (tc_aborted(sh)) {
           ok = false;
           break;
         }
-        const int sub = ks & 1;   // MMA stage within the row stage
-        if (sub == 0) {
-          rslot = rs;
-          rpar = rp;
-          if (++rs == a.nraw) {
-            rs = 0;
-            rp ^= 1u;
-          }
-          if (!tc_wait_warp(sh, &sh.raw_full[rslot], rpar, a.status)) {
+        uint4 xv[PS::NV];
+        if constexpr (MODE == 1) {
+          if (base + d + TC_PD - 1 < total) load_next(buf[(d + TC_PD - 1) % TC_PD]);
+          xv[0] = buf[d];
+        } else {
+          // this thread's bytes of the A stage: 16-byte chunks of its row in
+          // the row stage, swizzled by the row (rows and features past the end
+          // arrive as zeros)
+          const uint32_t slot = (uint32_t)(ri % TC_NRAW);
+          if (c_ka % RAW_A == 0 &&
+              !tc_wait_warp(sh, &sh.raw_full[slot], (uint32_t)((ri / TC_NRAW) & 1), a.status)) {
             ok = false;
             break;
           }
+#pragma unroll
+          for (int v = 0; v < PS::NV; ++v) {
+            const int c16 = (PS::KA / 16) * (c_ka % RAW_A) + PS::NV * part + v;
+            xv[v] = lds16(raw_s + slot * TC_RAW_BYTES +
+                          (uint32_t)(rr * TC_BOX + ((c16 ^ (rr & 7)) << 4)));
+          }
         }
-        const int slot = bi & (TC_NAB - 1);
-        if (!tc_wait_warp(sh, &sh.ab_empty[slot], ((uint32_t)bi / TC_NAB & 1u) ^ 1u, a.status)) {
+        // convert this thread's bytes to FP16 pairs
+        uint32_t o[PS::COLS];
+#pragma unroll
+        for (int v = 0; v < PS::NV; ++v) {
+          const uint4 x = xv[v];
+          T = dp4a_uu(x.x, 0x01010101u, T);
+          T = dp4a_uu(x.y, 0x01010101u, T);
+          T = dp4a_uu(x.z, 0x01010101u, T);
+          T = dp4a_uu(x.w, 0x01010101u, T);
+          o[8 * v + 0] = u8x2_to_f16x2(x.x, 0x5140u);
+          o[8 * v + 1] = u8x2_to_f16x2(x.x, 0x7362u);
+          o[8 * v + 2] = u8x2_to_f16x2(x.y, 0x5140u);
+          o[8 * v + 3] = u8x2_to_f16x2(x.y, 0x7362u);
+          o[8 * v + 4] = u8x2_to_f16x2(x.z, 0x5140u);
+          o[8 * v + 5] = u8x2_to_f16x2(x.z, 0x7362u);
+          o[8 * v + 6] = u8x2_to_f16x2(x.w, 0x5140u);
+          o[8 * v + 7] = u8x2_to_f16x2(x.w, 0x7362u);
+        }
+        if constexpr (MODE == 0) {
+          if (c_ka % RAW_A == RAW_A - 1 || c_ka == nka - 1) {   // done with the row stage
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.raw_empty[ri % TC_NRAW]);
+            ++ri;
+          }
+        }
+        const int aslot = (int)(ai % PS::NA);
+        if (!tc_wait_warp(sh, &sh.a_empty[aslot], (uint32_t)((ai / PS::NA) & 1) ^ 1u,
+                          a.status)) {
           ok = false;
           break;
         }
-        // row r, features ks*64 + 16 part .. +15 -> core matrices 2 part, 2 part + 1
-        // 16-byte chunk sub*4 + part of row r, swizzled by r & 7; rows and
-        // features past the end arrive as zeros
-        const int c16 = (sub << 2) + part;
-        const uint4 v = lds16(raw_s + (uint32_t)rslot * TC_RAW_BYTES +
-                              (uint32_t)(r * TC_BOX + ((c16 ^ (r & 7)) << 4)));
-        T = dp4a_uu(v.x, 0x01010101u, T);
-        T = dp4a_uu(v.y, 0x01010101u, T);
-        T = dp4a_uu(v.z, 0x01010101u, T);
-        T = dp4a_uu(v.w, 0x01010101u, T);
-        const uint32_t at = a_s + (uint32_t)slot * TC_A_BYTES +
-                            (uint32_t)((r >> 3) * 1024 + (r & 7) * 16 + 2 * part * 128);
-        uint4 o;
-        o.x = u8x2_to_f16x2(v.x, 0x5140u);
-        o.y = u8x2_to_f16x2(v.x, 0x7362u);
-        o.z = u8x2_to_f16x2(v.y, 0x5140u);
-        o.w = u8x2_to_f16x2(v.y, 0x7362u);
-        sts16(at, o);
-        o.x = u8x2_to_f16x2(v.z, 0x5140u);
-        o.y = u8x2_to_f16x2(v.z, 0x7362u);
-        o.z = u8x2_to_f16x2(v.w, 0x5140u);
-        o.w = u8x2_to_f16x2(v.w, 0x7362u);
-        sts16(at + 128, o);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_after();
+        if constexpr (PS::COLS == 16) tmem_st16(lane_base + a_col + (uint32_t)(aslot * PS::ACOLS * PS::H), o);
+        else tmem_st8(lane_base + a_col + (uint32_t)(aslot * PS::ACOLS * PS::H), o);
+        tmem_st_wait();
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.a_full[slot]);
-        ++bi;
-        if (sub == 1 || ks == nks - 1) {
-          if (lane == 0) mbar_arrive(&sh.raw_empty[rslot]);
-          ++ri;
-        }
-        ++gs;
-        while (np > 0 && p0.trigger <= gs) {
-          if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) {
+        if (lane == 0) mbar_arrive(&sh.a_full[aslot]);
+        ++ai;
+        const bool unit_end = c_ka == nka - 1;
+        if (++kc == chunk || unit_end) {
+          // the accumulation cycle is complete: drain (chunked) and / or run
+          // the epilogue of the unit
+          kc = 0;
+          if (!tc_wait_warp(sh, &sh.acc_full, (uint32_t)(ci & 1), a.status)) {
             ok = false;
             break;
           }
-          p0 = p1;
-          --np;
-        }
-        if (!ok) break;
-        const bool chunk_end = ++kc == chunk || ks == nks - 1;
-        if (chunk_end) {
-          if (np == 2) {   // very short rows: drain the oldest before queueing
-            if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) {
+          tc_fence_after();
+          if (MODE == 1) tc_drain_chunk(a.models[0].Cp, PS::CPP * part, PS::CPP,
+                                        c_ka < chunk, lane_base);
+          if (unit_end) {
+            int g = 0;
+            const long long r = row_of(c_i, g);
+            const SegGroup& G = tc_group(a, g);
+            if (!tc_epilogue<MODE>(a, sh, xe, G, a.models[G.model], r, xr, h, part, T,
+                                   lane_base, ep)) {
               ok = false;
               break;
             }
-            p0 = p1;
-            --np;
+            T = 0;
           }
-          TcDrain p;
-          p.row0 = tl.row0;
-          p.nr = tl.nr;
-          p.g = tl.g;
-          p.tile = (int)t;
-          p.bits = (di & 1) | (((di >> 1) & 1) << 1) | ((ks == nks - 1) ? 4 : 0) |
-                   (ks < chunk ? 8 : 0) | heavy_bit;
-          kc = 0;
-          p.T = T;
-          p.trigger = gs + TC_LAG;
-          if (np == 0) p0 = p; else p1 = p;
-          ++np;
-          ++di;
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.acc_empty);
+          ++ci;
+        }
+        if (++c_ka == nka) {
+          c_ka = 0;
+          ++c_i;
         }
       }
-     }
-    }
-    while (ok && np > 0) {
-      if (!tc_drain(a, sh, xch, p0, qd, part, lane, tmem, ep)) break;
-      p0 = p1;
-      --np;
     }
   }
   tc_fence_before();
@@ -853,6 +948,7 @@ nb_status launch_derive_tc(nb_model* m, cudaStream_t st) {
   return NB_OK;
 }
 
+
 // ---------------------------------------------------------------------------
 // launch
 // ---------------------------------------------------------------------------
@@ -875,37 +971,32 @@ static TcModelArg tc_model_arg(const nb_model* m) {
 }
 
 // shared memory of a launch whose largest model has N limb rows
-static size_t tc_smem_bytes(int nraw, int N) {
-  return 1024 + sizeof(TcXch) + (size_t)nraw * TC_RAW_BYTES +
-         (size_t)TC_NAB * (TC_A_BYTES + (uint32_t)N * 128u);
+static size_t tc_smem_bytes(int mode, int N) {
+  return 1024 + ((sizeof(TcXch) + 1023) / 1024) * 1024 +
+         (mode == 0 ? (size_t)TC_NRAW * TC_RAW_BYTES : 0) + (size_t)TC_NB * (uint32_t)N * 128u;
 }
 
-static nb_status run_tc(TcArgs& a, int maxN, long long tiles_hint, cudaStream_t st) {
+template <int MODE>
+static nb_status run_tc(TcArgs& a, int maxN, long long units_hint, cudaStream_t st) {
   constexpr size_t kMax = 227 * 1024;
-  int nraw = TC_MAX_RAW;
-  while (nraw > 2 && tc_smem_bytes(nraw, maxN) > kMax) --nraw;
-  const size_t smem = tc_smem_bytes(nraw, maxN);
+  const size_t smem = tc_smem_bytes(MODE, maxN);
   if (smem > kMax) {
     set_error("tensor-core scorer: shared memory %zu bytes exceeds the limit", smem);
     return NB_EUNSUPPORTED;
   }
-  a.nraw = nraw;
   a.b_bytes = (uint32_t)maxN * 128u;
+  a.pf = 8;
   // more than half the shared memory of an SM keeps one CTA (and one
   // tensor-memory allocation) per SM
   const size_t launch_smem = smem < 120 * 1024 ? 120 * 1024 : smem;
-  NB_TRY_CUDA(cudaFuncSetAttribute(k_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  NB_TRY_CUDA(cudaFuncSetAttribute(k_score_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)launch_smem),
               "cudaFuncSetAttribute(k_score_tc)");
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(TC_THREADS);
-  cfg.dynamicSmemBytes = launch_smem;
-  cfg.stream = st;
   long long grid = num_sms();
-  if (tiles_hint > 0 && tiles_hint < grid) grid = tiles_hint;
-  cfg.gridDim = dim3((unsigned)grid);
+  if (units_hint > 0 && units_hint < grid) grid = units_hint;
   count_launch();
-  NB_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_score_tc, a), "k_score_tc launch");
+  k_score_tc<MODE><<<(unsigned)grid, TC_THREADS, launch_smem, st>>>(a);
+  NB_TRY_CUDA(cudaGetLastError(), "k_score_tc launch");
   return NB_OK;
 }
 
@@ -934,7 +1025,7 @@ static nb_status tc_row_map(CUtensorMap* map, const void* X, int64_t n, int F, i
     set_error("tensor-core scorer: cuTensorMapEncodeTiled is not available");
     return NB_ECUDA;
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)F, (cuuint64_t)n};
+  const cuuint64_t dims[2] = {(cuuint64_t)F, (cuuint64_t)(n > 0 ? n : 1)};
   const cuuint64_t strides[1] = {(cuuint64_t)ld};
   const cuuint32_t box[2] = {(cuuint32_t)TC_BOX, (cuuint32_t)TC_M};
   const cuuint32_t estr[2] = {1, 1};
@@ -953,6 +1044,7 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   TcArgs a{};
   nb_status ms = tc_row_map(&a.tmap, X, n, m->F, ld);
   if (ms != NB_OK) return ms;
+  a.maps = nullptr;
   a.groups = nullptr;
   a.hdr = nullptr;
   SegGroup& g = a.g0;
@@ -970,15 +1062,30 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   g.chunk0 = 0;
   g.model = 0;
   g.family = 2;
-  a.tiles0 = (n + TC_M - 1) / TC_M;
+  a.units0 = (n + 2 * TC_M - 1) / (2 * TC_M);
   a.models[0] = tc_model_arg(m);
   a.F = m->F;
   a.nks = (m->F + TC_KS - 1) / TC_KS;
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
   a.status = m->d.sstatus;
-  a.single = 1;
-  return run_tc(a, a.models[0].N, a.tiles0, st);
+  // the list of heavy rows (and its count) for the chunked pass: stream-ordered
+  // scratch of this call
+  const int cap = n < kTcHeavyCap ? (int)n : kTcHeavyCap;
+  void* scratch = nullptr;
+  NB_TRY_CUDA(cudaMallocAsync(&scratch, 16 + sizeof(long long) * (size_t)cap, st),
+              "cudaMallocAsync(heavy rows)");
+  a.heavy_n = static_cast<unsigned long long*>(scratch);
+  a.heavy = reinterpret_cast<long long*>(static_cast<char*>(scratch) + 16);
+  a.heavy_cap = cap;
+  const cudaError_t me = cudaMemsetAsync(scratch, 0, 16, st);
+  nb_status s = me == cudaSuccess ? NB_OK : cuda_status(me, "memset(heavy count)");
+  if (s == NB_OK) s = run_tc<0>(a, a.models[0].N, a.units0, st);
+  if (s == NB_OK) s = run_tc<1>(a, a.models[0].N, 0, st);
+  const cudaError_t fe = cudaFreeAsync(scratch, st);
+  if (s != NB_OK) return s;
+  NB_TRY_CUDA(fe, "cudaFreeAsync(heavy rows)");
+  return NB_OK;
 }
 
 // tensor map of a group's u8 rows for a batch work list (128 bytes at map)
@@ -1007,8 +1114,11 @@ nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, cons
   a.want_lp = want_lp;
   a.recheck = recheck;
   a.status = status;
-  a.single = 1;
-  return run_tc(a, maxN, 0, st);
+  // heavy rows of a batch stay marked for the segmented FP64 recheck
+  a.heavy = nullptr;
+  a.heavy_n = nullptr;
+  a.heavy_cap = 0;
+  return run_tc<0>(a, maxN, 0, st);
 }
 
 }  // namespace nbg

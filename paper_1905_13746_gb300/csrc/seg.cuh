@@ -31,7 +31,8 @@ struct SegGroup {
 struct SegHeader {
   int n_groups;       // groups of this list
   int pad;
-  long long tiles;    // tiles of the list (first family) / 64-row tiles (second)
+  long long tiles;    // tiles of the list: stage rows (two-class), 64 rows (general),
+                      // 256 rows (tensor-core)
   long long chunks;   // 32-row chunks of the list (recheck)
   long long pad2;
 };

@@ -1,7 +1,7 @@
 // Fifth-generation tensor core (tcgen05) helpers for one CTA (cta_group::1):
 // tensor-memory allocation, shared-memory matrix descriptors, the kind::f16
-// MMA with FP32 accumulation in tensor memory, completion tracking through
-// mbarriers, and tensor-memory loads for the epilogue.
+// instruction descriptor, completion tracking through mbarriers, and
+// tensor-memory loads and stores.
 #pragma once
 
 #include <stdint.h>
@@ -130,6 +130,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
       "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
       "r"(r[15])
+      : "memory");
+}
+
+// thread t of the warp writes 8 consecutive 32-bit columns of lane + t
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
       : "memory");
 }
 
