@@ -345,15 +345,21 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch
   const bool any_ovf = __any_sync(0xFFFFFFFFu, k1 > k0);
   const float tau_unit = M.hdr->tau_unit;
   float T = (float)Tpart;
-  // pass 1
+  // pass 1; the pair pass keeps the part's scores in registers for pass 2
   float best = -INFINITY, second = -INFINITY, emax = 0.f, se = 0.f;
   int bidx = 0x7FFFFFFF;
-#pragma unroll 1
-  for (int cb = c0; cb < c0 + PS::CPP; cb += 8) {
+  float keep[MODE == 0 ? PS::CPP : 1];
+#pragma unroll
+  for (int ch = 0; ch < PS::CPP / 8; ++ch) {
+    const int cb = c0 + 8 * ch;
     if (cb >= M.Cp) break;
     float sc[8], er[8], added;
     tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
-    if (part == 0 && cb == c0) T += added;
+    if (part == 0 && ch == 0) T += added;
+    if constexpr (MODE == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) keep[8 * ch + i] = sc[i];
+    }
     // the chunk's best, second best and sum of exp(s - chunk best), in class
     // order (ties keep the lower index); the exponentials are independent
     float b8 = -INFINITY, s8b = -INFINITY;
@@ -373,7 +379,7 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch
     float e8 = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      if (cb + i < M.C) e8 += expf(sc[i] - b8);
+      if (cb + i < M.C) e8 += __expf(sc[i] - b8);   // ~2^-21 relative: lse to ~1e-6
     // merge into the running values (sum of exp(s - best))
     if (b8 > best) {
       se = se * expf(best - b8) + e8;
@@ -451,11 +457,18 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch
     // row's log posteriors are 16-byte aligned
     float* lp = G.logpost + (valid ? grow : 0) * M.C;
     const bool vec = (reinterpret_cast<uintptr_t>(lp) & 15) == 0;
-#pragma unroll 1
-    for (int cb = c0; cb < c0 + PS::CPP; cb += 8) {
+#pragma unroll
+    for (int ch = 0; ch < PS::CPP / 8; ++ch) {
+      const int cb = c0 + 8 * ch;
       if (cb >= M.Cp) break;
-      float sc[8], er[8], added;
-      tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
+      float sc[8];
+      if constexpr (MODE == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sc[i] = keep[8 * ch + i];
+      } else {
+        float er[8], added;
+        tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
+      }
       if (!valid) continue;
       if (vec && cb + 8 <= M.C) {
         float4* d = reinterpret_cast<float4*>(lp + cb);
@@ -505,6 +518,16 @@ __device__ __forceinline__ void tc_drain_chunk(int Cp, int c0, int cpp, bool fir
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
+// This CTA's first weight stage of every unit in the pair pass: CTAs start at
+// different stages (in pairs, so that a row stage's two halves stay together;
+// only when the stages pair up exactly) and wrap around, so that they do not
+// all fetch the same weight stage from L2 at the same time.  The limb sums are
+// exact integers, so the order of the stages does not change them.
+template <int MODE>
+__device__ __forceinline__ int tc_rot(int nks) {
+  return (MODE == 0 && nks % 2 == 0) ? 2 * (int)((blockIdx.x * 37u) % (unsigned)(nks / 2)) : 0;
+}
+
 // units of this CTA: the pass's unit count, dealt round-robin
 template <int MODE>
 __device__ __forceinline__ long long tc_units(const TcArgs& a) {
@@ -569,6 +592,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
         const int g = MODE == 0 ? tc_unit(a, n_groups, t).g : 0;
         const TcModelArg& M = a.models[tc_group(a, g).model];
         const uint32_t sb = (uint32_t)M.N * 128u;
+        const int rot = tc_rot<MODE>(nks);
         for (int ks = 0; ks < nks; ++ks, ++bi) {
           const int slot = (int)(bi % TC_NB);
           const uint32_t par = (uint32_t)((bi / TC_NB) & 1);
@@ -577,7 +601,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             break;
           }
           mbar_expect_tx(&sh.b_full[slot], sb);
-          bulk_g2s(B + (size_t)slot * a.b_bytes, M.wlay + (size_t)ks * sb, sb, &sh.b_full[slot]);
+          const int kse = ks + rot < nks ? ks + rot : ks + rot - nks;
+          bulk_g2s(B + (size_t)slot * a.b_bytes, M.wlay + (size_t)kse * sb, sb, &sh.b_full[slot]);
           last[slot] = bi;
         }
       }
@@ -606,7 +631,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
         if (a.maps)
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
                        : "memory");
-        for (int f0 = 0; f0 < F; f0 += TC_BOX, ++ri) {
+        const int nraw = (F + TC_BOX - 1) / TC_BOX, rot = tc_rot<MODE>(nks) / 2;
+        for (int rs = 0; rs < nraw; ++rs, ++ri) {
+          const int f0 = TC_BOX * (rs + rot < nraw ? rs + rot : rs + rot - nraw);
           const int slot = (int)(ri % TC_NRAW);
           const uint32_t par = (uint32_t)((ri / TC_NRAW) & 1);
           if (!tc_wait(sh, &sh.raw_empty[slot], par ^ 1u, a.status)) {
@@ -855,8 +882,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             break;
           }
           tc_fence_after();
-          if (MODE == 1) tc_drain_chunk(a.models[0].Cp, PS::CPP * part, PS::CPP,
-                                        c_ka < chunk, lane_base);
+          if (MODE == 1) {
+            tc_drain_chunk(a.models[0].Cp, PS::CPP * part, PS::CPP, c_ka < chunk, lane_base);
+            // the chunk's sums are in the int64 columns: the MMAs may go on
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.acc_empty);
+          }
           if (unit_end) {
             int g = 0;
             const long long r = row_of(c_i, g);
@@ -868,9 +900,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             }
             T = 0;
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.acc_empty);
+          if (MODE == 0) {   // the accumulators are read: the next unit's MMAs may start
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.acc_empty);
+          }
           ++ci;
         }
         if (++c_ka == nka) {
