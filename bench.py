@@ -781,6 +781,109 @@ def run_many_class(args, device, steps=None):
     return line
 
 
+def run_gauss_mc(args, device, Fs=(64, 256, 1024), steps=5):
+    """Gaussian many-class scoring, C = 64 classes: the tensor-core scorer
+    (label mode) against the CUDA-core scorer of the same model, per F, with
+    the share of rows each sends to the FP64 recheck; the tensor-core scorer
+    forced into the log-posterior mode is timed on the same rows."""
+    import torch
+
+    import paper_1905_13746_gb300 as nb
+    import synth
+    C = 64
+    hbm_peak, peak_kind = _peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            tflops = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        tflops = 1900.0
+    stream = torch.cuda.Stream(device)
+    rows = []
+    clk_all = []
+    for F in Fs:
+        # rows of 2 GiB in total (inputs larger than L2 between timed calls)
+        N = args.gmc_bytes // (4 * F)
+        w = synth.gaussian_workload(synth.seed_for(1) + F, F=F, C=C, n_fit_per_class=40,
+                                    n_score_per_class=1)
+        mu = torch.as_tensor(w["mu"], dtype=torch.float32, device=device)
+        sd = torch.as_tensor(w["sd"], dtype=torch.float32, device=device)
+        g = torch.Generator(device=device)
+        g.manual_seed(synth.seed_for(1) + 7 * F)
+        y = torch.randint(0, C, (N,), generator=g, device=device, dtype=torch.int32)
+        X = torch.empty((N, F), dtype=torch.float32, device=device)
+        for r0 in range(0, N, 1 << 18):
+            yy = y[r0:r0 + (1 << 18)].long()
+            X[r0:r0 + yy.shape[0]] = torch.randn((yy.shape[0], F), generator=g, device=device) \
+                * sd[yy] + mu[yy]
+        Xfit = torch.from_numpy(w["X_fit"]).to(device)
+        yfit = torch.from_numpy(w["y_fit"]).to(device)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            model = nb.fit(Xfit, yfit, C, kind=nb.NB_GAUSSIAN, stream=stream)
+        stream.synchronize()
+        out = _out(N, C, device)
+        out["logpost"] = None
+
+        def timed(recheck, want_lp, reps=steps):
+            o = dict(out)
+            if want_lp:
+                o["logpost"] = torch.empty((N, C), dtype=torch.float32, device=device)
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    nb.score(model, X, want_logpost=want_lp, recheck=recheck, out=o,
+                             stream=stream)
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    nb.score(model, X, want_logpost=want_lp, recheck=recheck, out=o,
+                             stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+            nre = int(o["n_rechecked"].item())
+            lab = o["label"]
+            del o
+            return e0.elapsed_time(e1) / reps, nre, lab
+
+        path = nb.score_path(model, X, nb.NB_RECHECK_LABEL)
+        with ClockSampler(device.index or 0) as clk:
+            tc_ms, tc_re, tc_lab = timed(nb.NB_RECHECK_LABEL, False)
+        clk_all.append(clk.summary())
+        model.set_tile_config(nb.NB_VARIANT_REGISTER, 0, 0, 0)
+        cc_ms, cc_re, cc_lab = timed(nb.NB_RECHECK_LABEL, False)
+        agree = bool(torch.equal(tc_lab, cc_lab))
+        del tc_lab, cc_lab
+        cc_lp_ms, cc_lp_re, _ = timed(nb.NB_RECHECK_LP, True, reps=2)
+        model.set_tile_config(nb.NB_VARIANT_PIPELINED, 0, 0, 0)
+        tc_lp_ms, tc_lp_re, _ = timed(nb.NB_RECHECK_LP, True, reps=2)
+        Cp = (C + 15) // 16 * 16
+        bytes_ = N * F * 4 + N * 5
+        rows.append({
+            "F": F, "files": N, "path": path,
+            "tensor_core_ms": tc_ms, "tensor_core_files_per_s": N / (tc_ms * 1e-3),
+            "tensor_core_recheck_frac": tc_re / N,
+            "cuda_core_ms": cc_ms, "cuda_core_recheck_frac": cc_re / N,
+            "labels_agree": agree,
+            "speedup": cc_ms / tc_ms,
+            "hbm_frac": bytes_ / (tc_ms * 1e-3) / 1e9 / hbm_peak,
+            "executed_tensor_tflops": 2.0 * N * Cp * 8 * ((F + 7) // 8 * 8) / (tc_ms * 1e-3)
+            / 1e12,
+            "log_posterior_mode": {"cuda_core_ms": cc_lp_ms,
+                                   "cuda_core_recheck_frac": cc_lp_re / N,
+                                   "tensor_core_ms": tc_lp_ms,
+                                   "tensor_core_recheck_frac": tc_lp_re / N},
+        })
+        del X, y, out, model
+        torch.cuda.empty_cache()
+    return {"workload": f"Gaussian NB, C={C}, class means U(0,10), deviations U(0.5,3), "
+                        f"x ~ N(mu_y, sd_y^2) FP32, uniform labels; fit on 40 files per class, "
+                        f"score {args.gmc_bytes >> 30} GiB of rows per F, label mode "
+                        f"(margins, no log posteriors)",
+            "hbm_peak_gbs": hbm_peak, "tensor_peak_tflops": tflops, "peak_kind": peak_kind,
+            "per_F": rows, "clocks": clk_all[0] if clk_all else None}
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample of the same workload)
 # ----------------------------------------------------------------------------
@@ -953,6 +1056,9 @@ def main():
                     help="print only the C=64, F=8192 many-class measurement")
     ap.add_argument("--mc-n", type=int, default=2_000_000)
     ap.add_argument("--mc-sub", type=int, default=131072)
+    ap.add_argument("--gaussian-mc", action="store_true",
+                    help="print only the C=64 Gaussian many-class sweep (F = 64..1024)")
+    ap.add_argument("--gmc-bytes", type=int, default=2 << 30)
     ap.add_argument("--groupwise", action="store_true",
                     help="print only the group-wise pipeline (size groups, top-k opcodes)")
     ap.add_argument("--gw-n", type=int, default=1_000_000)
@@ -991,6 +1097,11 @@ def main():
         r = run_many_class(args, device)
         if rank == 0:
             print(json.dumps({"many_class": r}), flush=True)
+        return 0
+    if args.gaussian_mc:
+        r = run_gauss_mc(args, device)
+        if rank == 0:
+            print(json.dumps({"gaussian_many_class": r}), flush=True)
         return 0
     if args.groupwise:
         r = run_groupwise(args, device)

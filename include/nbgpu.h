@@ -132,6 +132,13 @@ typedef struct nb_server nb_server;
  *            NB_VARIANT_AUTO / NB_VARIANT_PIPELINED take the tensor-core
  *            scorer (fixed-point weights, exact accumulation),
  *            NB_VARIANT_REGISTER the CUDA-core scorer.
+ *            Gaussian, 3..64 classes, F <= 8192, X 16-byte aligned and ld a
+ *            multiple of 4: NB_VARIANT_AUTO takes the tensor-core scorer
+ *            (FP16 limbs, FP32 accumulation, rigorous per-row bound) in the
+ *            label and OFF recheck modes and the CUDA-core scorer in the
+ *            log-posterior mode (its bound leaves most rows to FP64 there);
+ *            NB_VARIANT_PIPELINED takes the tensor-core scorer in every mode;
+ *            NB_VARIANT_REGISTER the CUDA-core scorer.
  *   stages, rows_per_stage: pipeline depth and rows per shared-memory stage
  *            (0 = defaults: stages of 16-48 KB filling ~100-180 KB per block);
  *   rows_per_warp: 1 (32 lanes per row) or 2 (16 lanes per row, more table
@@ -244,6 +251,20 @@ NB_API nb_status nb_score_group(const nb_model* model, const void* X, nb_dtype d
                          int64_t n, int64_t ld, uint8_t* label, float* margin,
                          float* logpost, const nb_score_opts* opts,
                          void* cuda_stream, int64_t* n_rechecked);
+
+/* The scorer nb_score_group launches for these arguments (before its FP64
+ * recheck launch).  Host only: reads the model's shape and tile
+ * configuration and the address and pitch of X, launches nothing. */
+typedef enum {
+  NB_PATH_TWO_CLASS = 0,      /* two-class difference-form scorer */
+  NB_PATH_TENSOR = 1,         /* many-class multinomial tensor-core scorer */
+  NB_PATH_TENSOR_GAUSS = 2,   /* many-class Gaussian tensor-core scorer */
+  NB_PATH_GENERAL = 3         /* CUDA-core scorer (either kind) */
+} nb_path;
+/* Returns an nb_path, or -1 (and sets the last error) when model is NULL or
+ * recheck is not an nb_recheck. */
+NB_API int nb_score_path(const nb_model* model, const void* X, nb_dtype dtype, int64_t ld,
+                         int recheck);
 
 /* ---- batches of groups: one persistent launch per kernel family ----------
  * The paper scores files group by group, each group with its own model

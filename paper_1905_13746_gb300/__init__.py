@@ -51,6 +51,7 @@ class NbTileConfig(ctypes.Structure):
 
 
 NB_VARIANT_AUTO, NB_VARIANT_PIPELINED, NB_VARIANT_REGISTER = 0, 1, 2
+NB_PATH_TWO_CLASS, NB_PATH_TENSOR, NB_PATH_TENSOR_GAUSS, NB_PATH_GENERAL = 0, 1, 2, 3
 NB_SELECT_TOTAL, NB_SELECT_FILES = 0, 1
 ST_BAD_ROUTE = 32          # status bit of nb_route / nb_gather / nb_groupwise_status
 
@@ -126,6 +127,7 @@ _SIGS = [
     ("nb_groupwise_classify", ctypes.c_int, [_P, _P, _i64, _P, _i64, _P, _P, _P, _P, _P]),
     ("nb_groupwise_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("nb_groupwise_destroy", None, [_P]),
+    ("nb_score_path", ctypes.c_int, [_P, _P, ctypes.c_int, _i64, ctypes.c_int]),
     ("nb_last_error", ctypes.c_char_p, []),
     ("nb_kernel_launches", ctypes.c_uint64, []),
     ("nb_version", ctypes.c_char_p, []),
@@ -387,6 +389,15 @@ def score(model, X, want_logpost=True, recheck=NB_RECHECK_LP, stream=None, out=N
                    want_logpost=want_logpost, recheck=recheck, aux=Xf.aux(), stream=stream,
                    n_rechecked=out["n_rechecked"].data_ptr())
     return out
+
+
+def score_path(model, X, recheck=NB_RECHECK_LP):
+    """The NB_PATH_* scorer that score(model, X, recheck=recheck) launches."""
+    Xf = as_features(X)
+    r = lib().nb_score_path(model.handle, Xf.data.data_ptr(), Xf.dtype_code, Xf.ld, recheck)
+    if r < 0:
+        raise NbError(NB_EINVAL, nb_last_error())
+    return r
 
 
 # ---- batches of groups -----------------------------------------------------

@@ -82,6 +82,14 @@ static nb_status alloc_model(nb_model* m) {
   const size_t o_tcw = take(tc ? tc_w_bytes(m->C, m->F) : 0);
   const size_t o_tcq = take(tc ? sizeof(int32_t) * C * F : 0);
   const size_t o_tch = take(tc ? sizeof(TcHeader) : 0);
+  const bool tg = tcg_tables(m->kind, m->C, m->F);
+  const int F8 = (m->F + kTcgFS - 1) / kTcgFS * kTcgFS;
+  const size_t o_tgw = take(tg ? tcg_w_bytes(m->C, m->F) : 0);
+  const size_t o_tgk = take(tg ? sizeof(float) * C : 0);
+  const size_t o_tgc = take(tg ? sizeof(float) * F8 : 0);
+  const size_t o_tgb = take(tg ? sizeof(float) * F8 : 0);
+  const size_t o_tga = take(tg ? sizeof(float) * F8 : 0);
+  const size_t o_tgh = take(tg ? sizeof(TcgHeader) : 0);
   void* mem = nullptr;
   cudaError_t e = cudaMalloc(&mem, off);
   if (e != cudaSuccess) return cuda_status(e, "cudaMalloc(model)");
@@ -114,6 +122,12 @@ static nb_status alloc_model(nb_model* m) {
   d.tc_w = tc ? reinterpret_cast<uint8_t*>(b + o_tcw) : nullptr;
   d.tc_q = tc ? reinterpret_cast<int32_t*>(b + o_tcq) : nullptr;
   d.tc_hdr = tc ? reinterpret_cast<TcHeader*>(b + o_tch) : nullptr;
+  if (tg) d.tc_w = reinterpret_cast<uint8_t*>(b + o_tgw);
+  d.tcg_kc = tg ? reinterpret_cast<float*>(b + o_tgk) : nullptr;
+  d.tcg_ctr = tg ? reinterpret_cast<float*>(b + o_tgc) : nullptr;
+  d.tcg_bmax = tg ? reinterpret_cast<float*>(b + o_tgb) : nullptr;
+  d.tcg_amax = tg ? reinterpret_cast<float*>(b + o_tga) : nullptr;
+  d.tcg_hdr = tg ? reinterpret_cast<TcgHeader*>(b + o_tgh) : nullptr;
   return NB_OK;
 }
 
@@ -184,8 +198,8 @@ static nb_status check_fit_args(nb_kind kind, const void* X, nb_dtype dtype, int
       set_error("fit: Gaussian models take F32 features");
       return NB_EINVAL;
     }
-    if (C > 32) {
-      set_error("fit: Gaussian models support C <= 32");
+    if (C > kTcMaxC) {
+      set_error("fit: Gaussian models support C <= %d", kTcMaxC);
       return NB_EUNSUPPORTED;
     }
     if (n < 1 || !(vs >= 0.0)) {
@@ -387,6 +401,25 @@ extern "C" void nb_model_free(nb_model* m) {
   delete m;
 }
 
+static nb_path score_path(const nb_model* m, const void* X, nb_dtype dtype, int64_t ld,
+                          int recheck) {
+  const bool aligned = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                       ((ld * elem_size(dtype)) % 16 == 0);
+  if (m->kind == NB_MULTINOMIAL && m->C == 2 && aligned) return NB_PATH_TWO_CLASS;
+  if (tc_eligible(m, dtype, X, ld)) return NB_PATH_TENSOR;
+  if (dtype == NB_F32 && tcg_eligible(m, X, ld, recheck)) return NB_PATH_TENSOR_GAUSS;
+  return NB_PATH_GENERAL;
+}
+
+extern "C" int nb_score_path(const nb_model* m, const void* X, nb_dtype dtype, int64_t ld,
+                             int recheck) {
+  if (!m || recheck < NB_RECHECK_OFF || recheck > NB_RECHECK_LP) {
+    set_error("nb_score_path: NULL model or unknown recheck mode");
+    return -1;
+  }
+  return (int)score_path(m, X, dtype, ld, recheck);
+}
+
 extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype dtype, int64_t n,
                                     int64_t ld, uint8_t* label, float* margin, float* logpost,
                                     const nb_score_opts* opts, void* cuda_stream,
@@ -434,19 +467,19 @@ extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype d
   if (n_rechecked) NB_TRY_CUDA(cudaMemsetAsync(n_rechecked, 0, sizeof(int64_t), st), "memset");
   ScoreOut o{label, margin, logpost, n_rechecked, want_lp, recheck};
   nb_status s;
-  const int es = elem_size(dtype);
-  const bool aligned =
-      ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ld * es) % 16 == 0);
-  if (m->kind == NB_MULTINOMIAL && m->C == 2 && aligned) {
-    // the two-class scorers count the rows they mark, so the recheck can skip
-    // its scan when there are none
-    o.counted = n_rechecked != nullptr;
-    s = launch_score2(m, X, dtype, n, ld, aux, o, st);
+  switch (score_path(m, X, dtype, ld, recheck)) {
+    case NB_PATH_TWO_CLASS:
+      // the two-class scorers count the rows they mark, so the recheck can
+      // skip its scan when there are none
+      o.counted = n_rechecked != nullptr;
+      s = launch_score2(m, X, dtype, n, ld, aux, o, st);
+      break;
+    case NB_PATH_TENSOR: s = launch_score_tc(m, X, n, ld, aux, o, st); break;
+    case NB_PATH_TENSOR_GAUSS:
+      s = launch_score_tcg(m, static_cast<const float*>(X), n, ld, o, st);
+      break;
+    default: s = launch_score_general(m, X, dtype, n, ld, aux, o, st); break;
   }
-  else if (tc_eligible(m, dtype, X, ld))
-    s = launch_score_tc(m, X, n, ld, aux, o, st);
-  else
-    s = launch_score_general(m, X, dtype, n, ld, aux, o, st);
   if (s != NB_OK) return s;
   return launch_recheck(m, X, dtype, n, ld, aux, o, st);
 }

@@ -892,45 +892,45 @@ __global__ void __launch_bounds__(256) k_gauss_partial(const float* X, int64_t l
                                                        int F, int C, const int32_t* y, int pass,
                                                        const double* mu_c, const double* mu_all,
                                                        double* partial, int64_t chunk_rows,
-                                                       int* status) {
+                                                       int tile, int* status) {
   // partial layout: [chunk][slot 0..C][F]
-  extern __shared__ double acc[];   // [8 warps][C+1][kGTile]
+  extern __shared__ double acc[];   // [8 warps][C+1][tile]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = blockIdx.y * kGTile;
+  const int j0 = blockIdx.y * tile;
   const int64_t r0 = (int64_t)blockIdx.x * chunk_rows;
   int64_t r1 = r0 + chunk_rows;
   if (r1 > n) r1 = n;
   const int S = C + 1;
-  for (int k = threadIdx.x; k < 8 * S * kGTile; k += blockDim.x) acc[k] = 0.0;
+  for (int k = threadIdx.x; k < 8 * S * tile; k += blockDim.x) acc[k] = 0.0;
   __syncthreads();
-  double* my = acc + (size_t)warp * S * kGTile;
+  double* my = acc + (size_t)warp * S * tile;
   for (int64_t i = r0 + warp; i < r1; i += 8) {
     const int c = y[i];
     if (c < 0 || c >= C) {
       if (lane == 0) atomicOr(status, ST_BAD_LABEL);
       continue;
     }
-    for (int jj = lane; jj < kGTile; jj += 32) {
+    for (int jj = lane; jj < tile; jj += 32) {
       const int j = j0 + jj;
       if (j >= F) break;
       const double x = (double)X[i * ld + j];
       if (!isfinite(x)) atomicOr(status, ST_BAD_VALUE);
       if (pass == 0) {
-        my[c * kGTile + jj] += x;
-        my[C * kGTile + jj] += x;
+        my[c * tile + jj] += x;
+        my[C * tile + jj] += x;
       } else {
         const double dc = x - mu_c[(int64_t)c * F + j];
         const double da = x - mu_all[j];
-        my[c * kGTile + jj] += dc * dc;
-        my[C * kGTile + jj] += da * da;
+        my[c * tile + jj] += dc * dc;
+        my[C * tile + jj] += da * da;
       }
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < S * kGTile; k += blockDim.x) {
+  for (int k = threadIdx.x; k < S * tile; k += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += acc[(size_t)w * S * kGTile + k];
-    const int slot = k / kGTile, jj = k % kGTile, j = j0 + jj;
+    for (int w = 0; w < 8; ++w) s += acc[(size_t)w * S * tile + k];
+    const int slot = k / tile, jj = k % tile, j = j0 + jj;
     if (j < F) partial[((int64_t)blockIdx.x * S + slot) * F + j] = s;
   }
 }
@@ -1033,17 +1033,18 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
   double* partial = static_cast<double*>(scratch);
   double* mu_all = partial + part_elems;
   double* m2_all = mu_all + F;
-  const int smem = (int)(sizeof(double) * 8 * S * kGTile);
+  const int tile = gauss_tile(C);
+  const int smem = (int)(sizeof(double) * 8 * S * tile);
   if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(k_gauss_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem),
                 "cudaFuncSetAttribute");
-  dim3 grid(nchunk, (F + kGTile - 1) / kGTile);
+  dim3 grid(nchunk, (F + tile - 1) / tile);
   const int rb = (S * F + 255) / 256;
   for (int pass = 0; pass < 2; ++pass) {
     count_launch();
     k_gauss_partial<<<grid, 256, smem, st>>>(X, ld, n, F, C, y, pass, d.p0, mu_all, partial,
-                                             chunk_rows, d.status);
+                                             chunk_rows, tile, d.status);
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_partial");
     count_launch();
     k_gauss_reduce<<<rb < 1024 ? rb : 1024, 256, 0, st>>>(
@@ -1058,6 +1059,7 @@ nb_status launch_fit_gaussian(nb_model* m, const float* X, int64_t n, int64_t ld
                                        d.g_mu, d.g_ivar, d.g_const, d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_gauss_finalize");
   NB_TRY_CUDA(cudaFreeAsync(scratch, st), "cudaFreeAsync(gauss scratch)");
+  if (d.tcg_kc) return launch_derive_tcg(m, st);
   return NB_OK;
 }
 

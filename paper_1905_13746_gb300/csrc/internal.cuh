@@ -73,6 +73,14 @@ struct TcHeader {
 // tensor-core scorer limits: classes, features
 constexpr int kTcMaxC = 64;
 constexpr int kTcMaxF = 32768;
+constexpr int kTcgMaxF = 8192;   // Gaussian tensor-core tables
+constexpr int kTcgFS = 32;       // ... features per stage (a multiple of 8 dividing 32)
+
+// scalars of the Gaussian tensor-core tables (one struct in HBM)
+struct TcgHeader {
+  int bad;            // a weight outside the FP16 range: the tables are not used
+  float wsum;         // sum_j (max_c |B_cj| + max_c |A_cj|), rounded up
+};
 
 // ---------------------------------------------------------------------------
 // model (library-owned)
@@ -107,6 +115,13 @@ struct ModelDev {
   float* g_mu;         // C x F_pad
   float* g_ivar;       // C x F_pad  1 / var
   float* g_const;      // C          gconst in FP32
+  // Gaussian tensor-core tables (3 <= C <= kTcMaxC, F <= kTcgMaxF), else nullptr;
+  // the FP16 limbs of B and A go to tc_w
+  float* tcg_kc;       // C          K_c
+  float* tcg_ctr;      // F rounded up to kTcgFS: centres m_j
+  float* tcg_bmax;     // ... max_c |B_cj|
+  float* tcg_amax;     // ... max_c |A_cj|
+  TcgHeader* tcg_hdr;  // 1
 };
 
 }  // namespace nbg
@@ -173,6 +188,18 @@ inline bool tc_tables(nb_kind kind, int C, int F) {
 }
 bool tc_eligible(const nb_model* m, nb_dtype dt, const void* X, int64_t ld);
 nb_status launch_derive_tc(nb_model* m, cudaStream_t st);
+
+// many-class Gaussian tensor-core scorer (score_tcg.cu)
+inline size_t tcg_w_bytes(int C, int F) {
+  return (size_t)((F + kTcgFS - 1) / kTcgFS) * tc_classes_padded(C) * (16 * kTcgFS);
+}
+inline bool tcg_tables(nb_kind kind, int C, int F) {
+  return kind == NB_GAUSSIAN && C >= 3 && C <= kTcMaxC && F <= kTcgMaxF;
+}
+bool tcg_eligible(const nb_model* m, const void* X, int64_t ld, int recheck);
+nb_status launch_derive_tcg(nb_model* m, cudaStream_t st);
+nb_status launch_score_tcg(const nb_model* m, const float* X, int64_t n, int64_t ld,
+                           const ScoreOut& o, cudaStream_t st);
 nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t ld,
                           const nb_aux* aux, const ScoreOut& o, cudaStream_t st);
 
@@ -200,6 +227,10 @@ void count_launch();
 // Gaussian fit: rows per deterministic partial sum, features per block tile
 constexpr int kGChunkRows = 256;
 constexpr int kGTile = 64;
+// features per block tile of a fit with C classes: 64 up to 32 classes, 32
+// above (the block's shared partial sums, 8 (C + 1) tile doubles, must fit);
+// the tile changes which block sums a feature, not the order of its sums
+inline int gauss_tile(int C) { return C <= 32 ? kGTile : kGTile / 2; }
 // rows per partial sum of a fit of n rows: 32 for small fits (more blocks in
 // flight), else kGChunkRows; the partials are summed in chunk order, so the
 // result depends only on n (every Gaussian fit path uses this rule)
@@ -218,7 +249,7 @@ __global__ void k_label_hist(const int32_t* y, int64_t n, int C, unsigned long l
 __global__ void k_gauss_partial(const float* X, int64_t ld, int64_t n, int F, int C,
                                 const int32_t* y, int pass, const double* mu_c,
                                 const double* mu_all, double* partial, int64_t chunk_rows,
-                                int* status);
+                                int tile, int* status);
 __global__ void k_gauss_reduce(const double* partial, int nchunk, int F, int C,
                                const unsigned long long* nc, int64_t n, int pass, double* mu_c,
                                double* mu_all, double* m2_c, double* m2_all);

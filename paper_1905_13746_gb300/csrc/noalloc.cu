@@ -116,17 +116,18 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
   k_label_hist<<<(unsigned)(g < sms * 4 ? g : sms * 4), 256, 0, st>>>(
       y, n, C, reinterpret_cast<unsigned long long*>(d.nc), d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_label_hist");
-  const int smem = (int)(sizeof(double) * 8 * S * kGTile);
+  const int tile = gauss_tile(C);
+  const int smem = (int)(sizeof(double) * 8 * S * tile);
   if (smem > kSmemOptIn)
     NB_TRY_CUDA(cudaFuncSetAttribute(k_gauss_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem),
                 "cudaFuncSetAttribute");
-  const dim3 grid((unsigned)nchunk, (F + kGTile - 1) / kGTile);
+  const dim3 grid((unsigned)nchunk, (F + tile - 1) / tile);
   const int rb = (S * F + 255) / 256;
   for (int pass = 0; pass < 2; ++pass) {
     count_launch();
     k_gauss_partial<<<grid, 256, smem, st>>>(X, ld, n, F, C, y, pass, d.p0, mu_all, partial,
-                                             chunk_rows, d.status);
+                                             chunk_rows, tile, d.status);
     NB_TRY_CUDA(cudaGetLastError(), "k_gauss_partial");
     count_launch();
     k_gauss_reduce<<<rb < 1024 ? rb : 1024, 256, 0, st>>>(
@@ -140,6 +141,10 @@ extern "C" nb_status nb_refit_gaussian_noalloc(nb_model* m, const float* X, int6
                                        prior != nullptr, d.p0, d.p1, d.log_pi, d.gconst, d.g_mu,
                                        d.g_ivar, d.g_const, d.status);
   NB_TRY_CUDA(cudaGetLastError(), "k_gauss_finalize");
+  if (d.tcg_kc) {
+    s = launch_derive_tcg(m, st);
+    if (s != NB_OK) return s;
+  }
   if (!(opts && opts->no_sync)) {
     int w = 0;
     NB_TRY_CUDA(cudaMemcpyAsync(&w, d.status, sizeof(int), cudaMemcpyDeviceToHost, st),

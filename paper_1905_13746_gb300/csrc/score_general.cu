@@ -301,7 +301,7 @@ struct GGArgs {
 };
 
 __global__ void __launch_bounds__(256) k_score_gauss(const GGArgs a) {
-  __shared__ float ssh[8][32], tsh[8][32];
+  __shared__ float ssh[8][kTcMaxC], tsh[8][kTcMaxC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   const int kdepth = (a.F + 31) / 32 + 5 + 8;

@@ -42,9 +42,9 @@ def seed_for(config_index: int) -> int:
 # Gaussian workload
 # ----------------------------------------------------------------------------
 def gaussian_workload(seed, F=64, C=2, n_fit_per_class=1000,
-                      n_score_per_class=5000):
+                      n_score_per_class=5000, spread=10.0):
     rng = np.random.default_rng(seed)
-    mu = rng.uniform(0.0, 10.0, size=(C, F))
+    mu = rng.uniform(0.0, spread, size=(C, F))
     sd = rng.uniform(0.5, 3.0, size=(C, F))
 
     def draw(n_per):
