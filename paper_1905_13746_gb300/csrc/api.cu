@@ -68,7 +68,7 @@ static nb_status alloc_model(nb_model* m) {
   const size_t o_c2 = take(sizeof(C2Header));
   const size_t o_delta = take(sizeof(float) * Fp);
   const size_t o_dq = take(sizeof(int32_t) * Fp);
-  const size_t o_limbs = take(3 * Fp);
+  const size_t o_limbs = take(7 * Fp);   // three limb planes + packed limb words
   const size_t o_il0 = take(sizeof(float) * Fp);
   const size_t o_il1 = take(sizeof(float) * Fp);
   const size_t o_il2 = take(sizeof(float) * Fp);

@@ -461,6 +461,9 @@ __global__ void __launch_bounds__(1024) k_derive_c2(const double* log_theta, con
     L[((size_t)0 * nvec8 + v) * 16 + b] = (unsigned char)(q0 & 255);
     L[((size_t)1 * nvec8 + v) * 16 + b] = (unsigned char)(q1 & 255);
     L[((size_t)2 * nvec8 + v) * 16 + b] = (unsigned char)(q2 & 255);
+    // the same limbs packed into one word per feature (overflow entries)
+    reinterpret_cast<uint32_t*>(L + (size_t)3 * F_pad)[j] =
+        (uint32_t)(q0 & 255) | ((uint32_t)(q1 & 255) << 8) | ((uint32_t)(q2 & 255) << 16);
     // FP32 tables for 4 / 8 / 16 elements per vector: quad q of vector v is
     // slot q * (F_pad / EPV) + v
     {
@@ -671,6 +674,9 @@ __global__ void __launch_bounds__(kFinT) k_fit_finish_c2(
       L[((size_t)0 * nvec8 + v) * 16 + b] = (unsigned char)(q0 & 255);
       L[((size_t)1 * nvec8 + v) * 16 + b] = (unsigned char)(q1 & 255);
       L[((size_t)2 * nvec8 + v) * 16 + b] = (unsigned char)(q2 & 255);
+      // the same limbs packed into one word per feature (overflow entries)
+      reinterpret_cast<uint32_t*>(L + (size_t)3 * F_pad)[jj] =
+          (uint32_t)(q0 & 255) | ((uint32_t)(q1 & 255) << 8) | ((uint32_t)(q2 & 255) << 16);
     }
   }
   if (tid < 2) bias[tid] = (float)log_pi[tid];

@@ -101,7 +101,8 @@ struct ModelDev {
   C2Header* c2;        // 1
   float* delta;        // F_pad      FP32 Delta, plain order
   int32_t* delta_q;    // F_pad      fixed-point Delta
-  uint4* limbs;        // 3 * nvec8  int8 limbs of delta_q, interleaved (u8 path)
+  uint4* limbs;        // 3 * nvec8  int8 limbs of delta_q, interleaved (u8 path), then
+                       //            F_pad packed words (limb l in byte l)
   float4* il[3];       // interleaved FP32 quads for 4/8/16 elements per vector
   // general-C tables (CUDA-core scorer)
   float* w;            // C x F_pad  centred weights log theta_cj - mean_c log theta_cj

@@ -12,9 +12,9 @@
 // total T are accumulated with dp4a in four int32 sums per row, reduced by a
 // butterfly inside the lane group (exact), and combined into an int64 only
 // when the row is finished.  Overflow entries (count - 255 at a column) are
-// split over the row's lanes and added limb by limb, the limbs read from the
-// shared-memory copy of the table.  FP32 paths decode each vector and FMA
-// into four accumulators, then the same butterfly.
+// split over the row's lanes and added limb by limb, the column's three limbs
+// read as one packed word (staged after the limb planes).  FP32 paths decode
+// each vector and FMA into four accumulators, then the same butterfly.
 //
 // Finished rows wait in registers (lane j holds the j-th) and are finalised
 // 32 at a time, one lane per row: label, margin, log posteriors, FP64-recheck
@@ -66,8 +66,10 @@ __device__ __forceinline__ uint32_t u8_keep_mask(int vb) {
 }
 
 // FULL: every lane's KV vectors lie inside the row (no bound or tail checks);
-// the kernel then carries no per-vector branches.
-template <int DT, int KV, int RPW, int NCW, bool FULL>
+// the kernel then carries no per-vector branches.  OVF (u8 only): the rows
+// carry an overflow list, and the packed limb words (one 32-bit word per
+// feature, limb l in byte l) follow the three limb planes in shared memory.
+template <int DT, int KV, int RPW, int NCW, bool FULL, bool OVF>
 __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
     k_score2_pipe(const S2Args a, const PipeArgs p) {
   constexpr int LPR = 32 / RPW;
@@ -122,7 +124,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
         wq[kv][q] = (FULL || v < nv) ? tab[q * nt + v] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  const signed char* limb = reinterpret_cast<const signed char*>(sm);   // u8 overflow limbs
+  // u8 overflow entries: the packed limb words after the three planes
+  const uint32_t* limbw = reinterpret_cast<const uint32_t*>(sm + (size_t)3 * nt * 16);
   const int tail_v = (!FULL && a.F < nv * EPV) ? nv - 1 : -1;
 
   RowSum res{0, 0, 0, 0u, 0.f, 0.f};
@@ -155,6 +158,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
       const unsigned char* rp = st + (size_t)(valid ? r : 0) * a.ld_bytes;
       RowSum mine{0, 0, 0, 0u, 0.f, 0.f};
       if (DT == NB_U8) {
+        // the row's staged overflow range (stage-relative), read before the
+        // dense part so that its latency hides behind the dp4a chains
+        int e0 = 0, e1 = 0;
+        if (OVF && valid && in_smem) {
+          e0 = (int)(sp[r] - ebase);
+          e1 = (int)(sp[r + 1] - ebase);
+        }
         // two independent sets of the four dp4a chains (even / odd vectors)
         int c0[2] = {0, 0}, c1[2] = {0, 0}, c2[2] = {0, 0};
         uint32_t ct[2] = {0u, 0u};
@@ -190,19 +200,35 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
         }
         int a0 = c0[0] + c0[1], a1 = c1[0] + c1[1], a2 = c2[0] + c2[1];
         uint32_t tt = ct[0] + ct[1];
-        if (a.ovf_ptr && valid) {
-          const long long k0 = sp[r], k1 = sp[r + 1];
-          for (long long e = k0 + li; e < k1; e += LPR) {
-            const uint32_t col = in_smem ? scol[e - ebase] : a.ovf_col[e];
-            const int add = in_smem ? sadd[e - ebase] : a.ovf_add[e];
-            if (col < (uint32_t)a.F) {
-              const int vv = col >> 4, b = col & 15;
-              a0 += add * (int)limb[(size_t)vv * 16 + b];
-              a1 += add * (int)limb[((size_t)nt + vv) * 16 + b];
-              a2 += add * (int)limb[((size_t)2 * nt + vv) * 16 + b];
-              tt += (uint32_t)add;
-            } else {
-              atomicOr(a.status, ST_OVF_RANGE);
+        if (OVF && valid) {
+          if (in_smem) {
+            for (int e = e0 + li; e < e1; e += LPR) {
+              const uint32_t col = scol[e];
+              const int add = sadd[e];
+              if (col < (uint32_t)a.F) {
+                const uint32_t w = limbw[col];
+                a0 += add * (int)(int8_t)(w & 255u);
+                a1 += add * (int)(int8_t)((w >> 8) & 255u);
+                a2 += add * (int)(int8_t)((w >> 16) & 255u);
+                tt += (uint32_t)add;
+              } else {
+                atomicOr(a.status, ST_OVF_RANGE);
+              }
+            }
+          } else {
+            const long long k0 = sp[r], k1 = sp[r + 1];
+            for (long long e = k0 + li; e < k1; e += LPR) {
+              const uint32_t col = a.ovf_col[e];
+              const int add = a.ovf_add[e];
+              if (col < (uint32_t)a.F) {
+                const uint32_t w = limbw[col];
+                a0 += add * (int)(int8_t)(w & 255u);
+                a1 += add * (int)(int8_t)((w >> 8) & 255u);
+                a2 += add * (int)(int8_t)((w >> 16) & 255u);
+                tt += (uint32_t)add;
+              } else {
+                atomicOr(a.status, ST_OVF_RANGE);
+              }
             }
           }
         }
@@ -272,9 +298,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 // launcher: NB_EUNSUPPORTED when the row does not fit (the caller then uses
 // the register-streaming kernel)
 // ---------------------------------------------------------------------------
-template <int DT, int KV, int RPW, int NCW, bool FULL>
+template <int DT, int KV, int RPW, int NCW, bool FULL, bool OVF>
 static nb_status run_pipe(const S2Args& a, const PipeArgs& p, int smem, cudaStream_t st) {
-  auto kern = k_score2_pipe<DT, KV, RPW, NCW, FULL>;
+  auto kern = k_score2_pipe<DT, KV, RPW, NCW, FULL, OVF>;
   if (smem > kSmemOptIn)   // per device and function: set at every launch
     NB_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                 "cudaFuncSetAttribute(pipe)");
@@ -305,6 +331,10 @@ nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_
   const int kv = (a.nvec_row + lpr - 1) / lpr;
   const int kv_max = dt == NB_F32 ? 8 : 4;
   if (kv < 1 || kv > kv_max || a.ld_bytes > 8192) return NB_EUNSUPPORTED;
+  // u8 rows with an overflow list also stage the packed limb words (4 bytes a
+  // feature) after the three limb planes
+  const bool ovf = dt == NB_U8 && a.ovf_ptr != nullptr;
+  const uint32_t tab_all = ovf ? 7u * (uint32_t)(a.nvec_tab * 16) : a.table_bytes;
   // Stage plan for `ncw` consumer warps: rows per stage in whole passes of
   // ncw * rpw rows, 16-48 KB; stages filling ~100 KB (eight consumers, two
   // blocks per SM) or ~180 KB (twelve, one block) unless given.
@@ -318,11 +348,11 @@ nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_
     int S = stages;
     if (S <= 0) {
       PipeArgs q{};
-      pipe_layout(q, rs, 1, a.ld_bytes, stage_entries != 0, false, a.table_bytes, a.n);
+      pipe_layout(q, rs, 1, a.ld_bytes, stage_entries != 0, false, tab_all, a.n);
       S = q.stages_off + q.stage_bytes > budget ? 2 : (int)((budget - q.stages_off) / q.stage_bytes);
     }
     S = S < 2 ? 2 : (S > kMaxStages ? kMaxStages : S);
-    pipe_layout(p, rs, S, a.ld_bytes, stage_entries != 0, false, a.table_bytes, a.n);
+    pipe_layout(p, rs, S, a.ld_bytes, stage_entries != 0, false, tab_all, a.n);
     return (int)(p.stages_off + (uint32_t)p.S * p.stage_bytes);
   };
   int ncw = (rpw == 1 && (dt == NB_F32 ? kv <= 8 : kv <= 2)) ? 8 : 12;
@@ -342,10 +372,14 @@ nb_status launch_score2_pipe(const S2Args& a, nb_dtype dt, int stages, int rows_
   ak.k_base = kv * ((16 / elem_size(dt)) / 4) + 2 + (rpw == 2 ? 4 : 5) + 2;
   // rows that fill every lane's vectors exactly take the branch-free kernel
   const bool full = a.nvec_row == kv * lpr && (a.F * elem_size(dt)) % 16 == 0;
-#define NB_PIPE_CASE(D, K, R, N)                                               \
-  if (dt == D && kv == K && rpw == R && ncw == N)                              \
-    return full ? run_pipe<D, K, R, N, true>(ak, p, smem, st)                  \
-                : run_pipe<D, K, R, N, false>(ak, p, smem, st);
+#define NB_PIPE_CASE(D, K, R, N)                                                            \
+  if (dt == D && kv == K && rpw == R && ncw == N) {                                         \
+    if (D == NB_U8 && ovf)                                                                  \
+      return full ? run_pipe<D, K, R, N, true, D == NB_U8>(ak, p, smem, st)                 \
+                  : run_pipe<D, K, R, N, false, D == NB_U8>(ak, p, smem, st);               \
+    return full ? run_pipe<D, K, R, N, true, false>(ak, p, smem, st)                        \
+                : run_pipe<D, K, R, N, false, false>(ak, p, smem, st);                      \
+  }
 #define NB_PIPE_DT(D)                                                                        \
   NB_PIPE_CASE(D, 1, 1, 8) NB_PIPE_CASE(D, 2, 1, 8) NB_PIPE_CASE(D, 3, 1, 12)                 \
   NB_PIPE_CASE(D, 4, 1, 12) NB_PIPE_CASE(D, 1, 2, 12) NB_PIPE_CASE(D, 2, 2, 12)               \
