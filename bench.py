@@ -756,6 +756,36 @@ def run_many_class(args, device, steps=None):
     torch.cuda.synchronize()
     f32_sub = time_score(f32, osub)
     del f32
+    # the same N files stored as BF16 and as FP8 E4M3 (counts <= 255: exact in
+    # BF16, rounded to E4M3 with row scale 2^0), scored on the tensor cores with
+    # log posteriors and the FP64 recheck
+    storage = {}
+    for name, tdt, code, esz in (("bf16", torch.bfloat16, nb.NB_BF16, 2),
+                                 ("fp8", torch.float8_e4m3fn, nb.NB_FP8E4M3, 1)):
+        Xs = torch.empty((N, F), dtype=tdt, device=device)
+        for r0 in range(0, N, 1 << 17):
+            Xs[r0:r0 + (1 << 17)] = X[r0:r0 + (1 << 17)].to(torch.float32).to(tdt)
+        fs = nb.Features(Xs.view(torch.uint8) if code == nb.NB_FP8E4M3 else Xs, code)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                nb.score(model, fs, out=out, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                nb.score(model, fs, out=out, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        b_s = N * F * esz + N * (1 + 4 + 4 * C)
+        storage[name] = {"path": nb.score_path(model, fs), "score_ms": ms,
+                         "files_per_s": N / (ms * 1e-3), "gbs": b_s / (ms * 1e-3) / 1e9,
+                         "frac_of_max_t_mem_t_flop":
+                             max(b_s / (hbm_peak * 1e9) * 1e3, t_flop) / ms,
+                         "n_rechecked": int(out["n_rechecked"].item())}
+        del fs, Xs
+        torch.cuda.empty_cache()
     line = {
         "workload": f"multinomial NB, C={C} (Zipf 1.1 priors), N={N} files x F={F} counts "
                     f"(Dirichlet(0.1) profiles, lognormal(8.5, 1) totals, clamped at 255, "
@@ -776,6 +806,7 @@ def run_many_class(args, device, steps=None):
         "subset": {"files": sub, "tensor_core_ms": tc_sub, "cuda_core_ms": cc_sub,
                    "cuda_core_n_rechecked_label_mode": cc_rechecked,
                    "plain_fp32_ms": f32_sub},
+        "storage": storage,
         "clocks": clk.summary(), "gpu_launches": launches,
     }
     return line

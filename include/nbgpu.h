@@ -106,8 +106,10 @@ typedef struct {
  *                       rows that a fast path cannot compute at all are still
  *                       recomputed in FP64: a two-class u8 row whose stored
  *                       counts total 2^24 or more (its int32 limb sums could
- *                       wrap) and tensor-core rows of 2^17 or more counts
- *                       beyond the scorer's exact-redo capacity;
+ *                       wrap), tensor-core rows of 2^17 or more counts beyond
+ *                       the scorer's exact-redo capacity (FP8 and BF16 rows:
+ *                       all of them) and FP8 / BF16 rows outside the
+ *                       tensor-core scorer's count check;
  *   NB_RECHECK_LABEL -- rows whose margin is within the rigorous error bound
  *                       of the fast path are recomputed in FP64, so every
  *                       label equals the FP64 decision;
@@ -128,9 +130,13 @@ typedef struct nb_server nb_server;
  *   variant  two classes: NB_VARIANT_AUTO: TMA-pipelined kernel when the row
  *            fits a stage, else the register-streaming kernel;
  *            NB_VARIANT_PIPELINED / NB_VARIANT_REGISTER: force one.
- *            3..64 classes with u8 storage, F and ld multiples of 16:
+ *            3..64 classes with U8, FP8E4M3 or BF16 storage, X 16-byte
+ *            aligned and ld * element size a multiple of 16:
  *            NB_VARIANT_AUTO / NB_VARIANT_PIPELINED take the tensor-core
- *            scorer (fixed-point weights, exact accumulation),
+ *            scorer (fixed-point weights, exact accumulation; FP8 and BF16
+ *            rows must hold counts: a row with a value that is not an integer
+ *            below 1024 after its row scale, or with an FP8 row exponent
+ *            other than 0 or 1, is recomputed in FP64 instead),
  *            NB_VARIANT_REGISTER the CUDA-core scorer.
  *            Gaussian, 3..64 classes, F <= 8192, X 16-byte aligned and ld a
  *            multiple of 4: NB_VARIANT_AUTO takes the tensor-core scorer
@@ -271,8 +277,10 @@ NB_API int nb_score_path(const nb_model* model, const void* X, nb_dtype dtype, i
  * (Sec. 3 size groups, Sec. 4 per-group models).  A batch scores many groups
  * of uneven size (1 to 10^5+ files) at once: the groups of two-class models
  * in one launch of the pipelined two-class kernel, the groups of many-class
- * models in one launch of the general kernel, then one FP64 recheck launch
- * per family -- independent of the number of groups.  Each row's arithmetic
+ * models in one launch of the tensor-core kernel (U8, FP8E4M3 or BF16 rows
+ * that nb_score_group would score there) and one of the general kernel (the
+ * rest), then one FP64 recheck launch per family -- independent of the number
+ * of groups.  Each row's arithmetic
  * is that of nb_score_group, so a group's results are the same bits alone
  * and inside any batch.
  *

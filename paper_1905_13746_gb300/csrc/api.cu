@@ -474,7 +474,7 @@ extern "C" nb_status nb_score_group(const nb_model* m, const void* X, nb_dtype d
       o.counted = n_rechecked != nullptr;
       s = launch_score2(m, X, dtype, n, ld, aux, o, st);
       break;
-    case NB_PATH_TENSOR: s = launch_score_tc(m, X, n, ld, aux, o, st); break;
+    case NB_PATH_TENSOR: s = launch_score_tc(m, X, dtype, n, ld, aux, o, st); break;
     case NB_PATH_TENSOR_GAUSS:
       s = launch_score_tcg(m, static_cast<const float*>(X), n, ld, o, st);
       break;

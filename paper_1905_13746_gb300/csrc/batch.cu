@@ -88,8 +88,8 @@ static nb_status batch_launch(nb_batch* b, cudaStream_t st) {
   if (!b->fam[2].empty()) {
     nb_status s = launch_score_tc_seg(list_of(b->dev, 2, b->max_groups), dh + 2,
                                       static_cast<char*>(b->dev) + b->maps_off,
-                                      b->fam[2].data(), (int)b->fam[2].size(), b->F, b->want_lp,
-                                      b->recheck, b->status, st);
+                                      b->fam[2].data(), (int)b->fam[2].size(), b->dtype, b->F,
+                                      b->want_lp, b->recheck, b->status, st);
     if (s != NB_OK) return s;
   }
   // also under NB_RECHECK_OFF: rows a scorer could not compute at all are marked
@@ -184,7 +184,8 @@ nb_status nbg::batch_create(const nb_model* const* models, int n_models, nb_dtyp
     b->slot_index.push_back((int)b->fam[f].size());
     b->fam[f].push_back(models[i]);
     int i2 = -1;
-    if (f == 1 && dtype == NB_U8 && models[i]->d.tc_w) {
+    if (f == 1 && (dtype == NB_U8 || dtype == NB_FP8E4M3 || dtype == NB_BF16) &&
+        models[i]->d.tc_w) {
       i2 = (int)b->fam[2].size();
       b->fam[2].push_back(models[i]);
     }
@@ -267,7 +268,7 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
     // a many-class group takes the tensor-core kernel exactly when scoring it
     // alone would, so both give the same bits
     if (f == 1 && g.n > 0 && b->slot_index2[g.model] >= 0 &&
-        tc_group_eligible(b->fam[1][b->slot_index[g.model]], g.X, g.ld))
+        tc_group_eligible(b->fam[1][b->slot_index[g.model]], b->dtype, g.X, g.ld))
       f = 2;
     if (f == 0 && g.n > 0 &&
         (((reinterpret_cast<uintptr_t>(g.X) & 15) != 0) || ((g.ld * es) % 16) != 0 ||
@@ -290,10 +291,12 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
     d.X = static_cast<const char*>(g.X);
     d.ld_bytes = g.ld * es;
     d.n = g.n;
-    d.ovf_ptr = g.aux.ovf_ptr;
-    d.ovf_col = g.aux.ovf_col;
-    d.ovf_add = g.aux.ovf_add;
-    d.row_exp = g.aux.row_exp;
+    // the overflow list belongs to u8 rows, the row scale to FP8 rows
+    const bool u8 = b->dtype == NB_U8;
+    d.ovf_ptr = u8 ? g.aux.ovf_ptr : nullptr;
+    d.ovf_col = u8 ? g.aux.ovf_col : nullptr;
+    d.ovf_add = u8 ? g.aux.ovf_add : nullptr;
+    d.row_exp = b->dtype == NB_FP8E4M3 ? g.aux.row_exp : nullptr;
     d.label = g.label;
     d.margin = g.margin;
     d.logpost = b->want_lp ? g.logpost : nullptr;
@@ -304,7 +307,7 @@ extern "C" nb_status nb_batch_score(nb_batch* b, const nb_group* groups, int n_g
     if (f == 2) {
       nb_status ms = tc_encode_rows(static_cast<char*>(h) + b->maps_off +
                                         (size_t)(hh[2].n_groups - 1) * kTcMapBytes,
-                                    g.X, g.n, b->F, g.ld);
+                                    g.X, g.n, b->F, g.ld * es, es);
       if (ms != NB_OK) return ms;
     }
     tiles[f] += f == 0 ? (g.n + rs - 1) / rs : (f == 1 ? (g.n + 63) / 64 : (g.n + 255) / 256);

@@ -201,7 +201,7 @@ bool tcg_eligible(const nb_model* m, const void* X, int64_t ld, int recheck);
 nb_status launch_derive_tcg(nb_model* m, cudaStream_t st);
 nb_status launch_score_tcg(const nb_model* m, const float* X, int64_t n, int64_t ld,
                            const ScoreOut& o, cudaStream_t st);
-nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t ld,
+nb_status launch_score_tc(const nb_model* m, const void* X, nb_dtype dt, int64_t n, int64_t ld,
                           const nb_aux* aux, const ScoreOut& o, cudaStream_t st);
 
 int num_sms();

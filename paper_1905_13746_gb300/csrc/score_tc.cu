@@ -15,7 +15,12 @@
 // sum over a row stays an integer below 2^24 -- exact in the FP32 accumulator
 // whatever the order of the tensor core's additions -- when the row holds
 // fewer than 2^17 stored counts.  Overflow-list entries (counts above 255) are
-// added exactly on the CUDA cores.  The only errors are the weight
+// added exactly on the CUDA cores.  FP8 E4M3 rows (row scale 2^e, e in {0, 1})
+// and BF16 rows take the same path: E4M3 values convert exactly to FP16 (the
+// row scale multiplies the limb sums in the epilogue), and BF16 values below
+// 1024 as well; the converters check that every value, scaled, is an integer
+// count below 1024 (else the row goes to the FP64 recheck), which keeps the
+// argument above with T counted in scaled units.  The only errors are the weight
 // quantisation, at most T 2^-(S+1) with T the file's token count, and two FP32
 // roundings when the score is formed; the epilogue bounds both and marks the
 // row for the FP64 recheck when the bound does not settle the label (or the
@@ -175,6 +180,46 @@ __device__ __forceinline__ uint32_t u8x2_to_f16x2(uint32_t w, uint32_t sel) {
   return r;
 }
 
+// two E4M3 values (the low 16 bits of w) -> two exact FP16 values
+__device__ __forceinline__ uint32_t e4m3x2_to_f16x2(uint32_t w) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"((unsigned short)w));
+  return r;
+}
+
+// two BF16 values -> two FP16 values (exact for the integers below 1024 that
+// the count check accepts)
+__device__ __forceinline__ uint32_t bf16x2_to_f16x2(uint32_t w) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;"
+      : "=r"(r)
+      : "f"(__uint_as_float(w & 0xFFFF0000u)), "f"(__uint_as_float(w << 16)));
+  return r;
+}
+
+// non-zero if a BF16 half of w is non-zero with magnitude below 2^-14 (its
+// FP16 image would be subnormal or zero, which the count check cannot tell
+// from an exact value)
+__device__ __forceinline__ uint32_t bf16x2_tiny(uint32_t w) {
+  const uint32_t mag = w & 0x7FFF7FFFu;
+  const uint32_t nz = mag + 0x7FFF7FFFu;      // bit 15 of a half set: half >= 1
+  const uint32_t big = mag + 0x47804780u;     // bit 15 of a half set: half >= 0x3880 (2^-14)
+  return nz & ~big & 0x80008000u;
+}
+
+// Count check of an FP16 pair h against the magic pair m2 = (M, M), M = 2^(10-e):
+// with w = h + M (FP16), a half of h is a non-negative multiple of 2^-e below M
+// exactly when that half of w lies in [M, 2M) (M's sign and exponent field)
+// and w - M == h; its count h 2^e is then the low 10 bits of w, added to the
+// packed lanes of tacc.  Returns non-zero when either half fails.
+__device__ __forceinline__ uint32_t f16x2_count_check(uint32_t h, uint32_t m2, uint32_t& tacc) {
+  uint32_t w, back;
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w) : "r"(h), "r"(m2));
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(back) : "r"(w), "r"(m2));
+  tacc += w & 0x03FF03FFu;
+  return (back ^ h) | ((w & 0xFC00FC00u) ^ m2);
+}
+
 // bounded wait that sleeps in the barrier instead of polling
 __device__ __forceinline__ bool tc_wait_sleep(uint64_t* bar, uint32_t parity) {
   const long long t0 = clock64();
@@ -264,9 +309,9 @@ __device__ __forceinline__ void tc_load_acc8(uint32_t lane_base, int h, int Cp, 
 template <int MODE>
 __device__ __forceinline__ void tc_scores8(const SegGroup& G, const TcModelArg& M, int F,
                                            uint32_t lane_base, int h, int cb, bool any_ovf,
-                                           long long k0, long long k1, float (&s)[8],
+                                           long long k0, long long k1, float rsc, float (&s)[8],
                                            float (&e)[8], float& added) {
-  const float sc = M.hdr->scale;
+  const float sc = M.hdr->scale * rsc;   // rsc: the row's power-of-two scale (FP8 rows)
   added = 0.f;
   if (MODE == 0) {
     // the three limbs' loads in flight together, one wait
@@ -331,7 +376,8 @@ template <int MODE>
 __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch& xe,
                                             const SegGroup& G, const TcModelArg& M,
                                             long long grow, int xr, int h, int part,
-                                            uint32_t Tpart, uint32_t lane_base, int& ep) {
+                                            uint32_t Tpart, float rsc, uint32_t lane_base,
+                                            int& ep) {
   using PS = TcPass<MODE>;
   const int lane = threadIdx.x & 31;
   const bool valid = grow >= 0;
@@ -354,7 +400,7 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch
     const int cb = c0 + 8 * ch;
     if (cb >= M.Cp) break;
     float sc[8], er[8], added;
-    tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
+    tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, rsc, sc, er, added);
     if (part == 0 && ch == 0) T += added;
     if constexpr (MODE == 0) {
 #pragma unroll
@@ -467,7 +513,7 @@ __device__ __forceinline__ bool tc_epilogue(const TcArgs& a, TcShared& sh, TcXch
         for (int i = 0; i < 8; ++i) sc[i] = keep[8 * ch + i];
       } else {
         float er[8], added;
-        tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, sc, er, added);
+        tc_scores8<MODE>(G, M, F, lane_base, h, cb, any_ovf, k0, k1, rsc, sc, er, added);
       }
       if (!valid) continue;
       if (vec && cb + 8 <= M.C) {
@@ -537,9 +583,14 @@ __device__ __forceinline__ long long tc_units(const TcArgs& a) {
   return (long long)((c + TC_M - 1) / TC_M);
 }
 
-template <int MODE>
+// DT: storage of the rows (NB_U8, NB_FP8E4M3 or NB_BF16; the chunked pass
+// takes u8 rows only).  A 128-byte row box holds BOXF features.
+template <int MODE, int DT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constant__ TcArgs a) {
   using PS = TcPass<MODE>;
+  static_assert(MODE == 0 || DT == NB_U8, "the chunked pass reads u8 rows");
+  constexpr int ES = DT == NB_BF16 ? 2 : 1;        // bytes per feature
+  constexpr int BOXF = TC_BOX / ES;                 // features per row stage
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   TcShared& sh = *reinterpret_cast<TcShared*>(tc_smem);
   TcXch& xe = *reinterpret_cast<TcXch*>(tc_smem + 1024);
@@ -631,9 +682,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
         if (a.maps)
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap)
                        : "memory");
-        const int nraw = (F + TC_BOX - 1) / TC_BOX, rot = tc_rot<MODE>(nks) / 2;
+        // row stages of BOXF features; the rotation counts weight stages of TC_KS
+        const int nraw = (F + BOXF - 1) / BOXF, rot = tc_rot<MODE>(nks) * TC_KS / BOXF;
         for (int rs = 0; rs < nraw; ++rs, ++ri) {
-          const int f0 = TC_BOX * (rs + rot < nraw ? rs + rot : rs + rot - nraw);
+          const int f0 = BOXF * (rs + rot < nraw ? rs + rot : rs + rot - nraw);
           const int slot = (int)(ri % TC_NRAW);
           const uint32_t par = (uint32_t)((ri / TC_NRAW) & 1);
           if (!tc_wait(sh, &sh.raw_empty[slot], par ^ 1u, a.status)) {
@@ -798,7 +850,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
     long long ri = 0;   // pair pass: row stages consumed
     const uint32_t raw_s = smem_addr(raw) + (uint32_t)(h * TC_M * TC_BOX);
     const int rr = 32 * qd + lane;   // row within the tile
-    constexpr int RAW_A = TC_BOX / PS::KA;   // A stages per row stage
+    constexpr int RAW_A = BOXF / PS::KA;     // A stages per row stage
+    constexpr int NVT = PS::NV * ES;         // 16-byte chunks per thread per A stage
+    constexpr int CPA = PS::KA * ES / 16;    // 16-byte chunks of a row per A stage
+    // FP8 / BF16 rows: the magic pair of the count check, and the row's flag
+    // and scale (set at the start of each unit)
+    uint32_t m2 = 0x64006400u, bad = 0u;
+    float rsc = 1.f;
 
     // consumer state
     long long c_i = 0;
@@ -812,7 +870,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
           ok = false;
           break;
         }
-        uint4 xv[PS::NV];
+        uint4 xv[NVT];
         if constexpr (MODE == 1) {
           if (base + d + TC_PD - 1 < total) load_next(buf[(d + TC_PD - 1) % TC_PD]);
           xv[0] = buf[d];
@@ -827,29 +885,72 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             break;
           }
 #pragma unroll
-          for (int v = 0; v < PS::NV; ++v) {
-            const int c16 = (PS::KA / 16) * (c_ka % RAW_A) + PS::NV * part + v;
+          for (int v = 0; v < NVT; ++v) {
+            const int c16 = CPA * (c_ka % RAW_A) + NVT * part + v;
             xv[v] = lds16(raw_s + slot * TC_RAW_BYTES +
                           (uint32_t)(rr * TC_BOX + ((c16 ^ (rr & 7)) << 4)));
           }
         }
-        // convert this thread's bytes to FP16 pairs
+        if (DT != NB_U8 && c_ka == 0) {
+          // a new unit: this thread's row scale (FP8 rows: 2^e, e in {0, 1};
+          // any other exponent sends the row to the FP64 recheck)
+          bad = 0u;
+          m2 = 0x64006400u;
+          rsc = 1.f;
+          if (DT == NB_FP8E4M3) {
+            int g = 0;
+            const long long r = row_of(c_i, g);
+            const int8_t* re = tc_group(a, g).row_exp;
+            const int e = (re && r >= 0) ? (int)re[r] : 0;
+            if (e == 1) {
+              m2 = 0x60006000u;
+              rsc = 2.f;
+            } else if (e != 0) {
+              bad = 1u;
+            }
+          }
+        }
+        // convert this thread's values to FP16 pairs
         uint32_t o[PS::COLS];
+        if constexpr (DT == NB_U8) {
 #pragma unroll
-        for (int v = 0; v < PS::NV; ++v) {
-          const uint4 x = xv[v];
-          T = dp4a_uu(x.x, 0x01010101u, T);
-          T = dp4a_uu(x.y, 0x01010101u, T);
-          T = dp4a_uu(x.z, 0x01010101u, T);
-          T = dp4a_uu(x.w, 0x01010101u, T);
-          o[8 * v + 0] = u8x2_to_f16x2(x.x, 0x5140u);
-          o[8 * v + 1] = u8x2_to_f16x2(x.x, 0x7362u);
-          o[8 * v + 2] = u8x2_to_f16x2(x.y, 0x5140u);
-          o[8 * v + 3] = u8x2_to_f16x2(x.y, 0x7362u);
-          o[8 * v + 4] = u8x2_to_f16x2(x.z, 0x5140u);
-          o[8 * v + 5] = u8x2_to_f16x2(x.z, 0x7362u);
-          o[8 * v + 6] = u8x2_to_f16x2(x.w, 0x5140u);
-          o[8 * v + 7] = u8x2_to_f16x2(x.w, 0x7362u);
+          for (int v = 0; v < NVT; ++v) {
+            const uint4 x = xv[v];
+            T = dp4a_uu(x.x, 0x01010101u, T);
+            T = dp4a_uu(x.y, 0x01010101u, T);
+            T = dp4a_uu(x.z, 0x01010101u, T);
+            T = dp4a_uu(x.w, 0x01010101u, T);
+            o[8 * v + 0] = u8x2_to_f16x2(x.x, 0x5140u);
+            o[8 * v + 1] = u8x2_to_f16x2(x.x, 0x7362u);
+            o[8 * v + 2] = u8x2_to_f16x2(x.y, 0x5140u);
+            o[8 * v + 3] = u8x2_to_f16x2(x.y, 0x7362u);
+            o[8 * v + 4] = u8x2_to_f16x2(x.z, 0x5140u);
+            o[8 * v + 5] = u8x2_to_f16x2(x.z, 0x7362u);
+            o[8 * v + 6] = u8x2_to_f16x2(x.w, 0x5140u);
+            o[8 * v + 7] = u8x2_to_f16x2(x.w, 0x7362u);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < NVT; ++v) {
+            const uint32_t w[4] = {xv[v].x, xv[v].y, xv[v].z, xv[v].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if constexpr (DT == NB_FP8E4M3) {
+                o[8 * v + 2 * k] = e4m3x2_to_f16x2(w[k] & 0xFFFFu);
+                o[8 * v + 2 * k + 1] = e4m3x2_to_f16x2(w[k] >> 16);
+              } else {
+                o[4 * v + k] = bf16x2_to_f16x2(w[k]);
+                bad |= bf16x2_tiny(w[k]);
+              }
+            }
+          }
+          // every value an integer count x = v 2^e below 1024: x sits in the
+          // low 10 bits of v + M, summed in packed 16-bit lanes (16 words of at
+          // most 1023 per lane)
+          uint32_t tacc = 0u;
+#pragma unroll
+          for (int k = 0; k < PS::COLS; ++k) bad |= f16x2_count_check(o[k], m2, tacc);
+          T += (tacc & 0xFFFFu) + (tacc >> 16);
         }
         if constexpr (MODE == 0) {
           if (c_ka % RAW_A == RAW_A - 1 || c_ka == nka - 1) {   // done with the row stage
@@ -893,8 +994,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             int g = 0;
             const long long r = row_of(c_i, g);
             const SegGroup& G = tc_group(a, g);
-            if (!tc_epilogue<MODE>(a, sh, xe, G, a.models[G.model], r, xr, h, part, T,
-                                   lane_base, ep)) {
+            if (!tc_epilogue<MODE>(a, sh, xe, G, a.models[G.model], r, xr, h, part,
+                                   bad ? 0xFFFFFFFFu : T, rsc, lane_base, ep)) {
               ok = false;
               break;
             }
@@ -987,8 +1088,9 @@ nb_status launch_derive_tc(nb_model* m, cudaStream_t st) {
 // launch
 // ---------------------------------------------------------------------------
 bool tc_eligible(const nb_model* m, nb_dtype dt, const void* X, int64_t ld) {
-  return m->kind == NB_MULTINOMIAL && m->d.tc_w != nullptr && dt == NB_U8 &&
-         ld % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+  return m->kind == NB_MULTINOMIAL && m->d.tc_w != nullptr &&
+         (dt == NB_U8 || dt == NB_FP8E4M3 || dt == NB_BF16) &&
+         (ld * elem_size(dt)) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
          m->tile.variant != NB_VARIANT_REGISTER;
 }
 
@@ -1010,7 +1112,7 @@ static size_t tc_smem_bytes(int mode, int N) {
          (mode == 0 ? (size_t)TC_NRAW * TC_RAW_BYTES : 0) + (size_t)TC_NB * (uint32_t)N * 128u;
 }
 
-template <int MODE>
+template <int MODE, int DT>
 static nb_status run_tc(TcArgs& a, int maxN, long long units_hint, cudaStream_t st) {
   constexpr size_t kMax = 227 * 1024;
   const size_t smem = tc_smem_bytes(MODE, maxN);
@@ -1023,13 +1125,13 @@ static nb_status run_tc(TcArgs& a, int maxN, long long units_hint, cudaStream_t 
   // more than half the shared memory of an SM keeps one CTA (and one
   // tensor-memory allocation) per SM
   const size_t launch_smem = smem < 120 * 1024 ? 120 * 1024 : smem;
-  NB_TRY_CUDA(cudaFuncSetAttribute(k_score_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  NB_TRY_CUDA(cudaFuncSetAttribute(k_score_tc<MODE, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)launch_smem),
               "cudaFuncSetAttribute(k_score_tc)");
   long long grid = num_sms();
   if (units_hint > 0 && units_hint < grid) grid = units_hint;
   count_launch();
-  k_score_tc<MODE><<<(unsigned)grid, TC_THREADS, launch_smem, st>>>(a);
+  k_score_tc<MODE, DT><<<(unsigned)grid, TC_THREADS, launch_smem, st>>>(a);
   NB_TRY_CUDA(cudaGetLastError(), "k_score_tc launch");
   return NB_OK;
 }
@@ -1051,9 +1153,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
   return fn;
 }
 
-// 2-D map of n rows x F u8 features (row pitch ld bytes): 128 x 128 boxes,
-// 128-byte swizzle, zero fill out of bounds
-static nb_status tc_row_map(CUtensorMap* map, const void* X, int64_t n, int F, int64_t ld) {
+// 2-D map of n rows x F features of es bytes (1: u8 or FP8, 2: BF16; row pitch
+// ld bytes): boxes of 128 rows x 128 bytes, 128-byte swizzle, zero fill out of
+// bounds
+static nb_status tc_row_map(CUtensorMap* map, const void* X, int64_t n, int F, int64_t ld,
+                            int es = 1) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tc_encode_fn();
   if (!enc) {
     set_error("tensor-core scorer: cuTensorMapEncodeTiled is not available");
@@ -1061,9 +1165,10 @@ static nb_status tc_row_map(CUtensorMap* map, const void* X, int64_t n, int F, i
   }
   const cuuint64_t dims[2] = {(cuuint64_t)F, (cuuint64_t)(n > 0 ? n : 1)};
   const cuuint64_t strides[1] = {(cuuint64_t)ld};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_BOX, (cuuint32_t)TC_M};
+  const cuuint32_t box[2] = {(cuuint32_t)(TC_BOX / es), (cuuint32_t)TC_M};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(X), dims, strides,
+  const CUresult r = enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                         2, const_cast<void*>(X), dims, strides,
                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -1073,22 +1178,24 @@ static nb_status tc_row_map(CUtensorMap* map, const void* X, int64_t n, int F, i
   return NB_OK;
 }
 
-nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t ld,
+nb_status launch_score_tc(const nb_model* m, const void* X, nb_dtype dt, int64_t n, int64_t ld,
                           const nb_aux* aux, const ScoreOut& o, cudaStream_t st) {
   TcArgs a{};
-  nb_status ms = tc_row_map(&a.tmap, X, n, m->F, ld);
+  const int es = elem_size(dt);
+  nb_status ms = tc_row_map(&a.tmap, X, n, m->F, ld * es, es);
   if (ms != NB_OK) return ms;
   a.maps = nullptr;
   a.groups = nullptr;
   a.hdr = nullptr;
   SegGroup& g = a.g0;
+  const bool u8 = dt == NB_U8;
   g.X = static_cast<const char*>(X);
-  g.ld_bytes = ld;
+  g.ld_bytes = ld * es;
   g.n = n;
-  g.ovf_ptr = aux ? aux->ovf_ptr : nullptr;
-  g.ovf_col = aux ? aux->ovf_col : nullptr;
-  g.ovf_add = aux ? aux->ovf_add : nullptr;
-  g.row_exp = nullptr;
+  g.ovf_ptr = (u8 && aux) ? aux->ovf_ptr : nullptr;
+  g.ovf_col = (u8 && aux) ? aux->ovf_col : nullptr;
+  g.ovf_add = (u8 && aux) ? aux->ovf_add : nullptr;
+  g.row_exp = (dt == NB_FP8E4M3 && aux) ? aux->row_exp : nullptr;
   g.label = o.label;
   g.margin = o.margin;
   g.logpost = o.want_lp ? o.logpost : nullptr;
@@ -1103,6 +1210,14 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
   a.status = m->d.sstatus;
+  if (!u8) {
+    // FP8 / BF16 rows: heavy or unchecked rows stay marked for the FP64 recheck
+    a.heavy = nullptr;
+    a.heavy_n = nullptr;
+    a.heavy_cap = 0;
+    return dt == NB_FP8E4M3 ? run_tc<0, NB_FP8E4M3>(a, a.models[0].N, a.units0, st)
+                            : run_tc<0, NB_BF16>(a, a.models[0].N, a.units0, st);
+  }
   // the list of heavy rows (and its count) for the chunked pass: stream-ordered
   // scratch of this call
   const int cap = n < kTcHeavyCap ? (int)n : kTcHeavyCap;
@@ -1114,26 +1229,27 @@ nb_status launch_score_tc(const nb_model* m, const void* X, int64_t n, int64_t l
   a.heavy_cap = cap;
   const cudaError_t me = cudaMemsetAsync(scratch, 0, 16, st);
   nb_status s = me == cudaSuccess ? NB_OK : cuda_status(me, "memset(heavy count)");
-  if (s == NB_OK) s = run_tc<0>(a, a.models[0].N, a.units0, st);
-  if (s == NB_OK) s = run_tc<1>(a, a.models[0].N, 0, st);
+  if (s == NB_OK) s = run_tc<0, NB_U8>(a, a.models[0].N, a.units0, st);
+  if (s == NB_OK) s = run_tc<1, NB_U8>(a, a.models[0].N, 0, st);
   const cudaError_t fe = cudaFreeAsync(scratch, st);
   if (s != NB_OK) return s;
   NB_TRY_CUDA(fe, "cudaFreeAsync(heavy rows)");
   return NB_OK;
 }
 
-// tensor map of a group's u8 rows for a batch work list (128 bytes at map)
-nb_status tc_encode_rows(void* map, const void* X, int64_t n, int F, int64_t ld_bytes) {
-  return tc_row_map(static_cast<CUtensorMap*>(map), X, n, F, ld_bytes);
+// tensor map of a group's rows (es bytes per feature) for a batch work list
+// (128 bytes at map)
+nb_status tc_encode_rows(void* map, const void* X, int64_t n, int F, int64_t ld_bytes, int es) {
+  return tc_row_map(static_cast<CUtensorMap*>(map), X, n, F, ld_bytes, es);
 }
 
-bool tc_group_eligible(const nb_model* m, const void* X, int64_t ld_bytes) {
-  return tc_eligible(m, NB_U8, X, ld_bytes);
+bool tc_group_eligible(const nb_model* m, nb_dtype dt, const void* X, int64_t ld) {
+  return tc_eligible(m, dt, X, ld);
 }
 
 nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, const void* maps,
-                              const nb_model* const* models, int n_models, int F, int want_lp,
-                              int recheck, int* status, cudaStream_t st) {
+                              const nb_model* const* models, int n_models, nb_dtype dt, int F,
+                              int want_lp, int recheck, int* status, cudaStream_t st) {
   TcArgs a{};
   a.maps = static_cast<const CUtensorMap*>(maps);
   a.groups = groups;
@@ -1152,7 +1268,9 @@ nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, cons
   a.heavy = nullptr;
   a.heavy_n = nullptr;
   a.heavy_cap = 0;
-  return run_tc<0>(a, maxN, 0, st);
+  if (dt == NB_FP8E4M3) return run_tc<0, NB_FP8E4M3>(a, maxN, 0, st);
+  if (dt == NB_BF16) return run_tc<0, NB_BF16>(a, maxN, 0, st);
+  return run_tc<0, NB_U8>(a, maxN, 0, st);
 }
 
 }  // namespace nbg

@@ -72,10 +72,10 @@ nb_status launch_score_gen_seg(const SegGroup* groups, const SegHeader* hdr,
                                const nb_model* const* models, int n_models, nb_dtype dt, int F,
                                int want_lp, int recheck, int* status, cudaStream_t st);
 nb_status launch_score_tc_seg(const SegGroup* groups, const SegHeader* hdr, const void* maps,
-                              const nb_model* const* models, int n_models, int F, int want_lp,
-                              int recheck, int* status, cudaStream_t st);
-nb_status tc_encode_rows(void* map, const void* X, int64_t n, int F, int64_t ld_bytes);
-bool tc_group_eligible(const nb_model* m, const void* X, int64_t ld_bytes);
+                              const nb_model* const* models, int n_models, nb_dtype dt, int F,
+                              int want_lp, int recheck, int* status, cudaStream_t st);
+nb_status tc_encode_rows(void* map, const void* X, int64_t n, int F, int64_t ld_bytes, int es);
+bool tc_group_eligible(const nb_model* m, nb_dtype dt, const void* X, int64_t ld);
 constexpr size_t kTcMapBytes = 128;
 nb_status launch_recheck_seg(const SegGroup* groups, const SegHeader* hdr,
                              const nb_model* const* models, int n_models, nb_dtype dt, int F,

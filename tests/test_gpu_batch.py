@@ -15,10 +15,16 @@ pytestmark = pytest.mark.gpu
 nb = pytest.importorskip("paper_1905_13746_gb300")
 
 
+def _clip(fmt):
+    # counts of the compact formats stay where they are exact (u8) or where the
+    # tensor-core scorer takes every row (BF16, FP8 with row scale 2^0)
+    return 255 if fmt in ("u8", "bf16", "fp8") else 65535
+
+
 def _models(F, fmt, seed, Cs):
     out = []
     for i, C in enumerate(Cs):
-        X, y, _ = count_matrix(seed + 17 * i, 3000, F, C=C, clip=255 if fmt == "u8" else 65535)
+        X, y, _ = count_matrix(seed + 17 * i, 3000, F, C=C, clip=_clip(fmt))
         f, vals = stored(X, fmt)
         out.append((nb.fit(f, torch.from_numpy(y).cuda(), C), vals, y))
     return out
@@ -28,8 +34,7 @@ def _groups(F, fmt, seed, sizes, n_models, Cs):
     groups = []
     for k, n in enumerate(sizes):
         slot = k % n_models
-        X, _, _ = count_matrix(seed + 101 * k, max(n, 1), F, C=Cs[slot],
-                               clip=255 if fmt == "u8" else 65535)
+        X, _, _ = count_matrix(seed + 101 * k, max(n, 1), F, C=Cs[slot], clip=_clip(fmt))
         X = X[:n]
         f, v = stored(X, fmt)
         groups.append((slot, f, v))
@@ -49,10 +54,12 @@ def _check_against_single(models, batch, groups, single_outs):
     return int(nre.item())
 
 
-@pytest.mark.parametrize("fmt", ["u8ovf", "u8", "f32"])
+@pytest.mark.parametrize("fmt", ["u8ovf", "u8", "f32", "bf16", "fp8"])
 def test_batch_equals_single_groups_and_oracle(fmt):
     F = 1024 if fmt != "u8" else 2048
-    Cs = [2, 2, 3] if fmt != "f32" else [2, 3]
+    # two-class models batch U8 or F32 rows; BF16 and FP8 batches hold
+    # many-class models, whose groups take the tensor-core kernel
+    Cs = {"f32": [2, 3], "bf16": [3, 16], "fp8": [16, 5]}.get(fmt, [2, 2, 3])
     mods = _models(F, fmt, 5, Cs)
     sizes = [1, 17, 530, 5003, 0, 64, 1000, 2, 31, 33, 12000, 7]
     groups = _groups(F, fmt, 900, sizes, len(mods), Cs)

@@ -1,5 +1,6 @@
 """The many-class tensor-core scorer (tcgen05, 3 <= C <= 64 classes, u8
-storage with or without the overflow list, row pitch a multiple of 16 bytes) against the
+storage with or without the overflow list, BF16 and FP8 E4M3 rows, row pitch a
+multiple of 16 bytes) against the
 FP64 oracle, element by element, and against the CUDA-core scorer of the same
 model.  Its fixed-point weights make the FP32 accumulation exact, so the
 rigorous error bound stays small and the FP64 recheck rare even in the
@@ -102,3 +103,61 @@ def test_tensor_scorer_heavy_rows_redone_exactly():
     lab = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LABEL))
     compare(lab, ref, check_lp=False)
     assert lab["n_rechecked"] <= 30, lab["n_rechecked"]
+
+
+# BF16 and FP8 E4M3 rows: counts up to 255 are exact in BF16; E4M3 rounds them
+# (row scale 2^0), and the oracle scores the stored values
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+@pytest.mark.parametrize("C,F,n", [(5, 1000, 777), (17, 520, 129), (64, 4096, 1300)])
+def test_tensor_scorer_bf16_fp8_rows(fmt, C, F, n):
+    X, y, _ = count_matrix(1100 + C + F, 2500 + n, F, C=C, conc=0.1, clip=255)
+    model, vfit = _model("u8", X[:2500], y[:2500], C)
+    fsc, vsc = stored(X[2500:], fmt)
+    assert nb.score_path(model, fsc) == nb.NB_PATH_TENSOR
+    res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
+    _, ref = oracle_mn(vfit, y[:2500], C, vsc)
+    compare(res, ref)
+    assert res["n_rechecked"] <= max(3, n // 100), res["n_rechecked"]
+    lab = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LABEL))
+    compare(lab, ref, check_lp=False)
+
+
+def test_tensor_scorer_fp8_row_scales():
+    # rows whose largest count exceeds 448 carry a row scale 2^e: e = 1 stays on
+    # the tensor cores (scores scaled in the epilogue), e >= 2 goes to FP64
+    C, F = 8, 512
+    X, y, _ = count_matrix(1150, 5000, F, C=C, conc=0.1, clip=3000)
+    model, vfit = _model("u16", X[:2500], y[:2500], C)
+    fsc, vsc = stored(X[2500:], "fp8")
+    from oracle import formats
+    _, e = formats.pack_e4m3(X[2500:])
+    assert (e == 0).any() and (e == 1).any() and (e >= 2).any()
+    res = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_LP))
+    _, ref = oracle_mn(vfit, y[:2500], C, vsc)
+    compare(res, ref)
+    # without any recheck of near-ties, the e >= 2 rows are still recomputed in FP64
+    off = to_np(nb.score(model, fsc, recheck=nb.NB_RECHECK_OFF))
+    assert off["n_rechecked"] >= int((e >= 2).sum())
+    rows = np.nonzero(e >= 2)[0]
+    compare({k: (v[rows] if isinstance(v, np.ndarray) else v) for k, v in off.items()},
+            {k: (v[rows] if isinstance(v, np.ndarray) else v) for k, v in ref.items()})
+
+
+def test_tensor_scorer_bf16_values_outside_the_count_check():
+    # fractional, tiny, negative-free large and out-of-range BF16 values: the
+    # converters send their rows to the FP64 recheck, so the results still
+    # equal the oracle on the stored values, in every recheck mode
+    C, F = 6, 256
+    X, y, _ = count_matrix(1170, 3400, F, C=C, conc=0.1, clip=255)
+    model, vfit = _model("u8", X[:3000], y[:3000], C)
+    Xs = X[3000:].astype(np.float64)
+    odd = {0: 0.5, 1: 1e-30, 2: 1500.0, 3: 1023.0, 5: 3e-6, 6: 70000.0, 7: 2.75}
+    for r, v in odd.items():
+        Xs[r, (7 * r) % F] = v
+    fsc, vsc = stored(Xs, "bf16")
+    _, ref = oracle_mn(vfit, y[:3000], C, vsc)
+    for mode in (nb.NB_RECHECK_OFF, nb.NB_RECHECK_LABEL, nb.NB_RECHECK_LP):
+        res = to_np(nb.score(model, fsc, recheck=mode))
+        flagged = [r for r in odd if r != 3]
+        assert res["n_rechecked"] >= len(flagged), (mode, res["n_rechecked"])
+        compare(res, ref, check_lp=mode == nb.NB_RECHECK_LP)
