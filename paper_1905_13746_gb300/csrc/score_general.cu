@@ -345,29 +345,46 @@ __global__ void __launch_bounds__(256) k_score_gauss(const GGArgs a) {
     __syncwarp();
     if (lane == 0) {
       const float* s = ssh[warp];
+      const float* t = tsh[warp];
       int bi = 0;
       for (int c = 1; c < a.C; ++c)
         if (s[c] > s[bi]) bi = c;
-      float second = -INFINITY;
-      for (int c = 0; c < a.C; ++c)
-        if (c != bi && s[c] > second) second = s[c];
-      float tmax = 0.f;
-      for (int c = 0; c < a.C; ++c) tmax = fmaxf(tmax, tsh[warp][c]);
+      float second = -INFINITY, tmax = 0.f, P = 0.f;
+      for (int c = 0; c < a.C; ++c) {
+        tmax = fmaxf(tmax, t[c]);
+        if (c == bi) continue;
+        if (s[c] > second) second = s[c];
+        P += expf(s[c] - s[bi]);
+      }
       const float margin = s[bi] - second;
-      const float tau = 2.f * tmax + 1e-30f;
+      // lp_c = (s_c - s_top) - L: formed from the differences, so that no
+      // rounding at the scores' magnitude enters (lp_top = -L exactly)
+      const float L = log1pf(P);
       bool flag = false;
       if (a.recheck != NB_RECHECK_OFF) {
-        flag = !(margin > tau);
-        if (a.recheck == NB_RECHECK_LP && tau > 5e-6f * fmaxf(1.f, margin)) flag = true;
+        // label: the top class stays ahead of every other class c by more
+        // than the two classes' bounds (a far class's large bound does not
+        // matter, its score is far below)
+        for (int c = 0; c < a.C; ++c)
+          if (c != bi && !(s[bi] - s[c] > (t[bi] + t[c]) * 1.0001f)) flag = true;
+        if (a.recheck == NB_RECHECK_LP && !flag) {
+          // lp_c = d_c - L with d_c = s_c - s_top and L = log(1 + sum_{k != top}
+          // e^{d_k}); each d_k is off by at most D = t_top + t_max, so L is off
+          // by at most D e^{2D} P / (1 + P) (mean value; the softmax weights at
+          // the intermediate point are within e^{2D} of the computed ones), and
+          // lp_c by that plus t_c + t_top (c != top)
+          const float D = t[bi] + tmax;
+          const float eL = D * expf(2.f * D) * (P / (1.f + P)) * 1.01f + 1e-30f;
+          for (int c = 0; c < a.C; ++c) {
+            const float err = (c == bi ? 0.f : t[c] + t[bi]) + eL;
+            if (err > 5e-6f * fmaxf(1.f, fabsf((s[c] - s[bi]) - L))) flag = true;
+          }
+        }
       }
       a.label[r] = flag ? kLabelRecheck : (uint8_t)bi;
       a.margin[r] = margin;
-      if (a.want_lp) {
-        float se = 0.f;
-        for (int c = 0; c < a.C; ++c) se += expf(s[c] - s[bi]);
-        const float lse = s[bi] + logf(se);
-        for (int c = 0; c < a.C; ++c) a.logpost[r * a.C + c] = s[c] - lse;
-      }
+      if (a.want_lp)
+        for (int c = 0; c < a.C; ++c) a.logpost[r * a.C + c] = (s[c] - s[bi]) - L;
     }
     __syncwarp();
   }

@@ -183,3 +183,32 @@ def test_gaussian_refit_rebuilds_tensor_tables():
                                  yd.data_ptr())
     _, res = _score(model, Xs, nb.NB_RECHECK_LABEL)
     compare(res, oracle.score(Xs, oracle.gauss_fit(Xc, yc, C)), check_lp=False)
+
+
+@pytest.mark.parametrize("C,F", [(64, 64), (64, 1024), (16, 256)])
+def test_gaussian_log_posterior_mode_rechecks_few_rows(C, F):
+    # the CUDA-core scorer's log-posterior test weighs each class's bound
+    # against that class's own distance from the top: on separated classes
+    # almost no row needs FP64, and the results meet the tolerance
+    Xf, yf, Xs = _data(1600 + C + F, C, F, 40, 3000)
+    model = _fit(Xf, yf, C)
+    X, res = _score(model, Xs, nb.NB_RECHECK_LP)
+    assert nb.score_path(model, X, nb.NB_RECHECK_LP) == nb.NB_PATH_GENERAL
+    compare(res, oracle.score(Xs, oracle.gauss_fit(Xf, yf, C)))
+    assert res["n_rechecked"] <= 30, res["n_rechecked"]
+
+
+def test_gaussian_log_posterior_mode_close_classes():
+    # classes that differ by sampling noise alone: many rows go to FP64 in the
+    # log-posterior mode, and every label and log posterior still matches
+    C, F = 16, 128
+    rng = np.random.default_rng(1700)
+    mu = rng.uniform(0.0, 10.0, size=F)
+    sd = rng.uniform(0.5, 3.0, size=F)
+    yf = np.concatenate([np.arange(C), rng.integers(0, C, 30 * C - C)]).astype(np.int32)
+    Xf = rng.normal(mu, sd, size=(yf.shape[0], F)).astype(np.float32)
+    Xs = rng.normal(mu, sd, size=(2000, F)).astype(np.float32)
+    model = _fit(Xf, yf, C)
+    _, res = _score(model, Xs, nb.NB_RECHECK_LP)
+    compare(res, oracle.score(Xs, oracle.gauss_fit(Xf, yf, C)))
+    assert res["n_rechecked"] > 0
