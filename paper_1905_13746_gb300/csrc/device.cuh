@@ -38,6 +38,19 @@ __device__ __forceinline__ uint32_t dp4a_uu(uint32_t a, uint32_t b, uint32_t c) 
   return d;
 }
 
+// c + a.half0 * b.byte0 + a.half1 * b.byte1 (a: two unsigned 16-bit values,
+// b: four signed bytes); the .hi form takes bytes 2 and 3 of b
+__device__ __forceinline__ int dp2a_lo_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.lo.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_hi_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.hi.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 // Exact conversion of an unsigned 8- or 16-bit field to float: place the
 // field in the low significand bits of 2^23 and subtract 2^23.
 __device__ __forceinline__ float u_field_to_f32(uint32_t w, uint32_t sel) {

@@ -12,8 +12,11 @@
 //   * u8 storage: Delta is held as a 22-bit fixed-point integer split into
 //     three signed 8-bit limbs; dp4a accumulates x * limb exactly in int32, so
 //     the only error is the quantisation of Delta (<= 2^-S / 2 per count).
-//   * f32 / u16 / bf16 / fp8 / u8 storage: decode to FP32 and FMA against the
-//     FP32 Delta table, four accumulators per row per lane.
+//     FP8 E4M3 storage takes the same limbs: its values become exact integer
+//     counts (row scale 2^0 or 2^1, checked per value, see fp8_count_pairs)
+//     in 16-bit pairs, accumulated with dp2a.
+//   * f32 / u16 / bf16 storage: decode to FP32 and FMA against the FP32 Delta
+//     table, four accumulators per row per lane.
 // Every row also gets a rigorous bound tau on |d_gpu - d_exact|; rows whose
 // sign (or whose log posteriors to 1e-5) the bound cannot guarantee are marked
 // for the FP64 recheck.
@@ -26,7 +29,7 @@ namespace nbg {
 // ---------------------------------------------------------------------------
 // u8 storage, fixed-point Delta, exact integer accumulation
 // ---------------------------------------------------------------------------
-template <int LPR, int R>
+template <int DT, int LPR, int R>
 __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
@@ -61,7 +64,8 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
        t += nwarps) {
     const int64_t row0 = t * RPW + (int64_t)sub * R;
     int acc0[R], acc1[R], acc2[R];
-    uint32_t tot[R];
+    uint32_t tot[R], m2[R];
+    Fp8Check chk[R];
     const char* rp[R];
     bool ok[R];
 #pragma unroll
@@ -70,6 +74,8 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
       tot[r] = 0;
       ok[r] = row0 + r < a.n;
       rp[r] = a.X + (ok[r] ? row0 + r : 0) * a.ld_bytes;
+      m2[r] = DT == NB_FP8E4M3 ? fp8_magic((a.row_exp && ok[r]) ? (int)a.row_exp[row0 + r] : 0)
+                               : 0u;
     }
 #pragma unroll 2
     for (int v = li; v < nv; v += LPR) {
@@ -89,6 +95,10 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
+        if (DT == NB_FP8E4M3) {
+          fp8_vector_limbs(x[r], q0, q1, q2, m2[r], acc0[r], acc1[r], acc2[r], tot[r], chk[r]);
+          continue;
+        }
         acc0[r] = dp4a_us(x[r].x, q0.x, acc0[r]);
         acc0[r] = dp4a_us(x[r].y, q0.y, acc0[r]);
         acc0[r] = dp4a_us(x[r].z, q0.z, acc0[r]);
@@ -109,9 +119,11 @@ __global__ void __launch_bounds__(256) k_score2_u8(const S2Args a) {
     }
     long long D[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < R; ++r) {
       D[r] = ((long long)acc2[r] << 16) + ((long long)acc1[r] << 8) + (long long)acc0[r];
-    if (a.ovf_ptr) {
+      if (DT == NB_FP8E4M3) tot[r] = fp8_lane_total(tot[r], chk[r], m2[r]);
+    }
+    if (DT == NB_U8 && a.ovf_ptr) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!ok[r]) continue;
@@ -314,7 +326,7 @@ static nb_status dispatch_dt(nb_dtype dt, S2Args& a, int smem, cudaStream_t st) 
   const int64_t ntiles = (a.n + rpw - 1) / rpw;
   switch (dt) {
     case NB_U8:
-      return launch_persistent(k_score2_u8<LPR, R>, smem, ntiles, a, st);
+      return launch_persistent(k_score2_u8<NB_U8, LPR, R>, smem, ntiles, a, st);
     case NB_F32:
       return launch_persistent(k_score2_fp<NB_F32, LPR, R>, smem, ntiles, a, st);
     case NB_U16:
@@ -322,7 +334,7 @@ static nb_status dispatch_dt(nb_dtype dt, S2Args& a, int smem, cudaStream_t st) 
     case NB_BF16:
       return launch_persistent(k_score2_fp<NB_BF16, LPR, R>, smem, ntiles, a, st);
     case NB_FP8E4M3:
-      return launch_persistent(k_score2_fp<NB_FP8E4M3, LPR, R>, smem, ntiles, a, st);
+      return launch_persistent(k_score2_u8<NB_FP8E4M3, LPR, R>, smem, ntiles, a, st);
   }
   set_error("unknown dtype");
   return NB_EINVAL;
@@ -352,7 +364,7 @@ nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt, int64_t n
   a.marks = o.counted ? reinterpret_cast<unsigned long long*>(o.n_rechecked) : nullptr;
   a.status = m->d.sstatus;
   int smem;
-  if (dt == NB_U8) {
+  if (dt == NB_U8 || dt == NB_FP8E4M3) {   // fixed-point limbs, exact sums
     a.nvec_tab = m->nvec8;
     a.table = m->d.limbs;
     smem = 3 * m->nvec8 * 16;

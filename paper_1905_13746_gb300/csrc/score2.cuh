@@ -171,6 +171,104 @@ struct Decode<NB_FP8E4M3> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// FP8 E4M3 counts as exact integers
+// ---------------------------------------------------------------------------
+// Magic pair of a row with row scale 2^e: (M, M) in FP16, M = 2^(10 - e), for
+// e = 0 or 1; 0 for any other exponent (the row then fails the check).
+__device__ __forceinline__ uint32_t fp8_magic(int e) {
+  return e == 0 ? 0x64006400u : (e == 1 ? 0x60006000u : 0u);
+}
+
+// Count check state of one row's values.  With u = v + M in FP16 (v the E4M3
+// value, converted exactly), v 2^e is an integer in [0, 2^10) exactly when u
+// lies in [M, 2M) -- the sign and exponent field of every half equals M's,
+// which the OR and the AND of all halves both show -- and u - M == v; the
+// count is then the low 10 bits of u.  Fractions, negatives and NaN fail.
+struct Fp8Check {
+  uint32_t bd = 0u;             // OR of (u - M) ^ v
+  uint32_t orv = 0u;            // OR of u
+  uint32_t andv = 0xFFFFFFFFu;  // AND of u
+};
+
+__device__ __forceinline__ bool fp8_check_ok(const Fp8Check& c, uint32_t m2) {
+  return m2 != 0u && c.bd == 0u && (c.orv & 0xFC00FC00u) == m2 && (c.andv & 0xFC00FC00u) == m2;
+}
+
+// Four E4M3 codes (features f .. f+3 in the bytes of w) -> u01 = (M + x_f,
+// M + x_f+1) and u23 = (M + x_f+2, M + x_f+3) as 16-bit pairs, checked.
+__device__ __forceinline__ void fp8_biased_pairs(uint32_t w, uint32_t m2, uint32_t& u01,
+                                                 uint32_t& u23, Fp8Check& c) {
+  uint32_t h0, h1, b0, b1;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h0) : "h"((unsigned short)(w & 0xFFFFu)));
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h1) : "h"((unsigned short)(w >> 16)));
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(u01) : "r"(h0), "r"(m2));
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(u23) : "r"(h1), "r"(m2));
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(b0) : "r"(u01), "r"(m2));
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(b1) : "r"(u23), "r"(m2));
+  c.bd |= (b0 ^ h0) | (b1 ^ h1);
+  c.orv |= u01 | u23;
+  c.andv &= u01 & u23;
+}
+
+// One 16-byte vector of E4M3 codes against its three limb words, exact:
+// the counts x (low 10 bits of each biased half) times the limbs with dp2a,
+// and their total.  Any number of vectors per lane (int32 sums stay below
+// 128 T).
+__device__ __forceinline__ void fp8_vector_limbs(const uint4& x, const uint4& q0, const uint4& q1,
+                                                 const uint4& q2, uint32_t m2, int& a0, int& a1,
+                                                 int& a2, uint32_t& tt, Fp8Check& c) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+  const uint32_t l0[4] = {q0.x, q0.y, q0.z, q0.w}, l1[4] = {q1.x, q1.y, q1.z, q1.w},
+                 l2[4] = {q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint32_t u01, u23;
+    fp8_biased_pairs(w[k], m2, u01, u23, c);
+    const uint32_t x01 = u01 & 0x03FF03FFu, x23 = u23 & 0x03FF03FFu;
+    a0 = dp2a_hi_us(x23, l0[k], dp2a_lo_us(x01, l0[k], a0));
+    a1 = dp2a_hi_us(x23, l1[k], dp2a_lo_us(x01, l1[k], a1));
+    a2 = dp2a_hi_us(x23, l2[k], dp2a_lo_us(x01, l2[k], a2));
+    tt = (uint32_t)dp2a_hi_us(x23, 0x01010101u, dp2a_lo_us(x01, 0x01010101u, (int)tt));
+  }
+}
+
+// As fp8_vector_limbs on the biased halves M + x directly: each sum then
+// carries M times the sum of the limbs (and M per value in tt), which the
+// caller removes once per row (fp8_unbias).  The int32 sums stay exact for up
+// to 64 values per lane ((2^15 + 2^10) * 128 * 64 < 2^31).
+__device__ __forceinline__ void fp8_vector_limbs_biased(const uint4& x, const uint4& q0,
+                                                        const uint4& q1, const uint4& q2,
+                                                        uint32_t m2, int& a0, int& a1, int& a2,
+                                                        uint32_t& tt, Fp8Check& c) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+  const uint32_t l0[4] = {q0.x, q0.y, q0.z, q0.w}, l1[4] = {q1.x, q1.y, q1.z, q1.w},
+                 l2[4] = {q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint32_t u01, u23;
+    fp8_biased_pairs(w[k], m2, u01, u23, c);
+    a0 = dp2a_hi_us(u23, l0[k], dp2a_lo_us(u01, l0[k], a0));
+    a1 = dp2a_hi_us(u23, l1[k], dp2a_lo_us(u01, l1[k], a1));
+    a2 = dp2a_hi_us(u23, l2[k], dp2a_lo_us(u01, l2[k], a2));
+    tt = (uint32_t)dp2a_hi_us(u23, 0x01010101u, dp2a_lo_us(u01, 0x01010101u, (int)tt));
+  }
+}
+
+// Sum of the 16 signed limb bytes of a vector (the bias correction's weight)
+__device__ __forceinline__ int limb_byte_sum(const uint4& q) {
+  int s = dp4a_us(0x01010101u, q.x, 0);
+  s = dp4a_us(0x01010101u, q.y, s);
+  s = dp4a_us(0x01010101u, q.z, s);
+  return dp4a_us(0x01010101u, q.w, s);
+}
+
+// The lane's count total, or 2^24 when one of its values failed the check
+// (which sends the row to the FP64 recheck, see c2_tau_u8).
+__device__ __forceinline__ uint32_t fp8_lane_total(uint32_t tt, const Fp8Check& c, uint32_t m2) {
+  return fp8_check_ok(c, m2) ? tt : 16777216u;
+}
+
 // Sums four int32 values over the LPR lanes of a lane group (LPR = 4 .. 32,
 // a power of two) with log2(LPR) + 1 shuffles instead of 4 log2(LPR): the
 // first two steps halve the set of values each lane carries.  Returns the lane's share: lanes [0, LPR/4) of

@@ -9,7 +9,9 @@
 // slice of those vectors in registers (staged once per block by a bulk copy).
 //
 // u8 storage: the three int8 limbs of the fixed-point Delta and the count
-// total T are accumulated with dp4a in four int32 sums per row, reduced by a
+// total T are accumulated with dp4a in four int32 sums per row (FP8 E4M3
+// storage: the values as exact integer counts in 16-bit pairs, with dp2a),
+// reduced by a
 // butterfly inside the lane group (exact), and combined into an int64 only
 // when the row is finished.  Overflow entries (count - 255 at a column) are
 // split over the row's lanes and added limb by limb, the column's three limbs
@@ -41,7 +43,7 @@ struct RowSum {   // one finished row waiting for its epilogue
 template <int DT>
 __device__ __forceinline__ void finish_row(const S2Args& a, float hb, float inv_scale, float maxabs,
                                            long long row, const RowSum& r) {
-  if (DT == NB_U8) {
+  if (DT == NB_U8 || DT == NB_FP8E4M3) {
     const long long D = ((long long)r.a2 << 16) + ((long long)r.a1 << 8) + (long long)r.a0;
     const float Dsum = (float)D * inv_scale;
     const float d = Dsum + hb;
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
   // ------------------------------------------------------------- consumers
   using Dec = Decode<DT>;
   constexpr int EPV = Dec::EPV, QPV = EPV / 4;
+  constexpr bool LIMBS = DT == NB_U8 || DT == NB_FP8E4M3;   // fixed-point limbs, exact
   const float hb = a.hdr->b, inv_scale = a.hdr->inv_scale, maxabs = a.hdr->maxabs;
   if (!mbar_wait_bounded(&tabbar, 0)) {
     if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 #pragma unroll
   for (int kv = 0; kv < KV; ++kv) {
     const int v = li + LPR * kv;
-    if (DT == NB_U8) {
+    if (LIMBS) {
       const uint4* tab = reinterpret_cast<const uint4*>(sm);
       const uint4 z = make_uint4(0, 0, 0, 0);
       q0[kv] = (FULL || v < nv) ? tab[v] : z;
@@ -122,6 +125,19 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
 #pragma unroll
       for (int q = 0; q < QPV; ++q)
         wq[kv][q] = (FULL || v < nv) ? tab[q * nt + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  // FP8 rows: each lane's limb byte sums and value count remove the bias of
+  // the biased dp2a sums once per row
+  int fs0 = 0, fs1 = 0, fs2 = 0, fnv = 0;
+  if (DT == NB_FP8E4M3) {
+#pragma unroll
+    for (int kv = 0; kv < KV; ++kv) {
+      if (!(FULL || li + LPR * kv < nv)) continue;
+      fs0 += limb_byte_sum(q0[kv]);
+      fs1 += limb_byte_sum(q1[kv]);
+      fs2 += limb_byte_sum(q2[kv]);
+      fnv += 16;
     }
   }
   // u8 overflow entries: the packed limb words after the three planes
@@ -234,6 +250,35 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
         }
         // the group's sums end up in its four lane quarters (see sum4_transposed)
         mine.a0 = sum4_transposed<LPR>(a0, a1, a2, (int)tt, li);
+      } else if (DT == NB_FP8E4M3) {
+        // the row's scale selects the magic pair of the count check
+        const uint32_t m2 =
+            fp8_magic((a.row_exp && valid) ? (int)a.row_exp[row0 + r] : 0);
+        int a0 = 0, a1 = 0, a2 = 0;
+        uint32_t tt = 0u;
+        Fp8Check chk;
+#pragma unroll
+        for (int kv = 0; kv < KV; ++kv) {
+          const int v = li + LPR * kv;
+          if (FULL || v < nv) {
+            uint4 x = *reinterpret_cast<const uint4*>(rp + (size_t)v * 16);
+            if (!FULL && v == tail_v) {   // E4M3 zero past F
+              const int keep = a.F - 16 * (nv - 1);
+              x.x &= u8_keep_mask(keep);
+              x.y &= u8_keep_mask(keep - 4);
+              x.z &= u8_keep_mask(keep - 8);
+              x.w &= u8_keep_mask(keep - 12);
+            }
+            fp8_vector_limbs_biased(x, q0[kv], q1[kv], q2[kv], m2, a0, a1, a2, tt, chk);
+          }
+        }
+        // remove the bias M of every value (exact integer arithmetic)
+        const int mh = (int)(m2 & 0xFFFFu);
+        a0 -= mh * fs0;
+        a1 -= mh * fs1;
+        a2 -= mh * fs2;
+        tt -= (uint32_t)(mh * fnv);
+        mine.a0 = sum4_transposed<LPR>(a0, a1, a2, (int)fp8_lane_total(tt, chk, m2), li);
       } else {
         float acc[4] = {0.f, 0.f, 0.f, 0.f}, tf = 0.f;
 #pragma unroll
@@ -267,7 +312,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, NCW == 8 ? 2 : 1)
       const bool take = lane >= nres && lane < nres + RPW && r0 + (lane - nres) < nr;
       const int sl = take ? src : 0;
       RowSum got;
-      if (DT == NB_U8) {
+      if (LIMBS) {
         got.a0 = __shfl_sync(0xFFFFFFFFu, mine.a0, sl);
         got.a1 = __shfl_sync(0xFFFFFFFFu, mine.a0, sl + LPR / 4);
         got.a2 = __shfl_sync(0xFFFFFFFFu, mine.a0, sl + LPR / 2);

@@ -111,6 +111,36 @@ def test_score_two_class(fmt, F):
     compare(res, ref)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])   # auto, pipelined, register-streaming
+def test_score_two_class_fp8_exact_counts(variant):
+    # E4M3 values are summed as exact integer counts (row scale 2^0 or 2^1):
+    # the log-posterior mode needs almost no FP64 recheck; a row holding a
+    # fractional value, or with a larger row scale, goes to FP64 and still
+    # matches the oracle on the stored values, in every recheck mode
+    F = 1000
+    X, y, _ = count_matrix(262, 7000, F, clip=900, conc=0.05)
+    model, _, vfit, _ = _fit_score("u16", X[:3000], y[:3000], X[3000:3001])
+    model.set_tile_config(variant, 0, 0, 0)
+    codes, e = formats.pack_e4m3(X[3000:])
+    assert (e == 0).any() and (e == 1).any()
+    codes[0, 5], codes[1, 9] = 0x30, 0x3C          # 0.5 and 1.5: not integer counts
+    e[2] = 2                                       # row scale outside {2^0, 2^1}
+    ld = (F + 15) // 16 * 16
+    B = np.zeros((codes.shape[0], ld), np.uint8)
+    B[:, :F] = codes
+    f = nb.Features(torch.from_numpy(B).cuda()[:, :F], nb.NB_FP8E4M3,
+                    row_exp=torch.from_numpy(e).cuda())
+    _, ref = oracle_mn(vfit, y[:3000], 2, formats.unpack_e4m3(codes, e))
+    for mode in (nb.NB_RECHECK_LP, nb.NB_RECHECK_LABEL, nb.NB_RECHECK_OFF):
+        res = to_np(nb.score(model, f, recheck=mode))
+        if mode == nb.NB_RECHECK_OFF:   # the three odd rows are still recomputed in FP64
+            compare({k: (v[:3] if isinstance(v, np.ndarray) else v) for k, v in res.items()},
+                    {k: (v[:3] if isinstance(v, np.ndarray) else v) for k, v in ref.items()})
+        else:
+            compare(res, ref, check_lp=mode == nb.NB_RECHECK_LP)
+        assert 3 <= res["n_rechecked"] <= 3 + 40 + int((e >= 2).sum()), (mode, res["n_rechecked"])
+
+
 def test_score_two_class_low_totals_near_ties():
     # small totals and overlapping profiles: many rows near the boundary,
     # which exercises the marked-row FP64 recheck
