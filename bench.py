@@ -435,7 +435,7 @@ GW_F = 1024
 GW_KS = (20, 40, 80, 100, 160, 200)
 
 
-def run_groupwise(args, device, reps=20, warm=3):
+def run_groupwise(args, device, reps=20, warm=3, ks=None):
     """Sec. 3/4 pipeline on full u8 opcode histograms: train per size group
     (100 groups of 5 KB, small-group fallback, top-k opcodes by normalised
     class difference), then classify N files: route + gather + one batched
@@ -454,7 +454,8 @@ def run_groupwise(args, device, reps=20, warm=3):
     torch.cuda.synchronize()   # inputs made on the default stream, used on `stream`
     stream = torch.cuda.Stream(device)
     rows = []
-    ks = [int(v) for v in args.gw_k.split(",")] if args.gw_k else list(GW_KS)
+    if ks is None:
+        ks = [int(v) for v in args.gw_k.split(",")] if args.gw_k else list(GW_KS)
     for k in ks:
         with torch.cuda.stream(stream):
             t0 = time.perf_counter()
@@ -1250,11 +1251,14 @@ def main():
     # feature-count sweep at F = 1,024 and 4,096 (u8 / FP8 / FP32 rows) and the
     # C = 64, F = 8,192 many-class workload (tensor cores; CUDA-core and plain
     # FP32 scorers on a subset beside it)
-    fsweep = many = None
+    fsweep = many = gauss = gw = None
     if ws == 1 and not args.no_extra:
         fsweep = run_fsweep(args, device, Fs=(1024, 4096))
         torch.cuda.empty_cache()
         many = run_many_class(args, device, steps=5)
+        torch.cuda.empty_cache()
+        gauss = run_gaussian(args, device)
+        gw = run_groupwise(args, device, reps=10, ks=(20, 200))
         torch.cuda.empty_cache()
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only) -----------------
@@ -1307,6 +1311,8 @@ def main():
         "serving": serving,
         "fsweep": fsweep,
         "many_class": many,
+        "gaussian": gauss,
+        "groupwise": gw,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "gpu_launches": launches,

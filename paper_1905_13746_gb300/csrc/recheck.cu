@@ -59,6 +59,11 @@ __device__ __forceinline__ double load_x(int dtype, const char* rp, int j, doubl
 }
 
 // The whole warp recomputes row r of v with model md; lane 0 writes outputs.
+// Each lane sums its features j = lane, lane + 32, ... in ascending order for
+// eight classes at a time (the row's value loaded once for the eight, eight
+// independent FMA chains); a zero count adds nothing to a multinomial score
+// (log theta is finite for alpha > 0) and is skipped.  Per class the lane's
+// sum and the butterfly over the lanes are those of one class at a time.
 __device__ __forceinline__ void recheck_row(const RView& v, const RModel& md, int64_t r,
                                             int want_lp, double* s_sh) {
   const int lane = threadIdx.x & 31;
@@ -66,30 +71,58 @@ __device__ __forceinline__ void recheck_row(const RView& v, const RModel& md, in
   const char* rp = v.X + r * v.ld * es;
   const double scale =
       (v.dtype == NB_FP8E4M3 && v.row_exp) ? ldexp(1.0, (int)v.row_exp[r]) : 1.0;
-  for (int c = 0; c < md.C; ++c) {
-    double acc = 0.0;
+  constexpr int CB = 8;
+  for (int c0 = 0; c0 < md.C; c0 += CB) {
+    const int nc = md.C - c0 < CB ? md.C - c0 : CB;
+    double acc[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) acc[k] = 0.0;
     if (md.kind == NB_MULTINOMIAL) {
-      const double* lt = md.p0 + (int64_t)c * v.F;
-      for (int j = lane; j < v.F; j += 32)
-        acc = fma(load_x(v.dtype, rp, v.cols ? v.cols[j] : j, scale), lt[j], acc);
+      const double* lt = md.p0 + (int64_t)c0 * v.F;
+      for (int j = lane; j < v.F; j += 32) {
+        const double x = load_x(v.dtype, rp, v.cols ? v.cols[j] : j, scale);
+        if (x == 0.0) continue;
+#pragma unroll
+        for (int k = 0; k < CB; ++k)
+          if (k < nc) acc[k] = fma(x, lt[(int64_t)k * v.F + j], acc[k]);
+      }
       if (v.dtype == NB_U8 && v.ovf_ptr) {
-        for (int64_t k = v.ovf_ptr[r] + lane; k < v.ovf_ptr[r + 1]; k += 32) {
-          const int j = v.ovf_col[k];
-          if (j < v.F) acc = fma((double)v.ovf_add[k], lt[j], acc);
+        for (int64_t e = v.ovf_ptr[r] + lane; e < v.ovf_ptr[r + 1]; e += 32) {
+          const int j = v.ovf_col[e];
+          if (j >= v.F) continue;
+          const double add = (double)v.ovf_add[e];
+#pragma unroll
+          for (int k = 0; k < CB; ++k)
+            if (k < nc) acc[k] = fma(add, lt[(int64_t)k * v.F + j], acc[k]);
         }
       }
     } else {
-      const double* mu = md.p0 + (int64_t)c * v.F;
-      const double* var = md.p1 + (int64_t)c * v.F;
+      const double* mu = md.p0 + (int64_t)c0 * v.F;
+      const double* var = md.p1 + (int64_t)c0 * v.F;
       for (int j = lane; j < v.F; j += 32) {
-        const double dx = load_x(v.dtype, rp, j, scale) - mu[j];
-        acc += dx * dx / var[j];
+        const double x = load_x(v.dtype, rp, j, scale);
+#pragma unroll
+        for (int k = 0; k < CB; ++k) {
+          if (k < nc) {
+            const double dx = x - mu[(int64_t)k * v.F + j];
+            acc[k] += dx * dx / var[(int64_t)k * v.F + j];
+          }
+        }
       }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
-    if (lane == 0)
-      s_sh[c] = md.kind == NB_MULTINOMIAL ? md.log_pi[c] + acc : md.gconst[c] - 0.5 * acc;
+    for (int k = 0; k < CB; ++k) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < CB; ++k) {
+        const int c = c0 + k;
+        if (k < nc)
+          s_sh[c] = md.kind == NB_MULTINOMIAL ? md.log_pi[c] + acc[k] : md.gconst[c] - 0.5 * acc[k];
+      }
+    }
   }
   __syncwarp();
   if (lane == 0) {
@@ -117,6 +150,7 @@ struct RArgs {
   int64_t n;
   int want_lp;
   int counted;   // *n_rechecked already holds the marked rows (skip when 0, do not add)
+  int rows;      // rows per warp chunk (a power of two <= 32)
   unsigned long long* n_rechecked;
 };
 
@@ -125,11 +159,15 @@ __global__ void __launch_bounds__(256) k_recheck(const RArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   pdl_wait();   // the scorer's labels and mark count
   if (a.counted && *a.n_rechecked == 0ull) return;   // the scorer marked no row
+  // a warp takes chunks of a.rows rows (lanes below a.rows read a label) and
+  // recomputes the chunk's marked rows one after another; small calls use short
+  // chunks, so that densely marked rows spread over many warps
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   unsigned long long cnt = 0;
-  for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < a.n; base += nwarps * 32) {
+  for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * a.rows; base < a.n;
+       base += nwarps * a.rows) {
     const int64_t row = base + lane;
-    const bool f = row < a.n && a.v.label[row] == kLabelRecheck;
+    const bool f = lane < a.rows && row < a.n && a.v.label[row] == kLabelRecheck;
     unsigned m = __ballot_sync(0xFFFFFFFFu, f);
     while (m) {
       const int src = __ffs(m) - 1;
@@ -163,10 +201,15 @@ nb_status launch_recheck(const nb_model* m, const void* X, nb_dtype dt, int64_t 
   a.want_lp = o.want_lp;
   a.counted = o.counted ? 1 : 0;
   a.n_rechecked = reinterpret_cast<unsigned long long*>(o.n_rechecked);
-  const int64_t chunks = (n + 255) / 256;
-  const int64_t cap = (int64_t)num_sms() * 8;
+  // rows per warp chunk: 32, halved while the call has fewer chunks than the
+  // grid has warps (down to one row per warp)
+  const int64_t cap = (int64_t)num_sms() * 8;   // blocks of 8 warps
+  int rows = 32;
+  while (rows > 1 && (n + rows - 1) / rows < cap * 8) rows >>= 1;
+  a.rows = rows;
+  const int64_t blocks = ((n + rows - 1) / rows + 7) / 8;
   count_launch();
-  NB_TRY_CUDA(launch_pdl(k_recheck, dim3((unsigned)(chunks < cap ? chunks : cap)), dim3(256), 0,
+  NB_TRY_CUDA(launch_pdl(k_recheck, dim3((unsigned)(blocks < cap ? blocks : cap)), dim3(256), 0,
                          st, a),
               "k_recheck launch");
   return NB_OK;
