@@ -169,11 +169,34 @@ def test_many_class_workload_full_size():
     s = np.exp(res["lp"].astype(np.float64)).sum(axis=1)
     assert np.abs(s - 1.0).max() < 1e-5
 
+    # the same rows stored BF16 (exact below 256) and FP8 E4M3 (rounded, row
+    # scale 2^0), scored on the tensor cores as the benchmark times them
+    host = _rows_host(X, rows)
+    for tdt, code in ((torch.bfloat16, nb.NB_BF16), (torch.float8_e4m3fn, nb.NB_FP8E4M3)):
+        Xs = torch.empty((Nm, Fm), dtype=tdt, device="cuda")
+        for r0 in range(0, Nm, 1 << 17):
+            Xs[r0:r0 + (1 << 17)] = X[r0:r0 + (1 << 17)].to(torch.float32).to(tdt)
+        f = nb.Features(Xs.view(torch.uint8) if code == nb.NB_FP8E4M3 else Xs, code)
+        assert nb.score_path(model, f) == nb.NB_PATH_TENSOR
+        r = to_np(nb.score(model, f))
+        torch.cuda.synchronize()
+        if code == nb.NB_BF16:
+            vals = host.astype(np.float64)
+        else:
+            codes, e = formats.pack_e4m3(host)
+            assert (e == 0).all()
+            assert (_rows_host(Xs.view(torch.uint8), rows) == codes).all()
+            vals = formats.unpack_e4m3(codes, e)
+        compare(r, oracle.score(vals, ref_model), rows=rows)
+        assert (r["label"] < C).all()
+        del Xs, f
+        torch.cuda.empty_cache()
+
 
 def test_feature_sweep_widest_point_full_size():
     # F = 16,384, N = 1M u8 counts (Dirichlet(0.05) profiles, 30% shared),
-    # fit on the first third; u8 scored with log posteriors, FP8 E4M3 rows
-    # (per-row exponent) with the label recheck: the oracle on sampled rows
+    # fit on the first third; u8 and FP8 E4M3 rows (per-row exponent) scored
+    # with log posteriors: the oracle on sampled rows
     seed = synth.seed_for(3)
     Fs = 16384
     Ns = 1_000_000
@@ -211,11 +234,16 @@ def test_feature_sweep_widest_point_full_size():
     ref_codes, ref_e = formats.pack_e4m3(Xs)
     assert (c8 == ref_codes).all() and (e8 == ref_e).all()
     ref8 = oracle.score(formats.unpack_e4m3(c8, e8), ref_model)
-    # the default shape and the register-streaming kernel; label mode
-    # guarantees the labels, not the log posteriors
+    # the default shape and the register-streaming kernel: exact integer
+    # counts, so labels and log posteriors both meet the tolerance, and the two
+    # kernels give the same bits
+    outs = []
     for cfg in [(nb.NB_VARIANT_AUTO, 0, 0, 0), (nb.NB_VARIANT_REGISTER, 0, 0, 0)]:
         model.set_tile_config(*cfg)
-        res8 = to_np(nb.score(model, f8, recheck=nb.NB_RECHECK_LABEL))
+        res8 = to_np(nb.score(model, f8, recheck=nb.NB_RECHECK_LP))
         torch.cuda.synchronize()
-        compare(res8, ref8, check_lp=False, rows=rows)
+        compare(res8, ref8, rows=rows)
         assert not (res8["label"] == 255).any()
+        outs.append(res8)
+    assert (outs[0]["label"] == outs[1]["label"]).all()
+    assert (outs[0]["margin"].view(np.uint32) == outs[1]["margin"].view(np.uint32)).all()

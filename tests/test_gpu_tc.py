@@ -161,3 +161,21 @@ def test_tensor_scorer_bf16_values_outside_the_count_check():
         flagged = [r for r in odd if r != 3]
         assert res["n_rechecked"] >= len(flagged), (mode, res["n_rechecked"])
         compare(res, ref, check_lp=mode == nb.NB_RECHECK_LP)
+
+
+@pytest.mark.parametrize("fmt", ["u8", "u8ovf", "bf16", "fp8"])
+def test_tensor_scorer_empty_and_single_row(fmt):
+    # no rows, one row (a single ragged tile), and 129 rows (one full tile and
+    # one row of the next)
+    C, F = 5, 300
+    X, y, _ = count_matrix(1190, 3000, F, C=C, conc=0.1, clip=255)
+    model, vfit = _model("u8", X, y, C)
+    e, _ = stored(X[:0], fmt)
+    r0 = nb.score(model, e)
+    assert r0["label"].numel() == 0 and int(r0["n_rechecked"].item()) == 0
+    for n in (1, 129):
+        f, v = stored(X[:n], fmt)
+        assert nb.score_path(model, f) == nb.NB_PATH_TENSOR
+        res = to_np(nb.score(model, f, recheck=nb.NB_RECHECK_LP))
+        _, ref = oracle_mn(vfit, y, C, v)
+        compare(res, ref)

@@ -212,3 +212,14 @@ def test_gaussian_log_posterior_mode_close_classes():
     _, res = _score(model, Xs, nb.NB_RECHECK_LP)
     compare(res, oracle.score(Xs, oracle.gauss_fit(Xf, yf, C)))
     assert res["n_rechecked"] > 0
+
+
+def test_gaussian_tensor_scorer_empty_and_single_row():
+    Xf, yf, Xs = _data(1800, 6, 40, 20, 200)
+    model = _fit(Xf, yf, 6)
+    X0, r0 = _score(model, Xs[:0], nb.NB_RECHECK_LABEL)
+    assert r0["label"].size == 0
+    for n in (1, 129):
+        X, res = _score(model, Xs[:n], nb.NB_RECHECK_LABEL)
+        assert nb.score_path(model, X, nb.NB_RECHECK_LABEL) == nb.NB_PATH_TENSOR_GAUSS
+        compare(res, oracle.score(Xs[:n], oracle.gauss_fit(Xf, yf, 6)), check_lp=False)
