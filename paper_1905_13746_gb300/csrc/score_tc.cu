@@ -636,7 +636,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
   if (warp == TC_WORK) {
     // ---- weight-limb producer -----------------------------------------
     if (lane == 0) {
-      long long bi = 0, last[TC_NB] = {-1, -1, -1, -1, -1};
+      long long bi = 0, last[TC_NB];
+      for (int s = 0; s < TC_NB; ++s) last[s] = -1;
       bool ok = true;
       for (long long it = 0; it < my_units && ok && !tc_aborted(sh); ++it) {
         const long long t = blockIdx.x + it * gridDim.x;
@@ -666,7 +667,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
   } else if (warp == TC_WORK + 2) {
     // ---- row producer (pair pass) ----------------------------------------
     if (MODE == 0 && lane == 0) {
-      long long ri = 0, last[TC_NRAW] = {-1, -1};
+      long long ri = 0, last[TC_NRAW];
+      for (int s = 0; s < TC_NRAW; ++s) last[s] = -1;
       bool ok = (smem_addr(raw) & 1023u) == 0;   // the swizzled reads assume 1 KB alignment
       if (!ok) {
         atomicOr(a.status, ST_TIMEOUT);
