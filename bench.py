@@ -271,12 +271,12 @@ def time_e2e(model, host, make_dev, out_like, n_tr, steps, warmup, stream):
 # ----------------------------------------------------------------------------
 # feature-count sweep and the small Gaussian workload
 # ----------------------------------------------------------------------------
-def _time_score(model, f, stream, reps=5, warm=2, recheck=None):
+def _time_score(model, f, stream, reps=5, warm=2, recheck=None, out=None):
     import torch
 
     import paper_1905_13746_gb300 as nb
     rc = nb.NB_RECHECK_LP if recheck is None else recheck
-    out = _out(f.n, model.C, f.data.device)
+    out = _out(f.n, model.C, f.data.device) if out is None else out
     with torch.cuda.stream(stream):
         for _ in range(warm):
             nb.score(model, f, out=out, stream=stream, recheck=rc)
@@ -288,6 +288,16 @@ def _time_score(model, f, stream, reps=5, warm=2, recheck=None):
         e1.record(stream)
         stream.synchronize()
     return e0.elapsed_time(e1) / reps, int(out["n_rechecked"].item())
+
+
+def _agreement(out, ref):
+    """Labels and log posteriors of a lossy storage format against the exact
+    format's (whose labels equal the FP64 decision on the raw counts)."""
+    import torch
+    same = (out["label"] == ref["label"]).double().mean().item()
+    d = (out["logpost"].double() - ref["logpost"].double()).abs() / \
+        ref["logpost"].double().abs().clamp(min=1.0)
+    return {"label_agreement": same, "max_lp_err": d.max().item()}
 
 
 def run_fsweep(args, device, Fs=(64, 256, 1024, 4096, 16384)):
@@ -323,7 +333,8 @@ def run_fsweep(args, device, Fs=(64, 256, 1024, 4096, 16384)):
         except nb.NbError as e:       # keep the default shape, say why
             tune_err = str(e)
             m.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
-        u8_ms, u8_re = _time_score(m, fu8, stream)
+        u8_out = _out(N, 2, device)
+        u8_ms, u8_re = _time_score(m, fu8, stream, out=u8_out)
         tuned = list(m.tile_config())
         m.set_tile_config(nb.NB_VARIANT_AUTO, 0, 0, 0)
         src = X.to(torch.float32) if N * F * 4 <= (16 << 30) else X.to(torch.int32).to(torch.uint16)
@@ -354,7 +365,11 @@ def run_fsweep(args, device, Fs=(64, 256, 1024, 4096, 16384)):
             m.set_tile_config(*best[2])
             return best
         fp8_ms, fp8_re, tc8 = best_for(f8, nb.NB_RECHECK_LP)
-        del f8
+        # E4M3 rounds counts above 16: its results against the raw counts' (u8)
+        f8_out = _out(N, 2, device)
+        _time_score(m, f8, stream, reps=1, warm=0, out=f8_out)
+        fp8_vs_raw = _agreement(f8_out, u8_out)
+        del f8, f8_out
         n32 = min(N, (48 << 30) // (4 * F))
         f32 = nb.Features(X[:n32].to(torch.float32), nb.NB_F32)
         torch.cuda.synchronize()
@@ -372,13 +387,14 @@ def run_fsweep(args, device, Fs=(64, 256, 1024, 4096, 16384)):
             "fp8": {"ms": fp8_ms, "files_per_s": N / (fp8_ms * 1e-3),
                     "gbs": N * (F + 1 + lp) / (fp8_ms * 1e-3) / 1e9,
                     "frac": N * (F + 1 + lp) / (fp8_ms * 1e-3) / 1e9 / hbm_peak,
-                    "recheck": "lp", "n_rechecked": fp8_re, "tile_config": tc8},
+                    "recheck": "lp", "n_rechecked": fp8_re, "tile_config": tc8,
+                    "vs_raw_counts": fp8_vs_raw},
             "f32": {"files": n32, "ms": f32_ms, "files_per_s": n32 / (f32_ms * 1e-3),
                     "gbs": n32 * (4 * F + lp) / (f32_ms * 1e-3) / 1e9,
                     "frac": n32 * (4 * F + lp) / (f32_ms * 1e-3) / 1e9 / hbm_peak,
                     "recheck": "label", "n_rechecked": f32_re, "n_rechecked_lp_mode": f32_lp,
                     "tile_config": tc32}})
-        del X, fu8, m
+        del X, fu8, m, u8_out
         torch.cuda.empty_cache()
     return {"workload": "two classes, Dirichlet(0.05) profiles with 30% shared features, "
                         "lognormal(8.5, 1) totals, counts clamped at 255; score with log "
@@ -760,6 +776,7 @@ def run_many_class(args, device, steps=None):
     # BF16, rounded to E4M3 with row scale 2^0), scored on the tensor cores with
     # log posteriors and the FP64 recheck
     storage = {}
+    u8_ref = {k: v.clone() for k, v in out.items()}   # the timed u8 step's results
     for name, tdt, code, esz in (("bf16", torch.bfloat16, nb.NB_BF16, 2),
                                  ("fp8", torch.float8_e4m3fn, nb.NB_FP8E4M3, 1)):
         Xs = torch.empty((N, F), dtype=tdt, device=device)
@@ -783,9 +800,11 @@ def run_many_class(args, device, steps=None):
                          "files_per_s": N / (ms * 1e-3), "gbs": b_s / (ms * 1e-3) / 1e9,
                          "frac_of_max_t_mem_t_flop":
                              max(b_s / (hbm_peak * 1e9) * 1e3, t_flop) / ms,
-                         "n_rechecked": int(out["n_rechecked"].item())}
+                         "n_rechecked": int(out["n_rechecked"].item()),
+                         "vs_raw_counts": _agreement(out, u8_ref)}
         del fs, Xs
         torch.cuda.empty_cache()
+    del u8_ref
     line = {
         "workload": f"multinomial NB, C={C} (Zipf 1.1 priors), N={N} files x F={F} counts "
                     f"(Dirichlet(0.1) profiles, lognormal(8.5, 1) totals, clamped at 255, "
