@@ -233,7 +233,7 @@ def test_feature_sweep_widest_point_full_size():
     c8, e8 = _rows_host(codes, rows), _rows_host(rexp, rows)
     ref_codes, ref_e = formats.pack_e4m3(Xs)
     assert (c8 == ref_codes).all() and (e8 == ref_e).all()
-    ref8 = oracle.score(formats.unpack_e4m3(c8, e8), ref_model)
+    ref8 = oracle.score(formats.unpack_e4m3(ref_codes, ref_e), ref_model)
     # the default shape and the register-streaming kernel: exact integer
     # counts, so labels and log posteriors both meet the tolerance, and the two
     # kernels give the same bits

@@ -50,8 +50,9 @@ def test_fit_counts_exact(fmt, F):
     counts, nc = model.counts()
     ref_counts = np.stack([vals[y == c].sum(axis=0) for c in range(2)]).astype(np.uint64)
     assert (counts == ref_counts).all()
-    assert nc.tolist() == [int((y == 0).sum()), int((y == 1).sum())]
-    ref = oracle.mn_finalize(ref_counts, nc, len(y))
+    ref_nc = np.array([(y == c).sum() for c in range(2)], dtype=np.uint64)
+    assert (nc == ref_nc).all()
+    ref = oracle.mn_finalize(ref_counts, ref_nc, len(y))
     lt, _, lpi = model.params()
     assert np.allclose(lt, ref["log_theta"], rtol=1e-14, atol=1e-13)
     assert np.allclose(lpi, ref["log_pi"], rtol=1e-14, atol=1e-14)
