@@ -209,15 +209,17 @@ __device__ __forceinline__ uint32_t bf16x2_tiny(uint32_t w) {
 
 // Count check of an FP16 pair h against the magic pair m2 = (M, M), M = 2^(10-e):
 // with w = h + M (FP16), a half of h is a non-negative multiple of 2^-e below M
-// exactly when that half of w lies in [M, 2M) (M's sign and exponent field)
-// and w - M == h; its count h 2^e is then the low 10 bits of w, added to the
-// packed lanes of tacc.  Returns non-zero when either half fails.
-__device__ __forceinline__ uint32_t f16x2_count_check(uint32_t h, uint32_t m2, uint32_t& tacc) {
+// exactly when that half of w lies in [M, 2M) (its sign and exponent field is
+// M's) and w - M == h; its count h 2^e is then the low 10 bits of w.  A failing
+// half leaves a bit in bd.  The biased halves M + x are summed into tt (the
+// caller removes M per value).
+__device__ __forceinline__ void f16x2_count_check(uint32_t h, uint32_t m2, uint32_t& tt,
+                                                  uint32_t& bd) {
   uint32_t w, back;
   asm("add.rn.f16x2 %0, %1, %2;" : "=r"(w) : "r"(h), "r"(m2));
   asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(back) : "r"(w), "r"(m2));
-  tacc += w & 0x03FF03FFu;
-  return (back ^ h) | ((w & 0xFC00FC00u) ^ m2);
+  bd |= (back ^ h) | ((w & 0xFC00FC00u) ^ m2);
+  tt = (uint32_t)dp2a_lo_us(w, 0x01010101u, (int)tt);
 }
 
 // bounded wait that sleeps in the barrier instead of polling
@@ -947,12 +949,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             }
           }
           // every value an integer count x = v 2^e below 1024: x sits in the
-          // low 10 bits of v + M, summed in packed 16-bit lanes (16 words of at
-          // most 1023 per lane)
-          uint32_t tacc = 0u;
+          // low 10 bits of v + M; T sums M + x (at most 2^15 + 2^10 for each of
+          // 32 values per A stage: no wrap below 2^32 for F <= 8192)
 #pragma unroll
-          for (int k = 0; k < PS::COLS; ++k) bad |= f16x2_count_check(o[k], m2, tacc);
-          T += (tacc & 0xFFFFu) + (tacc >> 16);
+          for (int k = 0; k < PS::COLS; ++k) f16x2_count_check(o[k], m2, T, bad);
         }
         if constexpr (MODE == 0) {
           if (c_ka % RAW_A == RAW_A - 1 || c_ka == nka - 1) {   // done with the row stage
@@ -996,8 +996,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_score_tc(const __grid_constan
             int g = 0;
             const long long r = row_of(c_i, g);
             const SegGroup& G = tc_group(a, g);
-            if (!tc_epilogue<MODE>(a, sh, xe, G, a.models[G.model], r, xr, h, part,
-                                   bad ? 0xFFFFFFFFu : T, rsc, lane_base, ep)) {
+            uint32_t Tu = T;
+            if (DT != NB_U8) {
+              // the unit's check; then the counts' total without the bias M of
+              // each of the 2 COLS values of every A stage
+              Tu = bad != 0u ? 0xFFFFFFFFu
+                        : T - (m2 & 0xFFFFu) * (uint32_t)(2 * PS::COLS) * (uint32_t)nka;
+            }
+            if (!tc_epilogue<MODE>(a, sh, xe, G, a.models[G.model], r, xr, h, part, Tu, rsc,
+                                   lane_base, ep)) {
               ok = false;
               break;
             }
