@@ -63,6 +63,11 @@ constexpr int TG_FPW = TG_FS / TG_PARTS;   // features per converter thread per 
 constexpr int TG_EPI = 4;                  // epilogue warps: one per lane quadrant
 constexpr int TG_THREADS = (TG_CONV + TG_EPI + 3) * 32;
 constexpr uint32_t TG_RAW_BYTES = TG_M * TG_BOXF * 4;   // 16 KB
+// a row slot: the box, then the box's features' centres, B bounds and A
+// bounds (TG_BOXF floats each), padded to keep the next box 1 KB aligned
+constexpr uint32_t TG_TAB_BYTES = 3 * TG_BOXF * 4;
+constexpr uint32_t TG_SLOT_BYTES = TG_RAW_BYTES + 1024;
+static_assert(TG_TAB_BYTES <= 1024 && TG_BOXF == TG_FS, "a row slot holds one stage's tables");
 constexpr int TG_ACC = 64;                 // accumulator buffer b at columns 64 b
 constexpr int TG_ACOL = 2 * TG_ACC;        // A stage s at columns 128 + TG_ACOLS s
 constexpr int TG_ACOLS = TG_KS / 2;        // tensor-memory columns of an A stage
@@ -134,8 +139,17 @@ __device__ __forceinline__ bool tg_wait_warp(TgShared& sh, uint64_t* bar, uint32
 
 template <int N>
 __device__ __forceinline__ void tg_lds(uint32_t addr, float (&x)[N]) {
-  static_assert(N == 2 || N == 4, "two or four features per load");
-  if constexpr (N == 4) {
+  static_assert(N == 2 || N == 4 || N == 8, "two, four or eight features per load");
+  if constexpr (N == 8) {
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
+                 : "r"(addr)
+                 : "memory");
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "r"(addr + 16u)
+                 : "memory");
+  } else if constexpr (N == 4) {
     asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
                  : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
                  : "r"(addr)
@@ -197,7 +211,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_score_tcg(const __grid_consta
   extern __shared__ __align__(1024) uint8_t tg_smem[];
   TgShared& sh = *reinterpret_cast<TgShared*>(tg_smem);
   uint8_t* raw = tg_smem + ((sizeof(TgShared) + 1023) / 1024) * 1024;   // 1 KB aligned
-  uint8_t* B = raw + (size_t)TG_NRAW * TG_RAW_BYTES;
+  uint8_t* B = raw + (size_t)TG_NRAW * TG_SLOT_BYTES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_units = (a.n + TG_M - 1) / TG_M;
   const long long my_units =
@@ -259,12 +273,18 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_score_tcg(const __grid_consta
             ok = false;
             break;
           }
-          mbar_expect_tx(&sh.raw_full[slot], TG_RAW_BYTES);
+          uint8_t* dst = raw + (size_t)slot * TG_SLOT_BYTES;
+          mbar_expect_tx(&sh.raw_full[slot], TG_RAW_BYTES + TG_TAB_BYTES);
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(raw + (size_t)slot * TG_RAW_BYTES)),
+              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
               "l"(map), "r"(f0), "r"((int)(t * TG_M)), "r"(smem_addr(&sh.raw_full[slot]))
               : "memory");
+          // the box's per-feature tables (the tables are padded to a multiple
+          // of TG_FS features, so f0 + TG_BOXF stays inside them)
+          bulk_g2s(dst + TG_RAW_BYTES, a.ctr + f0, 4 * TG_BOXF, &sh.raw_full[slot]);
+          bulk_g2s(dst + TG_RAW_BYTES + 4 * TG_BOXF, a.bmax + f0, 4 * TG_BOXF, &sh.raw_full[slot]);
+          bulk_g2s(dst + TG_RAW_BYTES + 8 * TG_BOXF, a.amax + f0, 4 * TG_BOXF, &sh.raw_full[slot]);
           last[slot] = ri;
         }
       }
@@ -394,7 +414,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_score_tcg(const __grid_consta
         // 4 TG_FPW part of the row's 128-byte segment, whose 16-byte chunks are
         // swizzled by the row
         const int byte = 4 * TG_FS * (ks % TG_SPB) + 4 * TG_FPW * part;
-        const uint32_t rs = raw_s + slot * TG_RAW_BYTES;
+        const uint32_t rs = raw_s + slot * TG_SLOT_BYTES;
         float xs[TG_FPW];
         if constexpr (TG_FPW == 8) {
           float lo[4], hi[4];
@@ -408,16 +428,18 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_score_tcg(const __grid_consta
         } else {
           tg_lds(rs + (uint32_t)((((byte >> 4) ^ (r & 7)) << 4) | (byte & 15)), xs);
         }
+        // this thread's features' centres and bounds, staged with the box
+        float ctr[TG_FPW], bm[TG_FPW], am[TG_FPW];
+        const uint32_t tab = smem_addr(raw) + slot * TG_SLOT_BYTES + TG_RAW_BYTES +
+                             (uint32_t)(4 * TG_FPW * part);   // the same for every row
+        tg_lds(tab, ctr);
+        tg_lds(tab + 4 * TG_BOXF, bm);
+        tg_lds(tab + 8 * TG_BOXF, am);
         if (ks % TG_SPB == TG_SPB - 1 || ks == nks - 1) {   // done with the row box
           __syncwarp();
           if (lane == 0) mbar_arrive(&sh.raw_empty[slot]);
           ++ri;
         }
-        const int j0 = TG_FS * ks + TG_FPW * part;
-        float ctr[TG_FPW], bm[TG_FPW], am[TG_FPW];
-        tg_ldg(a.ctr + j0, ctr);
-        tg_ldg(a.bmax + j0, bm);
-        tg_ldg(a.amax + j0, am);
         uint32_t o[4 * TG_FPW];
 #pragma unroll
         for (int f = 0; f < TG_FPW; ++f) {
@@ -753,7 +775,7 @@ nb_status launch_score_tcg(const nb_model* m, const float* X, int64_t n, int64_t
   a.want_lp = o.want_lp;
   a.recheck = o.recheck;
   a.status = m->d.sstatus;
-  const size_t smem = ((sizeof(TgShared) + 1023) / 1024) * 1024 + (size_t)TG_NRAW * TG_RAW_BYTES +
+  const size_t smem = ((sizeof(TgShared) + 1023) / 1024) * 1024 + (size_t)TG_NRAW * TG_SLOT_BYTES +
                       (size_t)a.nb * a.Cp * (2 * TG_KS);
   // more than half the shared memory of an SM keeps one CTA (and one
   // tensor-memory allocation) per SM
