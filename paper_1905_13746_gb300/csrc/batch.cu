@@ -196,6 +196,10 @@ nb_status nbg::batch_create(const nb_model* const* models, int n_models, nb_dtyp
     return s;
   };
   const int es = elem_size(dtype);
+  if (!b->fam[0].empty() && dtype != NB_U8 && dtype != NB_F32) {
+    set_error("nb_batch_create: two-class models batch U8 or F32 rows");
+    return fail(NB_EINVAL);
+  }
   if (!b->fam[0].empty()) {
     nb_status s = seg2_plan(dtype, F, b->F_pad, max_ld * es, (int)b->fam[0].size(), plain,
                             &b->plan, &b->kv, &b->rpw, &b->ncw, &b->smem);

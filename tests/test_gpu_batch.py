@@ -87,6 +87,10 @@ def test_batch_equals_single_groups_and_oracle(fmt):
 
 def test_batch_rejects_bad_groups():
     mods = _models(256, "u8", 3, [2])
+    # two-class models batch u8 or f32 rows only
+    for dt in (nb.NB_FP8E4M3, nb.NB_BF16, nb.NB_U16):
+        with pytest.raises(nb.NbError):
+            nb.Batch([mods[0][0]], dt, 256, 4)
     f, _ = stored(np.zeros((10, 256), np.int64), "u8")
     batch = nb.Batch([mods[0][0]], nb.NB_U8, 256, 4)
     out = batch.outputs(0, 10)
