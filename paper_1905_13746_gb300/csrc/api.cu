@@ -75,8 +75,8 @@ static nb_status alloc_model(nb_model* m) {
   const size_t o_w = take(sizeof(float) * C * Fp);
   const size_t o_bias = take(sizeof(float) * C);
   const size_t o_wmax = take(sizeof(float) * 4);
-  const size_t o_gmu = take(m->kind == NB_GAUSSIAN ? sizeof(float) * C * Fp : 0);
-  const size_t o_giv = take(m->kind == NB_GAUSSIAN ? sizeof(float) * C * Fp : 0);
+  const size_t o_gmu = take(m->kind == NB_GAUSSIAN ? sizeof(float) * gauss_cpad(C) * Fp : 0);
+  const size_t o_giv = take(m->kind == NB_GAUSSIAN ? sizeof(float) * gauss_cpad(C) * Fp : 0);
   const size_t o_gk = take(sizeof(float) * C);
   const bool tc = tc_tables(m->kind, m->C, m->F);
   const size_t o_tcw = take(tc ? tc_w_bytes(m->C, m->F) : 0);

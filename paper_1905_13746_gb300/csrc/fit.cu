@@ -978,9 +978,11 @@ __global__ void __launch_bounds__(256) k_gauss_finalize(
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gm = fmax(gm, red[w]);
   const double eps = var_smoothing * gm;
   __syncthreads();
-  for (int k = threadIdx.x; k < C * F_pad; k += blockDim.x) {
-    const int c = k / F_pad, j = k % F_pad;
-    if (j >= F) {
+  // the FP32 tables feature-major, gauss_cpad(C) classes per feature
+  const int CP = gauss_cpad(C);
+  for (int k = threadIdx.x; k < CP * F_pad; k += blockDim.x) {
+    const int j = k / CP, c = k % CP;
+    if (j >= F || c >= C) {
       g_mu[k] = 0.f;
       g_ivar[k] = 0.f;
       continue;

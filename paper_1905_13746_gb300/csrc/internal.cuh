@@ -72,6 +72,9 @@ struct TcHeader {
 
 // tensor-core scorer limits: classes, features
 constexpr int kTcMaxC = 64;
+// classes of a Gaussian model's FP32 tables per feature: blocks of 4 (C <= 4)
+// or 16, the class blocks of the CUDA-core scorer
+__host__ __device__ constexpr int gauss_cpad(int C) { return C <= 4 ? 4 : ((C + 15) / 16) * 16; }
 constexpr int kTcMaxF = 32768;
 constexpr int kTcgMaxF = 8192;   // Gaussian tensor-core tables
 constexpr int kTcgFS = 32;       // ... features per stage (a multiple of 8 dividing 32)
@@ -113,8 +116,8 @@ struct ModelDev {
   int32_t* tc_q;       // C x F fixed-point weights
   TcHeader* tc_hdr;    // 1
   // Gaussian FP32 tables
-  float* g_mu;         // C x F_pad
-  float* g_ivar;       // C x F_pad  1 / var
+  float* g_mu;         // F_pad x gauss_cpad(C), feature-major (classes past C: 0)
+  float* g_ivar;       // same layout, 1 / var
   float* g_const;      // C          gconst in FP32
   // Gaussian tensor-core tables (3 <= C <= kTcMaxC, F <= kTcgMaxF), else nullptr;
   // the FP16 limbs of B and A go to tc_w

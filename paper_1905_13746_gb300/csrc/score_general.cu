@@ -285,8 +285,21 @@ __global__ void __launch_bounds__(256) k_score_gen(const GArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Gaussian scorer: a warp per row, classes one after another
+// Gaussian scorer on the CUDA cores (any 2 <= C <= 64, FP32 rows)
 // ---------------------------------------------------------------------------
+// s_c = k_c - 1/2 sum_j v_cj (x_j - mu_cj)^2 (Sec. 4 with Gaussian class
+// conditionals; v = 1/var, k_c = log pi_c - 1/2 sum_j log(2 pi var_cj)).
+// A group of LPR lanes scores R rows at once: lane li takes features j = li,
+// li + LPR, ..., and for each block of CB classes keeps CB x R partial sums
+// q = sum v dx^2.  The block's warps stage mu and v of a chunk of features
+// (feature-major tables, CB consecutive classes per feature) in shared
+// memory, so that each is read from L2 once per block of rows and from
+// shared memory once per R rows.  The group's partial sums are combined by a
+// reduce-scatter (each exchange halves the values a lane holds: CB R (LPR -
+// 1) / LPR shuffles instead of CB R log2 LPR), which leaves lane li with the
+// finished sums of classes-and-rows li CB R / LPR ...; their scores and
+// bounds go to shared memory, and the LPR lanes then share each row's
+// arg-max, sum of exponentials, recheck tests and log-posterior stores.
 struct GGArgs {
   const float* X;
   int64_t ld, n;
@@ -300,94 +313,251 @@ struct GGArgs {
   int want_lp, recheck;
 };
 
-__global__ void __launch_bounds__(256) k_score_gauss(const GGArgs a) {
-  __shared__ float ssh[8][kTcMaxC], tsh[8][kTcMaxC];
+constexpr int kGaussWarps = 8;
+
+// lowest index among equal maxima; NaN never wins
+__device__ __forceinline__ void gauss_top2(float& b1, int& i1, float& b2, float ob1, int oi1,
+                                           float ob2) {
+  const bool other = ob1 > b1 || (ob1 == b1 && oi1 < i1);
+  const float lo = other ? b1 : ob1;
+  if (other) {
+    b1 = ob1;
+    i1 = oi1;
+  }
+  b2 = fmaxf(fmaxf(b2, ob2), lo);
+}
+
+template <int LPR, int R, int CB>
+__global__ void __launch_bounds__(kGaussWarps * 32, 2) k_score_gauss(const GGArgs a) {
+  constexpr int G = 32 / LPR;     // row groups per warp
+  constexpr int RPW = G * R;      // rows per warp
+  constexpr int RPB = kGaussWarps * RPW;   // rows per block tile
+  constexpr int NP = CB * R;      // sums q of a class block
+  constexpr int OWN = NP / LPR;   // pairs a lane finishes
+  constexpr int CM = CB == 4 ? 4 : kTcMaxC;   // classes kept per row
+  constexpr int FPL = LPR == 8 ? 8 : 4;   // features per lane per staged chunk
+  constexpr int FC = LPR * FPL;   // features per staged chunk
+  // a staged feature holds the class block's mu (CB floats) then v; the row
+  // stride keeps eight lanes' 16-byte reads of consecutive features on
+  // distinct banks
+  constexpr int SR = CB == 4 ? 12 : 2 * CB + 4;
+  static_assert(NP % LPR == 0, "the reduce-scatter ends with whole pairs per lane");
+  __shared__ __align__(16) float s_tab[FC * SR];
+  __shared__ float s_s[kGaussWarps][RPW][CM], s_t[kGaussWarps][RPW][CM];
+  __shared__ float s_a4[kTcMaxC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const int kdepth = (a.F + 31) / 32 + 5 + 8;
-  const float gam = kdepth * 5.9604645e-8f / (1.f - kdepth * 5.9604645e-8f);
-  for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < a.n; r += nwarps) {
-    const float* xr = a.X + r * a.ld;
-    for (int c = 0; c < a.C; ++c) {
-      const float* mu = a.mu + (int64_t)c * a.F_pad;
-      const float* iv = a.ivar + (int64_t)c * a.F_pad;
-      // q = sum v dx^2 (the score); a2 = sum v |dx| |m| and a4 = sum v m^2 feed
-      // the bound below
-      float q = 0.f, a2 = 0.f, a4 = 0.f;
-      for (int j = lane; j < a.F; j += 32) {
-        const float x = __ldg(xr + j), m = mu[j], v = iv[j];
-        const float dx = x - m;
-        q = fmaf(dx * dx, v, q);
-        a2 = fmaf(fabsf(dx) * fabsf(m), v, a2);
-        a4 = fmaf(m * m, v, a4);
-      }
+  const int grp = lane / LPR, li = lane % LPR;
+  const int C = a.C, F = a.F, CP = gauss_cpad(C);
+  constexpr float u = 5.9604645e-8f;
+
+  // a4_c = sum_j mu_cj^2 v_cj (row independent; enters the bound only)
+  for (int c = warp; c < C; c += kGaussWarps) {
+    float s4 = 0.f;
+    for (int j = lane; j < F; j += 32) {
+      const float m = a.mu[(int64_t)j * CP + c];
+      s4 = fmaf(m * m, a.ivar[(int64_t)j * CP + c], s4);
+    }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        q += __shfl_xor_sync(0xFFFFFFFFu, q, off);
-        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, off);
-        a4 += __shfl_xor_sync(0xFFFFFFFFu, a4, off);
+    for (int off = 16; off > 0; off >>= 1) s4 += __shfl_xor_sync(0xFFFFFFFFu, s4, off);
+    if (lane == 0) s_a4[c] = s4;
+  }
+  __syncthreads();
+  // rounding depth of each sum: F / LPR sequential adds, the log2 LPR
+  // combining levels, and 8 for the remaining operations
+  int lg = 0;
+  while ((1 << lg) < LPR) ++lg;
+  const int kdepth = (F + LPR - 1) / LPR + lg + 8;
+  const float gam = kdepth * u / (1.f - kdepth * u);
+
+  const int64_t nbt = (a.n + RPB - 1) / RPB;
+  for (int64_t bt = blockIdx.x; bt < nbt; bt += gridDim.x) {   // uniform over the block
+    const int64_t r0 = bt * RPB + (int64_t)warp * RPW + (int64_t)grp * R;
+    const float* xr[R];
+    bool ok[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      ok[i] = r0 + i < a.n;
+      xr[i] = a.X + (ok[i] ? r0 + i : 0) * a.ld;
+    }
+    for (int cb = 0; cb < C; cb += CB) {
+      // sum p = k R + i: class cb + k, row r0 + i
+      float pq[NP];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) pq[p] = 0.f;
+      for (int f0 = 0; f0 < F; f0 += FC) {
+        // stage mu and v of features f0 .. f0 + FC - 1, classes cb .. cb + CB - 1
+        // (feature-major tables: CB consecutive floats per feature; padding
+        // classes and features past F are zero and add nothing)
+        __syncthreads();
+        for (int e = threadIdx.x; e < FC * (CB / 4) * 2; e += kGaussWarps * 32) {
+          const int fl = e / ((CB / 4) * 2), rem = e % ((CB / 4) * 2);
+          const int which = rem / (CB / 4), q4 = rem % (CB / 4);
+          const int j = f0 + fl;
+          float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (j < F)
+            v4 = __ldg(reinterpret_cast<const float4*>((which ? a.ivar : a.mu) +
+                                                       (int64_t)j * CP + cb) + q4);
+          *reinterpret_cast<float4*>(s_tab + fl * SR + which * CB + 4 * q4) = v4;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 0; jj < FPL; ++jj) {
+          const int fl = li + LPR * jj, j = f0 + fl;
+          if (j >= F) break;
+          float x[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) x[i] = ok[i] ? __ldg(xr[i] + j) : 0.f;
+          const float* tb = s_tab + fl * SR;
+#pragma unroll
+          for (int k4 = 0; k4 < CB / 4; ++k4) {
+            const float4 m4 = *reinterpret_cast<const float4*>(tb + 4 * k4);
+            const float4 v4 = *reinterpret_cast<const float4*>(tb + CB + 4 * k4);
+            const float mm[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = 4 * k4 + e;
+#pragma unroll
+              for (int i = 0; i < R; ++i) {
+                const float dx = x[i] - mm[e];
+                pq[k * R + i] = fmaf(dx * vv[e], dx, pq[k * R + i]);
+              }
+            }
+          }
+        }
       }
-      if (lane == 0) {
-        // |s - s_FP64| with u = 2^-24: per term, m = fl(mu) and v = fl(1/var)
-        // are within u relative, dx = fl(x - m) is within u(|dx| + |m|) of
-        // x - mu, so v dx^2 is within u v (4 dx^2 + 2 |dx||m|) + 2u^2 v (dx^2 +
-        // m^2); the FP32 sum adds gamma * q; kc and the final subtraction add
-        // u (|kc| + |s|).  1% slack covers the FP32 evaluation of the bound.
-        const float u = 5.9604645e-8f;
-        const float sc = a.kc[c] - 0.5f * q;
-        ssh[warp][c] = sc;
-        tsh[warp][c] = (0.5f * (u * (4.f * q + 2.f * a2) * (1.f + 2.f * u) +
-                                2.f * u * u * (q + a4) + gam * q) +
-                        u * (fabsf(a.kc[c]) + fabsf(sc))) * 1.01f +
-                       1e-12f * (q + fabsf(a.kc[c])) + 1e-30f;
+      // reduce-scatter over the group
+#pragma unroll
+      for (int off = LPR / 2, n = NP; off > 0; off >>= 1, n >>= 1) {
+        const bool up = (li & off) != 0;   // this lane keeps the upper half
+#pragma unroll
+        for (int p = 0; p < n / 2; ++p) {
+          const float sq = up ? pq[p] : pq[p + n / 2], kq = up ? pq[p + n / 2] : pq[p];
+          pq[p] = kq + __shfl_xor_sync(0xFFFFFFFFu, sq, off);
+        }
+      }
+      // lane li now holds pairs li OWN .. li OWN + OWN - 1
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        const int p = li * OWN + o, k = p / R, i = p % R, c = cb + k;
+        if (c >= C) continue;
+        const float qq = pq[o], kc = a.kc[c];
+        // |s - s_FP64| with u = 2^-24: m = fl(mu) and v = fl(1/var) are within
+        // u relative, dx = fl(x - m) within u (|dx| + |m|) of x - mu, so each
+        // term v dx^2 is within u v (4 dx^2 + 2 |dx| |m|) + 2 u^2 v (dx^2 +
+        // m^2); the FP32 sums add gam q; k_c and the final subtraction add
+        // u (|k_c| + |s|).  sum v |dx| |m| <= sqrt(sum v dx^2 sum v m^2)
+        // (Cauchy-Schwarz on the FP32 values; 1e-3 covers the rounding of the
+        // two computed sums); 1% slack covers the FP32 evaluation of the bound.
+        const float aa = sqrtf(qq * s_a4[c]) * 1.001f;
+        const float sc = kc - 0.5f * qq;
+        s_s[warp][grp * R + i][c] = sc;
+        s_t[warp][grp * R + i][c] = (0.5f * (u * (4.f * qq + 2.f * aa) * (1.f + 2.f * u) +
+                                             2.f * u * u * (qq + s_a4[c]) + gam * qq) +
+                                     u * (fabsf(kc) + fabsf(sc))) * 1.01f +
+                                    1e-12f * (qq + fabsf(kc)) + 1e-30f;
       }
     }
     __syncwarp();
-    if (lane == 0) {
-      const float* s = ssh[warp];
-      const float* t = tsh[warp];
-      int bi = 0;
-      for (int c = 1; c < a.C; ++c)
-        if (s[c] > s[bi]) bi = c;
-      float second = -INFINITY, tmax = 0.f, P = 0.f;
-      for (int c = 0; c < a.C; ++c) {
-        tmax = fmaxf(tmax, t[c]);
-        if (c == bi) continue;
-        if (s[c] > second) second = s[c];
-        P += expf(s[c] - s[bi]);
+    // epilogue: the group's lanes share each row's classes
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int rl = grp * R + i;
+      const float* sr = s_s[warp][rl];
+      const float* tr = s_t[warp][rl];
+      float b1 = -INFINITY, b2 = -INFINITY, tmax = 0.f;
+      int i1 = 0x7FFFFFFF;
+      bool nan = false;
+      for (int c = li; c < C; c += LPR) {
+        const float sv = sr[c];
+        nan |= !(sv == sv) || !(tr[c] == tr[c]);
+        tmax = fmaxf(tmax, tr[c]);
+        gauss_top2(b1, i1, b2, sv, c, -INFINITY);
       }
-      const float margin = s[bi] - second;
+#pragma unroll
+      for (int off = LPR / 2; off > 0; off >>= 1) {
+        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, off);
+        const int oi1 = __shfl_xor_sync(0xFFFFFFFFu, i1, off);
+        const float ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, off);
+        gauss_top2(b1, i1, b2, ob1, oi1, ob2);
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xFFFFFFFFu, tmax, off));
+        nan |= __shfl_xor_sync(0xFFFFFFFFu, (int)nan, off) != 0;
+      }
+      const int bi = i1 < C ? i1 : 0;   // every score NaN: class 0, and the row is marked
+      const float sb = sr[bi], tb = tr[bi];
+      float P = 0.f;
+      for (int c = li; c < C; c += LPR)
+        if (c != bi) P += expf(sr[c] - sb);
+#pragma unroll
+      for (int off = LPR / 2; off > 0; off >>= 1) P += __shfl_xor_sync(0xFFFFFFFFu, P, off);
+      const float margin = sb - b2;
       // lp_c = (s_c - s_top) - L: formed from the differences, so that no
       // rounding at the scores' magnitude enters (lp_top = -L exactly)
       const float L = log1pf(P);
       bool flag = false;
       if (a.recheck != NB_RECHECK_OFF) {
-        // label: the top class stays ahead of every other class c by more
-        // than the two classes' bounds (a far class's large bound does not
-        // matter, its score is far below)
-        for (int c = 0; c < a.C; ++c)
-          if (c != bi && !(s[bi] - s[c] > (t[bi] + t[c]) * 1.0001f)) flag = true;
-        if (a.recheck == NB_RECHECK_LP && !flag) {
+        flag = nan;   // a NaN score or bound: FP64 decides
+        // label: the top class stays ahead of every other class c by more than
+        // the two classes' bounds (a far class's large bound does not matter)
+        for (int c = li; c < C; c += LPR)
+          if (c != bi && !(sb - sr[c] > (tb + tr[c]) * 1.0001f)) flag = true;
+        if (a.recheck == NB_RECHECK_LP) {
           // lp_c = d_c - L with d_c = s_c - s_top and L = log(1 + sum_{k != top}
           // e^{d_k}); each d_k is off by at most D = t_top + t_max, so L is off
           // by at most D e^{2D} P / (1 + P) (mean value; the softmax weights at
           // the intermediate point are within e^{2D} of the computed ones), and
           // lp_c by that plus t_c + t_top (c != top)
-          const float D = t[bi] + tmax;
+          const float D = tb + tmax;
           const float eL = D * expf(2.f * D) * (P / (1.f + P)) * 1.01f + 1e-30f;
-          for (int c = 0; c < a.C; ++c) {
-            const float err = (c == bi ? 0.f : t[c] + t[bi]) + eL;
-            if (err > 5e-6f * fmaxf(1.f, fabsf((s[c] - s[bi]) - L))) flag = true;
+          for (int c = li; c < C; c += LPR) {
+            const float err = (c == bi ? 0.f : tr[c] + tb) + eL;
+            if (err > 5e-6f * fmaxf(1.f, fabsf((sr[c] - sb) - L))) flag = true;
           }
         }
       }
-      a.label[r] = flag ? kLabelRecheck : (uint8_t)bi;
-      a.margin[r] = margin;
-      if (a.want_lp)
-        for (int c = 0; c < a.C; ++c) a.logpost[r * a.C + c] = (s[c] - s[bi]) - L;
+      int fl = flag ? 1 : 0;
+#pragma unroll
+      for (int off = LPR / 2; off > 0; off >>= 1) fl |= __shfl_xor_sync(0xFFFFFFFFu, fl, off);
+      if (ok[i]) {
+        const int64_t r = r0 + i;
+        if (li == 0) {
+          a.label[r] = fl ? kLabelRecheck : (uint8_t)bi;
+          a.margin[r] = margin;
+        }
+        if (a.want_lp)
+          for (int c = li; c < C; c += LPR) a.logpost[r * C + c] = (sr[c] - sb) - L;
+      }
     }
     __syncwarp();
   }
+}
+
+template <int LPR, int R, int CB>
+static nb_status run_score_gauss(const GGArgs& a, cudaStream_t st) {
+  constexpr int RPW = (32 / LPR) * R;
+  const int64_t ntile = (a.n + RPW - 1) / RPW;
+  int occ = 0;
+  NB_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &occ, k_score_gauss<LPR, R, CB>, kGaussWarps * 32, 0),
+              "occupancy(k_score_gauss)");
+  const int64_t cap = (int64_t)num_sms() * (occ > 0 ? occ : 1);
+  int64_t blocks = (ntile + kGaussWarps - 1) / kGaussWarps;
+  if (blocks > cap) blocks = cap;
+  count_launch();
+  k_score_gauss<LPR, R, CB><<<(unsigned)blocks, kGaussWarps * 32, 0, st>>>(a);
+  NB_TRY_CUDA(cudaGetLastError(), "k_score_gauss launch");
+  return NB_OK;
+}
+
+// lanes per row: the features a lane sums in sequence stay at most 32 (the
+// rounding depth of the bound); few classes take 4-class blocks of 4 rows
+static nb_status launch_score_gauss(const GGArgs& a, cudaStream_t st) {
+  if (a.C <= 4) {
+    if (a.F > 128) return run_score_gauss<16, 4, 4>(a, st);
+    return run_score_gauss<8, 4, 4>(a, st);
+  }
+  if (a.F > 512) return run_score_gauss<32, 4, 16>(a, st);
+  if (a.F > 128) return run_score_gauss<16, 4, 16>(a, st);
+  return run_score_gauss<8, 2, 16>(a, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,12 +671,7 @@ nb_status launch_score_general(const nb_model* m, const void* X, nb_dtype dt, in
     a.logpost = o.logpost;
     a.want_lp = o.want_lp;
     a.recheck = o.recheck;
-    const int64_t blocks = (n + 7) / 8;
-    const int64_t cap = (int64_t)num_sms() * 8;
-    count_launch();
-    k_score_gauss<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(a);
-    NB_TRY_CUDA(cudaGetLastError(), "k_score_gauss launch");
-    return NB_OK;
+    return launch_score_gauss(a, st);
   }
   const int es = elem_size(dt);
   GArgs a{};

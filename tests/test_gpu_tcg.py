@@ -223,3 +223,39 @@ def test_gaussian_tensor_scorer_empty_and_single_row():
         X, res = _score(model, Xs[:n], nb.NB_RECHECK_LABEL)
         assert nb.score_path(model, X, nb.NB_RECHECK_LABEL) == nb.NB_PATH_TENSOR_GAUSS
         compare(res, oracle.score(Xs[:n], oracle.gauss_fit(Xf, yf, 6)), check_lp=False)
+
+
+# the CUDA-core Gaussian scorer's shapes: 4- and 16-class blocks, groups of 8,
+# 16 and 32 lanes per row (F up to 128, 512 and beyond), staged feature chunks
+# with a ragged last one, block tiles with a ragged last one; the 64-class case
+# past the tensor-core scorer's largest F
+GEN_CASES = [(2, 7, 301), (3, 100, 517), (4, 300, 1000), (5, 33, 259), (17, 200, 700),
+             (64, 64, 1029), (48, 600, 333), (64, 9000, 70)]
+
+
+@pytest.mark.parametrize("C,F,n", GEN_CASES)
+@pytest.mark.parametrize("rc", ["label", "lp"])
+def test_gaussian_cuda_core_scorer_shapes(C, F, n, rc):
+    mode = nb.NB_RECHECK_LP if rc == "lp" else nb.NB_RECHECK_LABEL
+    Xf, yf, Xs = _data(1900 + C + F, C, F, 20, n)
+    model = _fit(Xf, yf, C)
+    model.set_tile_config(nb.NB_VARIANT_REGISTER, 0, 0, 0)
+    X, res = _score(model, Xs, mode)
+    assert nb.score_path(model, X, mode) == nb.NB_PATH_GENERAL
+    compare(res, oracle.score(Xs, oracle.gauss_fit(Xf, yf, C)), check_lp=rc == "lp")
+
+
+def test_gaussian_cuda_core_scorer_close_classes_label_mode():
+    # classes that differ by sampling noise: the bound, not the margin,
+    # decides; the rows it does not settle go to FP64 and every label matches
+    C, F = 24, 300
+    rng = np.random.default_rng(1950)
+    mu = rng.uniform(0.0, 10.0, size=F)
+    sd = rng.uniform(0.5, 3.0, size=F)
+    yf = np.concatenate([np.arange(C), rng.integers(0, C, 30 * C - C)]).astype(np.int32)
+    Xf = rng.normal(mu, sd, size=(yf.shape[0], F)).astype(np.float32)
+    Xs = rng.normal(mu, sd, size=(1500, F)).astype(np.float32)
+    model = _fit(Xf, yf, C)
+    model.set_tile_config(nb.NB_VARIANT_REGISTER, 0, 0, 0)
+    _, res = _score(model, Xs, nb.NB_RECHECK_LABEL)
+    compare(res, oracle.score(Xs, oracle.gauss_fit(Xf, yf, C)), check_lp=False)
