@@ -313,9 +313,10 @@ static int pick_lpr(int nvec_row) {
   return lpr;
 }
 
-// u8 rows: about eight 16-byte vectors per lane and at least two lanes per row
-// (measured, 4M files: F = 256 at 89% of HBM against 61% with two vectors per
-// lane; F = 64 at 65% against 61%, F = 4096 unchanged at 98%)
+// u8 and FP8 rows: about eight 16-byte vectors per lane and at least two lanes
+// per row (measured, 4M files: u8 F = 256 at 89% of HBM against 61% with two
+// vectors per lane, F = 64 at 65% against 61%, F = 4096 unchanged at 98%; FP8
+// F = 256 at 54% against 36%, F = 1024 at 48% against 37%)
 static int pick_lpr_u8(int nvec_row) {
   int lpr = 2;
   while (lpr < 32 && lpr * 8 < nvec_row) lpr *= 2;
@@ -348,6 +349,11 @@ static nb_status dispatch_dt(nb_dtype dt, S2Args& a, int smem, cudaStream_t st) 
     case NB_BF16:
       return launch_persistent(k_score2_fp<NB_BF16, LPR, R>, smem, ntiles, a, st);
     case NB_FP8E4M3:
+      if (a.nvec_row < 16) {
+        const int64_t rpw2 = (32 / LPR) * 2;
+        return launch_persistent(k_score2_u8<NB_FP8E4M3, LPR, 2>, smem, (a.n + rpw2 - 1) / rpw2,
+                                 a, st);
+      }
       return launch_persistent(k_score2_u8<NB_FP8E4M3, LPR, R>, smem, ntiles, a, st);
   }
   set_error("unknown dtype");
@@ -403,7 +409,8 @@ nb_status launch_score2(const nb_model* m, const void* X, nb_dtype dt, int64_t n
                            side_ok ? 1 : 0, st);
     if (s != NB_EUNSUPPORTED || cfg.variant == NB_VARIANT_PIPELINED) return s;
   }
-  const int lpr = dt == NB_U8 ? pick_lpr_u8(a.nvec_row) : pick_lpr(a.nvec_row);
+  const int lpr = (dt == NB_U8 || dt == NB_FP8E4M3) ? pick_lpr_u8(a.nvec_row)
+                                                    : pick_lpr(a.nvec_row);
   {
     const int epv = 16 / es;
     const int per_lane = (a.nvec_row + lpr - 1) / lpr;
