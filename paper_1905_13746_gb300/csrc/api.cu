@@ -77,7 +77,7 @@ static nb_status alloc_model(nb_model* m) {
   const size_t o_wmax = take(sizeof(float) * 4);
   const size_t o_gmu = take(m->kind == NB_GAUSSIAN ? sizeof(float) * gauss_cpad(C) * Fp : 0);
   const size_t o_giv = take(m->kind == NB_GAUSSIAN ? sizeof(float) * gauss_cpad(C) * Fp : 0);
-  const size_t o_gk = take(sizeof(float) * C);
+  const size_t o_gk = take(sizeof(float) * 2 * C);
   const bool tc = tc_tables(m->kind, m->C, m->F);
   const size_t o_tcw = take(tc ? tc_w_bytes(m->C, m->F) : 0);
   const size_t o_tcq = take(tc ? sizeof(int32_t) * C * F : 0);

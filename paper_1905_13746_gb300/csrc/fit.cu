@@ -995,16 +995,33 @@ __global__ void __launch_bounds__(256) k_gauss_finalize(
   }
   __syncthreads();
   const double kTwoPi = 6.283185307179586476925;
+  __shared__ double red4[8];
   for (int c = 0; c < C; ++c) {
-    double s = 0.0;
-    for (int j = threadIdx.x; j < F; j += blockDim.x) s += log(kTwoPi * var[(int64_t)c * F + j]);
+    // sum_j log(2 pi var_cj), and a4_c = sum_j m^2 v over the FP32 tables (a
+    // term of the CUDA-core scorer's rounding bound)
+    double s = 0.0, s4 = 0.0;
+    for (int j = threadIdx.x; j < F; j += blockDim.x) {
+      s += log(kTwoPi * var[(int64_t)c * F + j]);
+      const double mj = g_mu[(int64_t)j * CP + c];
+      s4 += mj * mj * (double)g_ivar[(int64_t)j * CP + c];
+    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
-    if (lane == 0) red[warp] = s;
+    for (int off = 16; off > 0; off >>= 1) {
+      s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+      s4 += __shfl_xor_sync(0xFFFFFFFFu, s4, off);
+    }
+    if (lane == 0) {
+      red[warp] = s;
+      red4[warp] = s4;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      double t = 0.0, t4 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        t += red[w];
+        t4 += red4[w];
+      }
+      g_const[C + c] = (float)t4;
       if (!prior_given) {
         if (nc[c] == 0) atomicOr(status, ST_BAD_LABEL);
         log_pi[c] = nc[c] ? log((double)nc[c]) - log((double)n) : 0.0;

@@ -118,7 +118,7 @@ struct ModelDev {
   // Gaussian FP32 tables
   float* g_mu;         // F_pad x gauss_cpad(C), feature-major (classes past C: 0)
   float* g_ivar;       // same layout, 1 / var
-  float* g_const;      // C          gconst in FP32
+  float* g_const;      // 2C         gconst in FP32, then a4_c = sum_j m^2 v (FP32 tables)
   // Gaussian tensor-core tables (3 <= C <= kTcMaxC, F <= kTcgMaxF), else nullptr;
   // the FP16 limbs of B and A go to tc_w
   float* tcg_kc;       // C          K_c

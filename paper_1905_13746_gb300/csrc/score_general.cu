@@ -344,24 +344,11 @@ __global__ void __launch_bounds__(kGaussWarps * 32, 2) k_score_gauss(const GGArg
   static_assert(NP % LPR == 0, "the reduce-scatter ends with whole pairs per lane");
   __shared__ __align__(16) float s_tab[FC * SR];
   __shared__ float s_s[kGaussWarps][RPW][CM], s_t[kGaussWarps][RPW][CM];
-  __shared__ float s_a4[kTcMaxC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / LPR, li = lane % LPR;
   const int C = a.C, F = a.F, CP = gauss_cpad(C);
   constexpr float u = 5.9604645e-8f;
 
-  // a4_c = sum_j mu_cj^2 v_cj (row independent; enters the bound only)
-  for (int c = warp; c < C; c += kGaussWarps) {
-    float s4 = 0.f;
-    for (int j = lane; j < F; j += 32) {
-      const float m = a.mu[(int64_t)j * CP + c];
-      s4 = fmaf(m * m, a.ivar[(int64_t)j * CP + c], s4);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s4 += __shfl_xor_sync(0xFFFFFFFFu, s4, off);
-    if (lane == 0) s_a4[c] = s4;
-  }
-  __syncthreads();
   // rounding depth of each sum: F / LPR sequential adds, the log2 LPR
   // combining levels, and 8 for the remaining operations
   int lg = 0;
@@ -448,11 +435,12 @@ __global__ void __launch_bounds__(kGaussWarps * 32, 2) k_score_gauss(const GGArg
         // u (|k_c| + |s|).  sum v |dx| |m| <= sqrt(sum v dx^2 sum v m^2)
         // (Cauchy-Schwarz on the FP32 values; 1e-3 covers the rounding of the
         // two computed sums); 1% slack covers the FP32 evaluation of the bound.
-        const float aa = sqrtf(qq * s_a4[c]) * 1.001f;
+        const float a4 = a.kc[C + c];   // sum_j m^2 v, from the fit
+        const float aa = sqrtf(qq * a4) * 1.001f;
         const float sc = kc - 0.5f * qq;
         s_s[warp][grp * R + i][c] = sc;
         s_t[warp][grp * R + i][c] = (0.5f * (u * (4.f * qq + 2.f * aa) * (1.f + 2.f * u) +
-                                             2.f * u * u * (qq + s_a4[c]) + gam * qq) +
+                                             2.f * u * u * (qq + a4) + gam * qq) +
                                      u * (fabsf(kc) + fabsf(sc))) * 1.01f +
                                     1e-12f * (qq + fabsf(kc)) + 1e-30f;
       }
