@@ -334,7 +334,9 @@ __global__ void __launch_bounds__(kGaussWarps * 32, 2) k_score_gauss(const GGArg
   constexpr int RPB = kGaussWarps * RPW;   // rows per block tile
   constexpr int NP = CB * R;      // sums q of a class block
   constexpr int OWN = NP / LPR;   // pairs a lane finishes
-  constexpr int CM = CB == 4 ? 4 : kTcMaxC;   // classes kept per row
+  // classes kept per row; 64 + 4 puts the rows of a warp's groups on different
+  // banks for the epilogue's reads of class li + LPR m
+  constexpr int CM = CB == 4 ? 4 : kTcMaxC + 4;
   constexpr int FPL = LPR == 8 ? 8 : 4;   // features per lane per staged chunk
   constexpr int FC = LPR * FPL;   // features per staged chunk
   // a staged feature holds the class block's mu (CB floats) then v; the row
